@@ -1,0 +1,196 @@
+/*
+ * aqmp.h -- C ABI of the GB300 (sm_103a) AQMP encoder library, libaqmp.so.
+ *
+ * AQMP (Adaptive Quadtree Matching Pursuit) encodes each image plane by
+ * Matching Pursuit over the blocks of a quadtree: a block that misses the
+ * accuracy tolerance within its atom budget is split into four quadrants
+ * that restart from the original pixels (Section 2.3, Algorithms 1-2); a
+ * decoder rebuilds the plane as y = D_N x per leaf (Algorithm 3).
+ *
+ * Conventions shared by every entry point:
+ *   - Return 0 (AQMP_OK) or a negative AQMP_E_* code; aqmp_last_error()
+ *     then holds a one-line message for the calling thread.
+ *   - Pointers are plain host or device addresses as stated per argument;
+ *     nothing here takes ownership of caller memory.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *     enqueued on it; calls that return counts synchronise it first.
+ *   - There is no CPU fallback: without a usable sm_103a GPU every call that
+ *     computes returns AQMP_E_CUDA.
+ */
+#ifndef AQMP_H
+#define AQMP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AQMP_OK                 0
+#define AQMP_E_ARG             -1  /* NULL pointer, bad block sizes or parameters */
+#define AQMP_E_SHAPE           -2  /* plane size not a multiple of max_block */
+#define AQMP_E_DICT            -3  /* unknown dictionary id */
+#define AQMP_E_OOM             -4  /* device or host allocation failed */
+#define AQMP_E_CUDA            -5  /* CUDA runtime / driver error, or no usable GPU */
+#define AQMP_E_QUEUE_OVERFLOW  -6  /* a device work queue or output ran out of room */
+#define AQMP_E_TIMEOUT         -7  /* a bounded device wait gave up */
+#define AQMP_E_UNSUPPORTED     -8  /* valid request this build does not serve */
+
+/* Dictionaries (Section 2.3 / Appendix A: a DCT basis concatenated with
+ * Haar wavelets).  At block side b the atoms are the b^2 2-D DCT-II atoms
+ * (Section 2.1, Eq. (1)-(2), outer products of 1-D rows) followed by the b^2
+ * 2-D Haar atoms; the single-family dictionaries exist for testing. */
+#define AQMP_DICT_DCT_HAAR  0      /* M = 2 b^2 atoms */
+#define AQMP_DICT_DCT       1      /* M = b^2 */
+#define AQMP_DICT_HAAR      2      /* M = b^2 */
+
+/* Arithmetic of the pursuit (see aqmp_params.precision). */
+#define AQMP_PREC_EXACT     0      /* exact-limb BF16 tensor-core correlation +
+                                      double-float pursuit: decisions agree with
+                                      an FP64 evaluation except where a
+                                      decision margin is below ~2^-36 of the
+                                      block norm, and such leaves are flagged */
+
+/* aqmp_params.flags */
+#define AQMP_FLAG_INPUT_DEVICE  1u /* plane pointers are device addresses */
+#define AQMP_FLAG_SIMT_GEMM     2u /* compute the initial correlation with the
+                                      integer SIMT kernel instead of tcgen05
+                                      (bit-identical result; for validation) */
+
+typedef struct {
+    float   rmse_tol;     /* per-block RMSE tolerance on the 0-255 scale:
+                             a block converges when ||r||^2 < tol^2 b^2
+                             (Eq. (3) with eps = tol b); >= 0 */
+    int32_t cap_num;      /* atom budget k(b) = max(1, b^2 cap_num / cap_den) */
+    int32_t cap_den;      /*   (min_sparsity of Algorithm 2), cap <= 1 */
+    int32_t min_block;    /* N_min, N_max: powers of two, 4 <= N_min <= N_max */
+    int32_t max_block;    /*   <= 64 (Section 2.3, set S) */
+    int32_t dict_id;      /* AQMP_DICT_* */
+    int32_t precision;    /* AQMP_PREC_* */
+    uint32_t flags;       /* AQMP_FLAG_* */
+} aqmp_params;
+
+/* Default parameters: tol 2, k = b^2/4, blocks 64 -> 4, DCT+Haar, exact. */
+void aqmp_params_default(aqmp_params *p);
+
+/* One 8-bit plane to encode (Algorithm 1 processes channels independently;
+ * each plane carries its own tolerance so that a batch can sweep it). */
+typedef struct {
+    const uint8_t *pixels;  /* row-major; host or device per the flags */
+    int32_t height;         /* multiples of max_block */
+    int32_t width;
+    int64_t pitch;          /* bytes between rows, >= width */
+    float   rmse_tol;       /* this plane's tolerance; < 0 = params->rmse_tol */
+} aqmp_plane;
+
+/* One leaf of the quadtree: block side b at (y, x) of `plane`, owning atoms
+ * [atom_off, atom_off + n_atoms) of the atom array. */
+typedef struct {
+    uint32_t plane;
+    uint32_t y, x;
+    uint32_t atom_off;
+    uint16_t b;
+    uint16_t n_atoms;
+    uint8_t  converged;     /* 1 if ||r||^2 < eps^2 was reached */
+    uint8_t  flags;         /* AQMP_LEAF_* */
+    uint16_t reserved;
+} aqmp_leaf;
+
+#define AQMP_LEAF_NEAR_TIE        1u  /* a decision of this leaf's pursuit fell
+                                         inside the certification band */
+#define AQMP_LEAF_NEAR_TIE_PARENT 2u  /* ... or one of an ancestor's (failed)
+                                         pursuits did */
+
+/* One MP step: atom index j (DCT atoms 0..b^2-1, Haar atoms b^2..2b^2-1;
+ * within a family atom (p, q) has index q b + p) and coefficient alpha.
+ * A leaf's atoms are listed in the order the pursuit chose them. */
+typedef struct {
+    uint32_t j;
+    float    alpha;
+} aqmp_atom;
+
+/* Work and outcome counters of one encode call. */
+typedef struct {
+    uint64_t n_leaves;
+    uint64_t n_atoms;
+    uint64_t attempts;          /* pursuits run, including those that split */
+    uint64_t atom_iterations;   /* MP steps run, including those of split blocks */
+    uint64_t near_tie_leaves;   /* leaves with any AQMP_LEAF_* flag */
+    uint64_t attempts_per_level[8];
+    uint64_t iterations_per_level[8];
+} aqmp_stats;
+
+typedef struct aqmp_code aqmp_code;   /* opaque, library-owned result */
+
+/* Encode `n_planes` planes (Algorithms 1-2).  Pixels are read on `stream`
+ * (copied in first when they are host memory); on success *out receives a
+ * new code object whose leaf and atom arrays live in device memory.  The
+ * call synchronises `stream` before returning.  Errors: AQMP_E_ARG,
+ * AQMP_E_SHAPE, AQMP_E_DICT, AQMP_E_OOM, AQMP_E_CUDA, AQMP_E_QUEUE_OVERFLOW,
+ * AQMP_E_TIMEOUT; *out is left NULL on error. */
+int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int n_planes,
+                       void *stream, aqmp_code **out);
+
+/* Convenience form: `channels` planes of h x w stacked one after another,
+ * plane c starting at pixels + c h pitch; every plane uses params->rmse_tol. */
+int aqmp_encode(const aqmp_params *params, const uint8_t *pixels, int channels, int h, int w,
+                size_t pitch, void *stream, aqmp_code **out);
+
+/* Counters of a finished encode (host struct, filled in place). */
+int aqmp_code_stats(const aqmp_code *code, aqmp_stats *stats);
+
+/* Host copies of the result in canonical order: planes ascending, roots
+ * row-major, leaves depth-first with children TL, TR, BL, BR.  `leaves`
+ * needs stats.n_leaves entries and `atoms` stats.n_atoms; atom_off in the
+ * copied leaves indexes the copied atom array.  `alpha_lo`, if not NULL,
+ * receives n_atoms floats: the low word of each coefficient as computed
+ * (alpha = atoms[i].alpha + alpha_lo[i] to ~2^-48 relative). */
+int aqmp_code_copy(const aqmp_code *code, aqmp_leaf *leaves, aqmp_atom *atoms, float *alpha_lo);
+
+/* Decode one plane (Algorithm 3): writes height x width floats, row-major
+ * with `out_pitch` elements between rows, into `out` (device memory if
+ * out_is_device, else host memory).  Unclipped reconstruction. */
+int aqmp_decode(const aqmp_code *code, int plane, float *out, int64_t out_pitch,
+                int out_is_device, void *stream);
+
+void aqmp_code_free(aqmp_code *code);
+
+/* The initial correlation of Section 2.2 step (b) for a batch of L blocks
+ * of side b: c[l][j] = <y_l, phi_j> for every atom j, with y_l the
+ * column-major unravel of block l (Appendix A).  `blocks` is device memory
+ * holding L blocks of b x b bytes, each row-major and contiguous; `corr` is
+ * device memory for L x M float pairs (hi, lo) whose sum is the correlation
+ * of the 2^-48 fixed-point dictionary with the block, rounded once.
+ * gemm: 0 = tcgen05 tensor-core kernel, 1 = integer SIMT kernel. */
+int aqmp_correlate(int b, int dict_id, const uint8_t *blocks, int64_t L, float *corr,
+                   int gemm, void *stream);
+
+/* Kernel timing.  While enabled, every kernel the library launches is
+ * bracketed by CUDA events on the stream it runs on; the durations are
+ * folded into per-kernel totals when the launching call synchronises.
+ * Names are "<kernel>_b<side>" (e.g. "mp_b64", "corr_tc_b16"). */
+typedef struct {
+    char     name[32];
+    uint64_t launches;
+    double   total_ms;
+} aqmp_kernel_time;
+
+int  aqmp_profile_enable(int on);                 /* returns the previous state */
+void aqmp_profile_reset(void);
+/* Copies up to `max` entries into `out` (host); *n receives the count. */
+int  aqmp_profile_read(aqmp_kernel_time *out, int max, int *n);
+
+/* Number of atoms M of a dictionary at side b (2 b^2 or b^2), or < 0. */
+int aqmp_num_atoms(int b, int dict_id);
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char *aqmp_last_error(void);
+
+/* Library version string. */
+const char *aqmp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AQMP_H */

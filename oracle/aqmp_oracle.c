@@ -24,7 +24,8 @@
  *
  * Readings where the paper is silent (each is listed in the design notes):
  *   eps^2 = tol^2 * b^2 on the 0-255 scale (a per-block RMSE tolerance),
- *   strict "<"; the budget counts MP steps; ties go to the lowest atom index;
+ *   strict "<"; the budget counts MP steps; ties go to the lowest atom index,
+ *   equality being decided to 2^-32 of the block norm (see TIE_REL);
  *   a zero correlation vector ends the pursuit; children are visited TL, TR,
  *   BL, BR and leaves are emitted in that depth-first order.
  */
@@ -109,6 +110,17 @@ int oracle_dictionary(int b, int dict_id, double *D)
 
 /* ------------------------------------------------------- Matching Pursuit */
 
+/* Equality in finite precision.  "Ties go to the lowest atom index" is a
+ * statement about exact values; two magnitudes that are equal in exact
+ * arithmetic come out of any floating-point evaluation a few units of
+ * rounding apart, in an order that depends on the evaluation.  So both this
+ * oracle and the library treat correlations within TIE_REL * ||y|| of the
+ * largest as tied (the lowest index among them wins), and an energy within
+ * TIE_REL * ||y||^2 of eps^2 as equal to it (not below it: the test stays
+ * strict).  TIE_REL = 2^-32 is far above either side's rounding error and
+ * far below any difference that matters for the image. */
+#define TIE_REL 0x1p-32
+
 /* MP(D, y, eps, k), Section 2.2 steps (a)-(d) with the stop rule Eq. (3).
  * r^0 = y.  Before every step the residual energy E = sum r^2 is recomputed;
  * E < eps2 ends the pursuit as converged; after k steps it ends unconverged.
@@ -117,8 +129,9 @@ int oracle_dictionary(int b, int dict_id, double *D)
  * r <- r - alpha phi_j.  A step whose largest |correlation| is exactly zero
  * ends the pursuit unconverged (nothing can be removed).
  *
- * Outputs (capacity k): out_j, out_alpha, out_margin[t] = |c_(1)| - |c_(2)|
- * at step t (second largest over the other atoms), out_energy[t] for
+ * Outputs (capacity k): out_j, out_alpha, out_margin[t] = distance of the
+ * nearest other atom's |c| to the tie boundary max|c| - TIE_REL ||y||
+ * (atoms identical to the chosen one excluded), out_energy[t] for
  * t = 0..steps (capacity k+1).  Any output pointer may be NULL.
  * Returns the number of steps taken. */
 int oracle_mp(const double *D, int n, int M, const double *y, double eps2, int k,
@@ -129,13 +142,16 @@ int oracle_mp(const double *D, int n, int M, const double *y, double eps2, int k
     double *c = malloc(sizeof(double) * M);
     if (!r || !c) { free(r); free(c); return -2; }
     memcpy(r, y, sizeof(double) * n);
+    double S2 = 0.0;
+    for (int v = 0; v < n; ++v) S2 += y[v] * y[v];
+    const double tie_c = TIE_REL * sqrt(S2), tie_e = TIE_REL * S2;
     int t = 0;
     *converged = 0;
     for (;;) {
         double E = 0.0;
         for (int v = 0; v < n; ++v) E += r[v] * r[v];
         if (out_energy) out_energy[t] = E;
-        if (E < eps2) { *converged = 1; break; }
+        if (E < eps2 - tie_e) { *converged = 1; break; }
         if (t == k) break;
         /* c[j] = <r, phi_j>, summed over ascending v.  Eight atoms are summed
          * side by side only to keep the CPU's adders busy: each c[j] is the
@@ -160,25 +176,30 @@ int oracle_mp(const double *D, int n, int M, const double *y, double eps2, int k
             for (int v = 0; v < n; ++v) s += phi[v] * r[v];
             c[j] = s;
         }
-        /* lowest index of largest magnitude */
+        /* largest magnitude, then the lowest index tied with it */
+        double cmax = 0.0;
+        for (j = 0; j < M; ++j)
+            if (fabs(c[j]) > cmax) cmax = fabs(c[j]);
+        if (cmax == 0.0) break;
+        const double edge = cmax - tie_c;
         int best = 0;
-        for (j = 1; j < M; ++j)
-            if (fabs(c[j]) > fabs(c[best])) best = j;
-        if (c[best] == 0.0) break;
+        while (fabs(c[best]) < edge) ++best;
         double alpha = c[best];
-        /* decision margin: gap to the largest |c| among atoms that differ from
-         * the chosen one (an atom listed twice, such as the DCT DC atom and
-         * the Haar scaling atom, always ties with itself) */
+        /* decision margin: nearest other atom to the tie boundary (an atom
+         * listed twice, such as the DCT DC atom and the Haar scaling atom,
+         * always ties with itself and is left out) */
         const double *pb = D + (size_t)best * n;
-        double second = 0.0;
+        double margin = INFINITY;
         for (j = 0; j < M; ++j) {
-            if (j == best || fabs(c[j]) < second) continue;
+            if (j == best) continue;
+            double d = fabs(fabs(c[j]) - edge);
+            if (d >= margin) continue;
             if (memcmp(D + (size_t)j * n, pb, sizeof(double) * n) == 0) continue;
-            second = fabs(c[j]);
+            margin = d;
         }
         if (out_j) out_j[t] = best;
         if (out_alpha) out_alpha[t] = alpha;
-        if (out_margin) out_margin[t] = fabs(alpha) - second;
+        if (out_margin) out_margin[t] = margin;
         for (int v = 0; v < n; ++v) r[v] -= alpha * pb[v];
         ++t;
     }

@@ -1,0 +1,275 @@
+"""Thin ctypes binding of libaqmp.so (include/aqmp.h): argument marshalling
+only.  Every step of the encoder runs in the library's CUDA kernels; there is
+no Python or CPU fallback, and a missing library raises immediately.
+
+Names follow the C ABI: ``aqmp_encode_planes``, ``aqmp_encode``,
+``aqmp_decode``, ``aqmp_code_copy``, ``aqmp_code_stats``, ``aqmp_correlate``,
+``aqmp_num_atoms``.  Device memory and streams come from PyTorch tensors and
+``torch.cuda.current_stream()``; numpy arrays are accepted as host memory.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libaqmp.so")
+
+AQMP_OK = 0
+ERRORS = {-1: "AQMP_E_ARG", -2: "AQMP_E_SHAPE", -3: "AQMP_E_DICT", -4: "AQMP_E_OOM", -5: "AQMP_E_CUDA",
+          -6: "AQMP_E_QUEUE_OVERFLOW", -7: "AQMP_E_TIMEOUT", -8: "AQMP_E_UNSUPPORTED"}
+AQMP_DICT_DCT_HAAR, AQMP_DICT_DCT, AQMP_DICT_HAAR = 0, 1, 2
+AQMP_PREC_EXACT = 0
+AQMP_FLAG_INPUT_DEVICE = 1
+AQMP_FLAG_SIMT_GEMM = 2
+AQMP_LEAF_NEAR_TIE = 1
+AQMP_LEAF_NEAR_TIE_PARENT = 2
+
+
+class AqmpError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class aqmp_params(ctypes.Structure):
+    _fields_ = [("rmse_tol", ctypes.c_float), ("cap_num", ctypes.c_int32), ("cap_den", ctypes.c_int32),
+                ("min_block", ctypes.c_int32), ("max_block", ctypes.c_int32), ("dict_id", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+
+
+class aqmp_plane(ctypes.Structure):
+    _fields_ = [("pixels", ctypes.c_void_p), ("height", ctypes.c_int32), ("width", ctypes.c_int32),
+                ("pitch", ctypes.c_int64), ("rmse_tol", ctypes.c_float)]
+
+
+class aqmp_stats(ctypes.Structure):
+    _fields_ = [("n_leaves", ctypes.c_uint64), ("n_atoms", ctypes.c_uint64), ("attempts", ctypes.c_uint64),
+                ("atom_iterations", ctypes.c_uint64), ("near_tie_leaves", ctypes.c_uint64),
+                ("attempts_per_level", ctypes.c_uint64 * 8), ("iterations_per_level", ctypes.c_uint64 * 8)]
+
+
+LEAF_DTYPE = np.dtype([("plane", np.uint32), ("y", np.uint32), ("x", np.uint32), ("atom_off", np.uint32),
+                       ("b", np.uint16), ("n_atoms", np.uint16), ("converged", np.uint8),
+                       ("flags", np.uint8), ("reserved", np.uint16)])
+ATOM_DTYPE = np.dtype([("j", np.uint32), ("alpha", np.float32)])
+
+# symbols declared in include/aqmp.h
+EXPORTS = ["aqmp_params_default", "aqmp_encode_planes", "aqmp_encode", "aqmp_code_stats", "aqmp_code_copy",
+           "aqmp_decode", "aqmp_code_free", "aqmp_correlate", "aqmp_num_atoms", "aqmp_last_error",
+           "aqmp_version", "aqmp_profile_enable", "aqmp_profile_reset", "aqmp_profile_read"]
+
+
+class aqmp_kernel_time(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double)]
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load_library(path: str | None = None):
+    """Load libaqmp.so (built by ``build_lib``); raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise ImportError(f"libaqmp.so not built at {p}: run `python -m paper_2605_09190_gb300.build_lib`")
+        lib = ctypes.CDLL(p)
+        V, I, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+        lib.aqmp_params_default.argtypes = [ctypes.POINTER(aqmp_params)]
+        lib.aqmp_params_default.restype = None
+        lib.aqmp_encode_planes.argtypes = [ctypes.POINTER(aqmp_params), ctypes.POINTER(aqmp_plane), I, V,
+                                           ctypes.POINTER(V)]
+        lib.aqmp_encode.argtypes = [ctypes.POINTER(aqmp_params), V, I, I, I, ctypes.c_size_t, V, ctypes.POINTER(V)]
+        lib.aqmp_code_stats.argtypes = [V, ctypes.POINTER(aqmp_stats)]
+        lib.aqmp_code_copy.argtypes = [V, V, V, V]
+        lib.aqmp_decode.argtypes = [V, I, V, I64, I, V]
+        lib.aqmp_code_free.argtypes = [V]
+        lib.aqmp_code_free.restype = None
+        lib.aqmp_correlate.argtypes = [I, I, V, I64, V, I, V]
+        lib.aqmp_num_atoms.argtypes = [I, I]
+        lib.aqmp_last_error.restype = ctypes.c_char_p
+        lib.aqmp_version.restype = ctypes.c_char_p
+        lib.aqmp_profile_enable.argtypes = [I]
+        lib.aqmp_profile_reset.argtypes = []
+        lib.aqmp_profile_reset.restype = None
+        lib.aqmp_profile_read.argtypes = [V, I, ctypes.POINTER(I)]
+        if path is None:
+            _lib = lib
+        return lib
+
+
+def _check(rc):
+    if rc != AQMP_OK:
+        msg = load_library().aqmp_last_error().decode(errors="replace")
+        raise AqmpError(rc, msg)
+
+
+def _stream_handle(stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def default_params(**kw) -> aqmp_params:
+    p = aqmp_params()
+    load_library().aqmp_params_default(ctypes.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+class Code:
+    """An encode result (library-owned, device resident)."""
+
+    def __init__(self, handle):
+        self._h = ctypes.c_void_p(handle)
+
+    def __del__(self):
+        self.free()
+
+    def free(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load_library().aqmp_code_free(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def stats(self) -> dict:
+        return aqmp_code_stats(self)
+
+    def copy(self):
+        return aqmp_code_copy(self)
+
+    def decode(self, plane: int = 0, out=None, stream=None):
+        return aqmp_decode(self, plane, out, stream)
+
+
+def _as_plane(x, tol, device_input):
+    if hasattr(x, "data_ptr"):             # torch tensor
+        if x.dtype.itemsize != 1 or x.dim() != 2 or x.stride(1) != 1:
+            raise ValueError("planes must be 2-D uint8 tensors with unit column stride")
+        h, w = x.shape
+        ptr, pitch = x.data_ptr(), x.stride(0)
+        on_dev = x.is_cuda
+    else:
+        x = np.ascontiguousarray(x, np.uint8)
+        h, w = x.shape
+        ptr, pitch, on_dev = x.ctypes.data, x.strides[0], False
+    if on_dev != device_input:
+        raise ValueError("all planes must be either device (CUDA) tensors or host arrays")
+    return aqmp_plane(ptr, h, w, pitch, -1.0 if tol is None else float(tol)), x
+
+
+def aqmp_encode_planes(planes, tols=None, params: aqmp_params | None = None, stream=None, simt_gemm=False,
+                       **param_kw) -> Code:
+    """Encode a list of 2-D uint8 planes (torch CUDA tensors, or host numpy
+    arrays / CPU tensors), one optional tolerance per plane."""
+    if params is None:
+        params = default_params(**param_kw)
+    first = planes[0]
+    device_input = bool(getattr(first, "is_cuda", False))
+    if tols is None or np.isscalar(tols):
+        tols = [tols] * len(planes)
+    arr = (aqmp_plane * len(planes))()
+    keep = []
+    for i, (pl, t) in enumerate(zip(planes, tols)):
+        arr[i], ref = _as_plane(pl, t, device_input)
+        keep.append(ref)
+    p = aqmp_params.from_buffer_copy(params)
+    p.flags = (p.flags | (AQMP_FLAG_INPUT_DEVICE if device_input else 0)
+               | (AQMP_FLAG_SIMT_GEMM if simt_gemm else 0))
+    out = ctypes.c_void_p()
+    _check(load_library().aqmp_encode_planes(ctypes.byref(p), arr, len(planes), _stream_handle(stream),
+                                             ctypes.byref(out)))
+    return Code(out.value)
+
+
+def aqmp_encode(pixels, params: aqmp_params | None = None, stream=None, **param_kw) -> Code:
+    """Encode a (channels, h, w) uint8 stack with the parameters' tolerance."""
+    return aqmp_encode_planes([pixels[c] for c in range(pixels.shape[0])], None, params, stream, **param_kw)
+
+
+def aqmp_code_stats(code: Code) -> dict:
+    s = aqmp_stats()
+    _check(load_library().aqmp_code_stats(code.handle, ctypes.byref(s)))
+    return {"n_leaves": s.n_leaves, "n_atoms": s.n_atoms, "attempts": s.attempts,
+            "atom_iterations": s.atom_iterations, "near_tie_leaves": s.near_tie_leaves,
+            "attempts_per_level": list(s.attempts_per_level),
+            "iterations_per_level": list(s.iterations_per_level)}
+
+
+def aqmp_code_copy(code: Code):
+    """Host copies (leaves, atoms, alpha_lo) in canonical depth-first order."""
+    st = aqmp_code_stats(code)
+    leaves = np.zeros(st["n_leaves"], LEAF_DTYPE)
+    atoms = np.zeros(st["n_atoms"], ATOM_DTYPE)
+    lo = np.zeros(st["n_atoms"], np.float32)
+    _check(load_library().aqmp_code_copy(code.handle, leaves.ctypes.data, atoms.ctypes.data, lo.ctypes.data))
+    return leaves, atoms, lo
+
+
+def aqmp_decode(code: Code, plane: int = 0, out=None, stream=None):
+    """Decode one plane into `out` (a CUDA float32 tensor, or a new host
+    numpy array when `out` is None)."""
+    lib = load_library()
+    if out is None:
+        st = aqmp_code_stats(code)          # noqa: F841 (validates the handle)
+        raise ValueError("pass an output buffer (torch CUDA tensor or numpy float32 array)")
+    if hasattr(out, "data_ptr"):
+        _check(lib.aqmp_decode(code.handle, plane, ctypes.c_void_p(out.data_ptr()), out.stride(0),
+                               1 if out.is_cuda else 0, _stream_handle(stream)))
+    else:
+        if out.dtype != np.float32 or not out.flags.c_contiguous:
+            raise ValueError("host output must be a C-contiguous float32 array")
+        _check(lib.aqmp_decode(code.handle, plane, ctypes.c_void_p(out.ctypes.data), out.shape[1], 0,
+                               _stream_handle(stream)))
+    return out
+
+
+def aqmp_correlate(b: int, dict_id: int, blocks, gemm: int = 0, stream=None):
+    """Initial correlations of L contiguous b x b uint8 blocks (a CUDA tensor
+    of shape (L, b, b)); returns a CUDA float32 tensor (L, M, 2) of
+    double-float pairs."""
+    import torch
+    L = blocks.shape[0]
+    M = aqmp_num_atoms(b, dict_id)
+    out = torch.empty((L, M, 2), dtype=torch.float32, device=blocks.device)
+    _check(load_library().aqmp_correlate(b, dict_id, ctypes.c_void_p(blocks.data_ptr()), L,
+                                         ctypes.c_void_p(out.data_ptr()), gemm, _stream_handle(stream)))
+    return out
+
+
+def aqmp_num_atoms(b: int, dict_id: int) -> int:
+    m = load_library().aqmp_num_atoms(b, dict_id)
+    if m < 0:
+        raise AqmpError(m, "bad side or dictionary")
+    return m
+
+
+def aqmp_version() -> str:
+    return load_library().aqmp_version().decode()
+
+
+def aqmp_profile_enable(on: bool = True) -> bool:
+    return bool(load_library().aqmp_profile_enable(1 if on else 0))
+
+
+def aqmp_profile_reset() -> None:
+    load_library().aqmp_profile_reset()
+
+
+def aqmp_profile_read() -> dict:
+    """{kernel name: (launches, total milliseconds)} accumulated so far."""
+    arr = (aqmp_kernel_time * 64)()
+    n = ctypes.c_int(0)
+    _check(load_library().aqmp_profile_read(arr, 64, ctypes.byref(n)))
+    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(n.value)}

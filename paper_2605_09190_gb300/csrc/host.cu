@@ -1,0 +1,730 @@
+// host.cu -- the C ABI of libaqmp.so: dictionary tables, device workspace,
+// the level-synchronous quadtree loop (Algorithms 1-2) and the decoder entry
+// (Algorithm 3).  All compute runs in this library's kernels; there is no
+// CPU path.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/aqmp.h"
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace aqmp;
+
+static_assert(sizeof(LeafRec) == sizeof(aqmp_leaf), "leaf record layout");
+static_assert(sizeof(AtomRec) == sizeof(aqmp_atom), "atom record layout");
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+#define CK(call)                                                                            \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return fail(e_ == cudaErrorMemoryAllocation ? AQMP_E_OOM : AQMP_E_CUDA,         \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+int ilog2(int v) { int l = 0; while ((1 << l) < v) ++l; return l; }
+
+// ---------------------------------------------------------------- FP64 bases
+//
+// The library's own generator (independent of the test oracle).
+// DCT-II, Section 2.1 Eq. (1)-(2): C[k][m] = a_k cos(pi (2m + 1) k / (2N)),
+// a_0 = sqrt(1/N), a_k = sqrt(2/N); the integer (2m + 1) k is formed first.
+// Haar (Section 2.3 names it; standard orthonormal form): row 0 constant
+// sqrt(1/N); row r >= 1 at scale s = 2^floor(log2 r), shift t = r - s has
+// support [t N/s, (t+1) N/s), value +sqrt(s/N) on its first half and
+// -sqrt(s/N) on its second.  Row 0 of both is the same expression, so the
+// DCT DC atom and the Haar scaling atom are identical bit for bit.
+void make_bases(int b, std::vector<double> &basis) {
+    basis.assign(2 * (size_t)b * b, 0.0);
+    double *C = basis.data(), *H = basis.data() + (size_t)b * b;
+    for (int k = 0; k < b; ++k) {
+        const double ak = k == 0 ? std::sqrt(1.0 / b) : std::sqrt(2.0 / b);
+        for (int m = 0; m < b; ++m) {
+            const long long num = (long long)(2 * m + 1) * k;
+            C[k * b + m] = k == 0 ? ak : ak * std::cos(M_PI * (double)num / (2.0 * b));
+        }
+    }
+    for (int m = 0; m < b; ++m) H[m] = std::sqrt(1.0 / b);
+    for (int r = 1; r < b; ++r) {
+        int scale = 1;                                   // 2^floor(log2 r)
+        while (scale * 2 <= r) scale *= 2;
+        const int t = r - scale;
+        const int len = b / scale;
+        const double v = std::sqrt((double)scale / b);
+        for (int m = t * len; m < t * len + len / 2; ++m) H[r * b + m] = v;
+        for (int m = t * len + len / 2; m < (t + 1) * len; ++m) H[r * b + m] = -v;
+    }
+}
+
+// Compensated dot product (Ogita-Rump-Oishi Dot2): result as accurate as if
+// computed in twice the working precision, then rounded.
+double dot2(const double *x, const double *y, int n) {
+    double s = 0.0, c = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double p = x[i] * y[i];
+        const double pe = std::fma(x[i], y[i], -p);
+        const double t = s + p;
+        const double z = t - s;
+        const double se = (s - (t - z)) + (p - z);
+        s = t;
+        c += se + pe;
+    }
+    return s + c;
+}
+
+// ----------------------------------------------------------- tensor maps
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// 2-D BF16 tensor [rows][cols] (cols contiguous) read in boxes of
+// box_rows x 64 elements with the 128-byte swizzle.
+int encode_bf16_map(CUtensorMap *map, const void *base, unsigned long long rows, unsigned long long cols,
+                    unsigned box_rows) {
+    auto enc = tensor_map_encoder();
+    if (!enc) return fail(AQMP_E_CUDA, "cuTensorMapEncodeTiled is unavailable");
+    cuuint64_t dims[2] = {cols, rows};
+    cuuint64_t strides[1] = {cols * 2};
+    cuuint32_t box[2] = {64, box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box,
+                     estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(AQMP_E_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return AQMP_OK;
+}
+
+// ------------------------------------------------------------ context
+
+struct DeviceBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    ~DeviceBuf() { if (p) cudaFree(p); }
+    int reserve(size_t want) {
+        if (want <= bytes) return AQMP_OK;
+        if (p) { cudaFree(p); p = nullptr; bytes = 0; }
+        want = std::max<size_t>(want, 256);
+        cudaError_t e = cudaMalloc(&p, want);
+        if (e != cudaSuccess) { p = nullptr; return fail(AQMP_E_OOM, "cudaMalloc(%zu): %s", want, cudaGetErrorString(e)); }
+        bytes = want;
+        return AQMP_OK;
+    }
+};
+
+// ------------------------------------------------------ kernel timing
+
+struct Profiler {
+    std::mutex mu;
+    bool on = false;
+    struct Pending { std::string name; cudaEvent_t a, b; };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> pool;
+    std::map<std::string, std::pair<unsigned long long, double>> totals;
+    cudaEvent_t get() {
+        if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    // Events around one launch; `launch` returns the launch's cudaError_t.
+    template <class F>
+    cudaError_t run(const std::string &name, cudaStream_t st, F &&launch) {
+        if (!on) return launch();
+        cudaEvent_t a = get(), b = get();
+        cudaEventRecord(a, st);
+        cudaError_t e = launch();
+        cudaEventRecord(b, st);
+        pending.push_back({name, a, b});
+        return e;
+    }
+    // After the stream has been synchronised.
+    void resolve() {
+        for (auto &p : pending) {
+            float ms = 0.0f;
+            if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+                auto &t = totals[p.name];
+                t.first += 1;
+                t.second += ms;
+            }
+            pool.push_back(p.a);
+            pool.push_back(p.b);
+        }
+        pending.clear();
+    }
+};
+Profiler g_prof;
+
+std::string kname(const char *k, int b) { return std::string(k) + "_b" + std::to_string(b); }
+
+struct Dict {
+    DictDev d{};
+    DeviceBuf limbs, dh, dl, sh, sl, w, basis, basis64;
+    CUtensorMap tmap;
+};
+
+struct Ctx {
+    int device = -1;
+    int num_sms = 0;
+    int cc_major = 0, cc_minor = 0;
+    std::mutex mu;
+    std::map<int, std::unique_ptr<Dict>> dicts;
+    DeviceBuf planes, staging, queues, Y, e0, c0, leaves, atoms, alpha_lo, counters;
+    Counters *host_ctr = nullptr;             // pinned
+};
+
+std::mutex g_ctx_mu;
+std::map<int, std::unique_ptr<Ctx>> g_ctx;
+
+int get_ctx(Ctx **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(AQMP_E_CUDA, "no CUDA device: %s", cudaGetErrorString(e));
+    std::lock_guard<std::mutex> g(g_ctx_mu);
+    auto &slot = g_ctx[dev];
+    if (!slot) {
+        auto c = std::make_unique<Ctx>();
+        c->device = dev;
+        CK(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev));
+        CK(cudaDeviceGetAttribute(&c->cc_major, cudaDevAttrComputeCapabilityMajor, dev));
+        CK(cudaDeviceGetAttribute(&c->cc_minor, cudaDevAttrComputeCapabilityMinor, dev));
+        if (c->cc_major != 10 || c->cc_minor != 3)
+            return fail(AQMP_E_CUDA, "device %d is sm_%d%d; this library is built for sm_103a only", dev,
+                        c->cc_major, c->cc_minor);
+        CK(cudaMallocHost(&c->host_ctr, sizeof(Counters)));
+        slot = std::move(c);
+    }
+    *out = slot.get();
+    return AQMP_OK;
+}
+
+int num_families(int dict_id) { return dict_id == AQMP_DICT_DCT_HAAR ? 2 : 1; }
+
+// Tables of one (side, dictionary), built once per device.
+int get_dict(Ctx *c, int b, int dict_id, cudaStream_t st, Dict **out) {
+    const int key = b * 16 + dict_id;
+    auto it = c->dicts.find(key);
+    if (it != c->dicts.end()) { *out = it->second.get(); return AQMP_OK; }
+    auto D = std::make_unique<Dict>();
+    DictDev &d = D->d;
+    d.b = b;
+    d.n = b * b;
+    d.nf = num_families(dict_id);
+    d.M = d.nf * d.n;
+    d.Mpad = std::max(128, (d.M + 127) / 128 * 128);
+    d.Kpad = std::max(kKBlock, (d.n + kKBlock - 1) / kKBlock * kKBlock);
+    int rc;
+    if ((rc = D->limbs.reserve(sizeof(__nv_bfloat16) * (size_t)kLimbs * d.Mpad * d.Kpad))) return rc;
+    if ((rc = D->dh.reserve(sizeof(int32_t) * (size_t)d.M * d.n))) return rc;
+    if ((rc = D->dl.reserve(sizeof(int32_t) * (size_t)d.M * d.n))) return rc;
+    if ((rc = D->sh.reserve(sizeof(long long) * d.M))) return rc;
+    if ((rc = D->sl.reserve(sizeof(long long) * d.M))) return rc;
+    if ((rc = D->w.reserve(sizeof(float) * 4 * (size_t)b * b))) return rc;
+    if ((rc = D->basis.reserve(sizeof(float) * 2 * (size_t)b * b))) return rc;
+    if ((rc = D->basis64.reserve(sizeof(double) * 2 * (size_t)b * b))) return rc;
+    d.limbs = (__nv_bfloat16 *)D->limbs.p;
+    d.Dh = (int32_t *)D->dh.p;
+    d.Dl = (int32_t *)D->dl.p;
+    d.Sh = (long long *)D->sh.p;
+    d.Sl = (long long *)D->sl.p;
+    d.W = (float2 *)D->w.p;
+    d.WT = d.W + b * b;
+    d.basis = (float *)D->basis.p;
+
+    std::vector<double> basis;
+    make_bases(b, basis);
+    // W = C H^T with exact structural zeros: entries below 2^-40 are the
+    // rounding of an exact zero (e.g. W[p][0] = <C_p, H_0> = 0 for p > 0)
+    std::vector<float> w(4 * (size_t)b * b);      // W then W^T, (hi, lo) interleaved
+    const double *C = basis.data(), *H = basis.data() + (size_t)b * b;
+    for (int p = 0; p < b; ++p)
+        for (int q = 0; q < b; ++q) {
+            double x = dot2(C + (size_t)p * b, H + (size_t)q * b, b);
+            if (std::fabs(x) < 0x1p-40) x = 0.0;
+            else if (std::fabs(x) < 1e-7)
+                return fail(AQMP_E_DICT, "cross-Gram entry W[%d][%d] = %g is neither zero nor well separated", p, q, x);
+            const float hi = (float)x, lo = (float)(x - (double)hi);
+            w[2 * ((size_t)p * b + q)] = hi;                         // W[p][q]
+            w[2 * ((size_t)p * b + q) + 1] = lo;
+            w[2 * ((size_t)b * b + (size_t)q * b + p)] = hi;         // W^T[q][p]
+            w[2 * ((size_t)b * b + (size_t)q * b + p) + 1] = lo;
+        }
+    CK(cudaMemcpyAsync(D->w.p, w.data(), sizeof(float) * w.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(D->basis64.p, basis.data(), sizeof(double) * basis.size(), cudaMemcpyHostToDevice, st));
+    const int fam0 = dict_id == AQMP_DICT_HAAR ? 1 : 0;
+    CK(build_fixed_tables_fam(d, (const double *)D->basis64.p, fam0, st));
+    if (dict_id == AQMP_DICT_HAAR) {
+        // single Haar family: decoder table slot 0 must hold the Haar basis
+        CK(cudaMemcpyAsync(d.basis, (const float *)D->basis.p + b * b, sizeof(float) * b * b,
+                           cudaMemcpyDeviceToDevice, st));
+    }
+    if ((rc = encode_bf16_map(&D->tmap, d.limbs, (unsigned long long)kLimbs * d.Mpad, d.Kpad, 128))) return rc;
+    d.tmap_limbs = &D->tmap;
+    CK(cudaStreamSynchronize(st));
+    *out = D.get();
+    c->dicts[key] = std::move(D);
+    return AQMP_OK;
+}
+
+int check_params(const aqmp_params *p) {
+    if (!p) return fail(AQMP_E_ARG, "params is NULL");
+    if (!(p->rmse_tol >= 0.0f)) return fail(AQMP_E_ARG, "rmse_tol must be >= 0");
+    if (p->cap_num < 0 || p->cap_den <= 0 || (long long)p->cap_num > (long long)p->cap_den)
+        return fail(AQMP_E_ARG, "sparsity cap must satisfy 0 <= cap_num <= cap_den, cap_den > 0");
+    if (!is_pow2(p->min_block) || !is_pow2(p->max_block) || p->min_block < 4 || p->max_block < p->min_block)
+        return fail(AQMP_E_ARG, "block sizes must be powers of two with 4 <= min_block <= max_block");
+    if (p->max_block > kMaxSide) return fail(AQMP_E_UNSUPPORTED, "max_block above %d is not built", kMaxSide);
+    if (p->dict_id < 0 || p->dict_id > 2) return fail(AQMP_E_DICT, "unknown dictionary id %d", p->dict_id);
+    if (p->precision != AQMP_PREC_EXACT) return fail(AQMP_E_UNSUPPORTED, "unknown precision %d", p->precision);
+    return AQMP_OK;
+}
+
+}  // namespace
+
+// ===================================================================== ABI
+
+struct aqmp_code {
+    int device = 0;
+    int dict_id = 0, min_block = 4, max_block = 64;
+    std::vector<std::pair<int, int>> shapes;
+    LeafRec *leaves = nullptr;
+    AtomRec *atoms = nullptr;
+    float *alpha_lo = nullptr;
+    unsigned long long n_leaves = 0, n_atoms = 0;
+    aqmp_stats stats{};
+    ~aqmp_code() {
+        if (leaves) cudaFree(leaves);
+        if (atoms) cudaFree(atoms);
+        if (alpha_lo) cudaFree(alpha_lo);
+    }
+};
+
+extern "C" {
+
+const char *aqmp_last_error(void) { return g_last_error.c_str(); }
+const char *aqmp_version(void) { return "aqmp-gb300 0.1 (sm_103a)"; }
+
+void aqmp_params_default(aqmp_params *p) {
+    if (!p) return;
+    p->rmse_tol = 2.0f;
+    p->cap_num = 1;
+    p->cap_den = 4;
+    p->min_block = 4;
+    p->max_block = 64;
+    p->dict_id = AQMP_DICT_DCT_HAAR;
+    p->precision = AQMP_PREC_EXACT;
+    p->flags = 0;
+}
+
+int aqmp_num_atoms(int b, int dict_id) {
+    if (!is_pow2(b) || dict_id < 0 || dict_id > 2) return AQMP_E_ARG;
+    return num_families(dict_id) * b * b;
+}
+
+int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int n_planes, void *stream,
+                       aqmp_code **out) {
+    g_last_error.clear();
+    if (!out) return fail(AQMP_E_ARG, "out is NULL");
+    *out = nullptr;
+    int rc = check_params(params);
+    if (rc) return rc;
+    if (!planes || n_planes <= 0) return fail(AQMP_E_ARG, "no planes");
+    const aqmp_params P = *params;
+    const bool dev_in = (P.flags & AQMP_FLAG_INPUT_DEVICE) != 0;
+    const bool simt = (P.flags & AQMP_FLAG_SIMT_GEMM) != 0;
+    unsigned long long npix = 0, roots = 0, staged = 0;
+    for (int i = 0; i < n_planes; ++i) {
+        const aqmp_plane &pl = planes[i];
+        if (!pl.pixels || pl.height <= 0 || pl.width <= 0 || pl.pitch < pl.width)
+            return fail(AQMP_E_ARG, "plane %d: bad pointer or shape", i);
+        if (pl.height % P.max_block || pl.width % P.max_block)
+            return fail(AQMP_E_SHAPE, "plane %d: %dx%d is not a multiple of max_block %d", i, pl.height,
+                        pl.width, P.max_block);
+        const float tol = pl.rmse_tol < 0.0f ? P.rmse_tol : pl.rmse_tol;
+        if (!(tol >= 0.0f)) return fail(AQMP_E_ARG, "plane %d: bad tolerance", i);
+        npix += (unsigned long long)pl.height * pl.width;
+        roots += (unsigned long long)(pl.height / P.max_block) * (pl.width / P.max_block);
+        staged += (unsigned long long)pl.height * pl.width;
+    }
+    if (npix / ((unsigned long long)P.min_block * P.min_block) > 0xffffffffull / 8)
+        return fail(AQMP_E_UNSUPPORTED, "batch too large for 32-bit queues");
+
+    Ctx *c;
+    if ((rc = get_ctx(&c))) return rc;
+    std::lock_guard<std::mutex> lock(c->mu);
+    cudaStream_t st = (cudaStream_t)stream;
+
+    const int nlev = ilog2(P.max_block) - ilog2(P.min_block) + 1;
+    std::vector<Dict *> dicts(nlev);
+    for (int l = 0; l < nlev; ++l)
+        if ((rc = get_dict(c, P.max_block >> l, P.dict_id, st, &dicts[l]))) return rc;
+
+    // capacities
+    std::vector<unsigned long long> cap(nlev), qoff(nlev + 1, 0);
+    unsigned long long ymax = 0, cmax = 0, emax = 0;
+    for (int l = 0; l < nlev; ++l) {
+        const int b = P.max_block >> l;
+        cap[l] = npix / ((unsigned long long)b * b);
+        qoff[l + 1] = qoff[l] + cap[l];
+        ymax = std::max(ymax, cap[l] * dicts[l]->d.Kpad);
+        cmax = std::max(cmax, cap[l] * dicts[l]->d.M);
+        emax = std::max(emax, cap[l]);
+    }
+    const unsigned long long leaf_cap = cap[nlev - 1];
+    const unsigned long long atom_cap =
+        (npix * (unsigned long long)P.cap_num + P.cap_den - 1) / P.cap_den + leaf_cap;
+
+    if ((rc = c->planes.reserve(sizeof(PlaneDesc) * n_planes))) return rc;
+    if (!dev_in && (rc = c->staging.reserve(staged))) return rc;
+    if ((rc = c->queues.reserve(sizeof(QueueEntry) * qoff[nlev]))) return rc;
+    if ((rc = c->Y.reserve(sizeof(__nv_bfloat16) * ymax))) return rc;
+    if ((rc = c->e0.reserve(sizeof(uint32_t) * emax))) return rc;
+    if ((rc = c->c0.reserve(sizeof(float2) * cmax))) return rc;
+    if ((rc = c->leaves.reserve(sizeof(LeafRec) * leaf_cap))) return rc;
+    if ((rc = c->atoms.reserve(sizeof(AtomRec) * atom_cap))) return rc;
+    if ((rc = c->alpha_lo.reserve(sizeof(float) * atom_cap))) return rc;
+    if ((rc = c->counters.reserve(sizeof(Counters)))) return rc;
+
+    // plane descriptors (and host pixels copied in)
+    std::vector<PlaneDesc> pd(n_planes);
+    unsigned long long soff = 0, roff = 0;
+    for (int i = 0; i < n_planes; ++i) {
+        const aqmp_plane &pl = planes[i];
+        PlaneDesc &d = pd[i];
+        if (dev_in) {
+            d.pix = pl.pixels;
+            d.pitch = pl.pitch;
+        } else {
+            uint8_t *dst = (uint8_t *)c->staging.p + soff;
+            CK(cudaMemcpy2DAsync(dst, pl.width, pl.pixels, pl.pitch, pl.width, pl.height, cudaMemcpyHostToDevice, st));
+            d.pix = dst;
+            d.pitch = pl.width;
+            soff += (unsigned long long)pl.height * pl.width;
+        }
+        d.h = pl.height;
+        d.w = pl.width;
+        d.tol = pl.rmse_tol < 0.0f ? P.rmse_tol : pl.rmse_tol;
+        d.root_off = (unsigned)roff;
+        d.roots_x = (unsigned)(pl.width / P.max_block);
+        d.pad = 0;
+        roff += (unsigned long long)(pl.height / P.max_block) * (pl.width / P.max_block);
+    }
+    CK(cudaMemcpyAsync(c->planes.p, pd.data(), sizeof(PlaneDesc) * n_planes, cudaMemcpyHostToDevice, st));
+    Counters *ctr = (Counters *)c->counters.p;
+    CK(cudaMemsetAsync(ctr, 0, sizeof(Counters), st));
+    QueueEntry *q = (QueueEntry *)c->queues.p;
+    CK(launch_seed_roots((const PlaneDesc *)c->planes.p, n_planes, P.max_block, (unsigned)roots, q,
+                         &ctr->queue_count[0], st));
+
+    std::vector<CUtensorMap> ymaps(nlev);
+    for (int l = 0; l < nlev; ++l) {
+        const int b = P.max_block >> l;
+        const DictDev &d = dicts[l]->d;
+        LevelArgs lv{};
+        lv.b = b;
+        lv.n = d.n;
+        lv.M = d.M;
+        lv.Mpad = d.Mpad;
+        lv.Kpad = d.Kpad;
+        lv.k = (int)std::max<long long>(1, (long long)d.n * P.cap_num / P.cap_den);
+        lv.level = l;
+        lv.is_last = (l == nlev - 1);
+        lv.queue = q + qoff[l];
+        lv.count = &ctr->queue_count[l];
+        lv.capacity = (unsigned)cap[l];
+        lv.next_queue = lv.is_last ? nullptr : q + qoff[l + 1];
+        lv.next_count = &ctr->queue_count[l + 1];
+        lv.next_capacity = lv.is_last ? 0u : (unsigned)cap[l + 1];
+
+        GatherArgs ga{b, d.n, d.Kpad, lv.queue, lv.count, lv.capacity, (const PlaneDesc *)c->planes.p,
+                      (__nv_bfloat16 *)c->Y.p, (uint32_t *)c->e0.p};
+        CK(g_prof.run(kname("gather", b), st, [&] { return launch_gather(ga, c->num_sms, st); }));
+
+        CorrArgs ca{};
+        ca.d = &d;
+        ca.Y = (const __nv_bfloat16 *)c->Y.p;
+        ca.count = lv.count;
+        ca.fixed_count = 0;
+        ca.capacity = lv.capacity;
+        ca.c0 = (float2 *)c->c0.p;
+        ca.ctr = ctr;
+        if (simt) {
+            CK(g_prof.run(kname("corr_simt", b), st, [&] { return launch_corr_simt(ca, st); }));
+        } else {
+            if ((rc = encode_bf16_map(&ymaps[l], c->Y.p, cap[l], d.Kpad, 64))) return rc;
+            ca.tmap_Y = &ymaps[l];
+            CK(g_prof.run(kname("corr_tc", b), st, [&] { return launch_corr_tc(ca, st); }));
+        }
+
+        MPArgs ma{};
+        ma.lv = lv;
+        ma.c0 = (const float2 *)c->c0.p;
+        ma.e0 = (const uint32_t *)c->e0.p;
+        ma.planes = (const PlaneDesc *)c->planes.p;
+        ma.W = d.W;
+        ma.WT = d.WT;
+        ma.leaves = (LeafRec *)c->leaves.p;
+        ma.leaf_cap = leaf_cap;
+        ma.atoms = (AtomRec *)c->atoms.p;
+        ma.alpha_lo = (float *)c->alpha_lo.p;
+        ma.atom_cap = atom_cap;
+        ma.ctr = ctr;
+        CK(g_prof.run(kname("mp", b), st, [&] { return launch_mp(ma, d.nf, c->num_sms, st); }));
+    }
+    CK(cudaMemcpyAsync(c->host_ctr, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    {
+        std::lock_guard<std::mutex> pl(g_prof.mu);
+        g_prof.resolve();
+    }
+    const Counters &h = *c->host_ctr;
+    if (h.error == kDevErrQueueOverflow) return fail(AQMP_E_QUEUE_OVERFLOW, "device queue overflow (site %u)", h.error_info);
+    if (h.error == kDevErrTimeout) return fail(AQMP_E_TIMEOUT, "device wait timed out (site %u)", h.error_info);
+    if (h.error) return fail(AQMP_E_CUDA, "device error %u (%u)", h.error, h.error_info);
+
+    auto code = std::make_unique<aqmp_code>();
+    code->device = c->device;
+    code->dict_id = P.dict_id;
+    code->min_block = P.min_block;
+    code->max_block = P.max_block;
+    for (int i = 0; i < n_planes; ++i) code->shapes.emplace_back(planes[i].height, planes[i].width);
+    code->n_leaves = h.n_leaves;
+    code->n_atoms = h.n_atoms;
+    CK(cudaMalloc(&code->leaves, sizeof(LeafRec) * std::max<unsigned long long>(1, h.n_leaves)));
+    CK(cudaMalloc(&code->atoms, sizeof(AtomRec) * std::max<unsigned long long>(1, h.n_atoms)));
+    CK(cudaMalloc(&code->alpha_lo, sizeof(float) * std::max<unsigned long long>(1, h.n_atoms)));
+    if (h.n_leaves)
+        CK(cudaMemcpyAsync(code->leaves, c->leaves.p, sizeof(LeafRec) * h.n_leaves, cudaMemcpyDeviceToDevice, st));
+    if (h.n_atoms) {
+        CK(cudaMemcpyAsync(code->atoms, c->atoms.p, sizeof(AtomRec) * h.n_atoms, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(code->alpha_lo, c->alpha_lo.p, sizeof(float) * h.n_atoms, cudaMemcpyDeviceToDevice, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    aqmp_stats &s = code->stats;
+    s.n_leaves = h.n_leaves;
+    s.n_atoms = h.n_atoms;
+    s.near_tie_leaves = h.near_tie_leaves;
+    for (int l = 0; l < nlev && l < 8; ++l) {
+        s.attempts_per_level[l] = h.attempts[l];
+        s.iterations_per_level[l] = h.iterations[l];
+        s.attempts += h.attempts[l];
+        s.atom_iterations += h.iterations[l];
+    }
+    *out = code.release();
+    return AQMP_OK;
+}
+
+int aqmp_encode(const aqmp_params *params, const uint8_t *pixels, int channels, int h, int w, size_t pitch,
+                void *stream, aqmp_code **out) {
+    if (!pixels || channels <= 0) return fail(AQMP_E_ARG, "no pixels");
+    std::vector<aqmp_plane> pl(channels);
+    for (int c = 0; c < channels; ++c) {
+        pl[c].pixels = pixels + (size_t)c * h * pitch;
+        pl[c].height = h;
+        pl[c].width = w;
+        pl[c].pitch = (int64_t)pitch;
+        pl[c].rmse_tol = -1.0f;
+    }
+    return aqmp_encode_planes(params, pl.data(), channels, stream, out);
+}
+
+int aqmp_code_stats(const aqmp_code *code, aqmp_stats *stats) {
+    if (!code || !stats) return fail(AQMP_E_ARG, "NULL argument");
+    *stats = code->stats;
+    return AQMP_OK;
+}
+
+int aqmp_code_copy(const aqmp_code *code, aqmp_leaf *leaves, aqmp_atom *atoms, float *alpha_lo) {
+    if (!code || (!leaves && code->n_leaves) || (!atoms && code->n_atoms)) return fail(AQMP_E_ARG, "NULL argument");
+    std::vector<LeafRec> L(code->n_leaves);
+    std::vector<AtomRec> A(code->n_atoms);
+    std::vector<float> lo(code->n_atoms);
+    if (code->n_leaves) CK(cudaMemcpy(L.data(), code->leaves, sizeof(LeafRec) * L.size(), cudaMemcpyDeviceToHost));
+    if (code->n_atoms) {
+        CK(cudaMemcpy(A.data(), code->atoms, sizeof(AtomRec) * A.size(), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(lo.data(), code->alpha_lo, sizeof(float) * lo.size(), cudaMemcpyDeviceToHost));
+    }
+    // canonical order: plane, root (row-major), then depth-first TL, TR, BL, BR
+    // = Z-order of the leaf's corner inside its root
+    const unsigned mb = (unsigned)code->max_block, nb = (unsigned)code->min_block;
+    auto key = [&](const LeafRec &r) {
+        const unsigned long long rx = code->shapes[r.plane].second / mb;
+        const unsigned long long root = (r.y / mb) * rx + (r.x / mb);
+        const unsigned cy = (r.y % mb) / nb, cx = (r.x % mb) / nb;
+        unsigned long long z = 0;
+        for (int bit = 15; bit >= 0; --bit) z = (z << 2) | (((cy >> bit) & 1u) << 1) | ((cx >> bit) & 1u);
+        return std::make_tuple((unsigned long long)r.plane, root, z);
+    };
+    std::vector<size_t> order(L.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::sort(order.begin(), order.end(), [&](size_t a, size_t b) { return key(L[a]) < key(L[b]); });
+    unsigned long long off = 0;
+    for (size_t i = 0; i < order.size(); ++i) {
+        LeafRec r = L[order[i]];
+        for (unsigned t = 0; t < r.n_atoms; ++t) {
+            atoms[off + t].j = A[r.atom_off + t].j;
+            atoms[off + t].alpha = A[r.atom_off + t].alpha;
+            if (alpha_lo) alpha_lo[off + t] = lo[r.atom_off + t];
+        }
+        r.atom_off = (uint32_t)off;
+        off += r.n_atoms;
+        std::memcpy(&leaves[i], &r, sizeof r);
+    }
+    return AQMP_OK;
+}
+
+int aqmp_decode(const aqmp_code *code, int plane, float *out, int64_t out_pitch, int out_is_device, void *stream) {
+    g_last_error.clear();
+    if (!code || !out || plane < 0 || plane >= (int)code->shapes.size()) return fail(AQMP_E_ARG, "bad argument");
+    const int h = code->shapes[plane].first, w = code->shapes[plane].second;
+    if (out_pitch < w) return fail(AQMP_E_ARG, "out_pitch below width");
+    Ctx *c;
+    int rc;
+    if ((rc = get_ctx(&c))) return rc;
+    std::lock_guard<std::mutex> lock(c->mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    DecodeArgs a{};
+    a.leaves = code->leaves;
+    a.n_leaves = code->n_leaves;
+    a.atoms = code->atoms;
+    a.plane = (uint32_t)plane;
+    a.nf = num_families(code->dict_id);
+    a.single_family = 0;
+    for (int b = code->min_block; b <= code->max_block; b *= 2) {
+        Dict *d;
+        if ((rc = get_dict(c, b, code->dict_id, st, &d))) return rc;
+        a.basis[ilog2(b)] = d->d.basis;
+    }
+    float *dst = out;
+    long long pitch = out_pitch;
+    void *tmp = nullptr;
+    if (!out_is_device) {
+        CK(cudaMalloc(&tmp, sizeof(float) * (size_t)h * w));
+        dst = (float *)tmp;
+        pitch = w;
+    }
+    a.out = dst;
+    a.out_pitch = pitch;
+    cudaError_t e = g_prof.run(kname("decode", code->max_block), st, [&] { return launch_decode(a, c->num_sms, st); });
+    if (e == cudaSuccess && !out_is_device)
+        e = cudaMemcpy2DAsync(out, sizeof(float) * out_pitch, dst, sizeof(float) * w, sizeof(float) * w, h,
+                              cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) {
+        std::lock_guard<std::mutex> pl(g_prof.mu);
+        g_prof.resolve();
+    }
+    if (tmp) cudaFree(tmp);
+    if (e != cudaSuccess) return fail(AQMP_E_CUDA, "decode: %s", cudaGetErrorString(e));
+    return AQMP_OK;
+}
+
+void aqmp_code_free(aqmp_code *code) { delete code; }
+
+int aqmp_profile_enable(int on) {
+    std::lock_guard<std::mutex> g(g_prof.mu);
+    const int prev = g_prof.on ? 1 : 0;
+    g_prof.on = on != 0;
+    return prev;
+}
+
+void aqmp_profile_reset(void) {
+    std::lock_guard<std::mutex> g(g_prof.mu);
+    g_prof.totals.clear();
+}
+
+int aqmp_profile_read(aqmp_kernel_time *out, int max, int *n) {
+    if (!n || (max > 0 && !out)) return fail(AQMP_E_ARG, "NULL argument");
+    std::lock_guard<std::mutex> g(g_prof.mu);
+    int i = 0;
+    for (auto &kv : g_prof.totals) {
+        if (i < max) {
+            std::memset(&out[i], 0, sizeof(aqmp_kernel_time));
+            std::strncpy(out[i].name, kv.first.c_str(), sizeof(out[i].name) - 1);
+            out[i].launches = kv.second.first;
+            out[i].total_ms = kv.second.second;
+        }
+        ++i;
+    }
+    *n = std::min(i, std::max(max, 0));
+    return AQMP_OK;
+}
+
+int aqmp_correlate(int b, int dict_id, const uint8_t *blocks, int64_t L, float *corr, int gemm, void *stream) {
+    g_last_error.clear();
+    if (!is_pow2(b) || b < 4 || b > kMaxSide) return fail(AQMP_E_ARG, "side must be a power of two in [4, %d]", kMaxSide);
+    if (dict_id < 0 || dict_id > 2) return fail(AQMP_E_DICT, "unknown dictionary id %d", dict_id);
+    if (L < 0 || (L > 0 && (!blocks || !corr))) return fail(AQMP_E_ARG, "bad pointers");
+    if (L == 0) return AQMP_OK;
+    if (L > 0x7fffffffLL) return fail(AQMP_E_UNSUPPORTED, "too many blocks");
+    Ctx *c;
+    int rc;
+    if ((rc = get_ctx(&c))) return rc;
+    std::lock_guard<std::mutex> lock(c->mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    Dict *D;
+    if ((rc = get_dict(c, b, dict_id, st, &D))) return rc;
+    const DictDev &d = D->d;
+    if ((rc = c->Y.reserve(sizeof(__nv_bfloat16) * (size_t)L * d.Kpad))) return rc;
+    CK(launch_gather_blocks(b, d.Kpad, blocks, L, (__nv_bfloat16 *)c->Y.p, nullptr, c->num_sms, st));
+    CorrArgs ca{};
+    ca.d = &d;
+    ca.Y = (const __nv_bfloat16 *)c->Y.p;
+    ca.count = nullptr;
+    ca.fixed_count = L;
+    ca.capacity = (unsigned)L;
+    ca.c0 = (float2 *)corr;
+    CUtensorMap ym;
+    if (gemm == 0) {
+        if ((rc = encode_bf16_map(&ym, c->Y.p, (unsigned long long)L, d.Kpad, 64))) return rc;
+        ca.tmap_Y = &ym;
+        CK(g_prof.run(kname("corr_tc", b), st, [&] { return launch_corr_tc(ca, st); }));
+    } else {
+        CK(g_prof.run(kname("corr_simt", b), st, [&] { return launch_corr_simt(ca, st); }));
+    }
+    CK(cudaStreamSynchronize(st));
+    {
+        std::lock_guard<std::mutex> pl(g_prof.mu);
+        g_prof.resolve();
+    }
+    return AQMP_OK;
+}
+
+}  // extern "C"

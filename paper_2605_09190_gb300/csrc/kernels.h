@@ -1,0 +1,94 @@
+// kernels.h -- argument blocks and launchers of the AQMP device kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+
+namespace aqmp {
+
+// Pursuit of one level (mp.cu).
+struct MPArgs {
+    LevelArgs lv;
+    const float2 *c0;            // [capacity][M] initial correlations (hi, lo)
+    const uint32_t *e0;          // [capacity] sum of squared pixels of each block
+    const PlaneDesc *planes;
+    const float2 *W;             // W = C H^T, b x b row-major, (hi, lo) pairs
+    const float2 *WT;            // its transpose
+    LeafRec *leaves;
+    unsigned long long leaf_cap;
+    AtomRec *atoms;
+    float *alpha_lo;
+    unsigned long long atom_cap;
+    Counters *ctr;
+};
+cudaError_t launch_mp(const MPArgs &a, int nf, int num_sms, cudaStream_t st);
+
+// Block gather (gather.cu): queue entries -> centred BF16 leaf vectors
+// (column-major unravel, zero padded to Kpad) and sums of squares.
+struct GatherArgs {
+    int b, n, Kpad;
+    const QueueEntry *queue;
+    const unsigned *count;
+    unsigned capacity;
+    const PlaneDesc *planes;
+    __nv_bfloat16 *Y;            // [capacity][Kpad]
+    uint32_t *e0;                // [capacity]
+};
+cudaError_t launch_gather(const GatherArgs &a, int num_sms, cudaStream_t st);
+
+// Same, for L contiguous row-major b x b blocks (aqmp_correlate).
+cudaError_t launch_gather_blocks(int b, int Kpad, const uint8_t *blocks, long long L,
+                                 __nv_bfloat16 *Y, uint32_t *e0, int num_sms, cudaStream_t st);
+
+// Fixed-point dictionary tables of one side (tables.cu).
+struct DictDev {
+    int b, n, M, Mpad, Kpad, nf;
+    __nv_bfloat16 *limbs;        // [kLimbs][Mpad][Kpad] balanced base-64 digits
+    int32_t *Dh, *Dl;            // [M][n]: D_fix = Dh 2^24 + Dl, Dl in [-2^23, 2^23)
+    long long *Sh, *Sl;          // per atom: sum_v D_fix = Sh 2^24 + Sl (canonical)
+    float2 *W, *WT;              // b x b (hi, lo)
+    float *basis;                // [2][b][b] FP32 1-D bases (DCT, Haar) for decoding
+    void *tmap_limbs;            // CUtensorMap for the tensor-core kernel (host copy)
+};
+
+// Initial correlation (corr_simt.cu / corr_tc.cu): c0[l][j] for l < *count.
+struct CorrArgs {
+    const DictDev *d;            // host pointer to the table descriptor
+    const __nv_bfloat16 *Y;      // [capacity][Kpad]
+    const unsigned *count;       // device count (NULL: use `fixed_count`)
+    long long fixed_count;
+    unsigned capacity;
+    float2 *c0;                  // [capacity][M]
+    Counters *ctr;               // may be NULL
+    const void *tmap_Y;          // CUtensorMap of Y (tensor-core kernel only)
+};
+cudaError_t launch_corr_simt(const CorrArgs &a, cudaStream_t st);
+cudaError_t launch_corr_tc(const CorrArgs &a, cudaStream_t st);
+bool corr_tc_available();
+
+// Decoder (decode.cu): one plane's leaves -> float image.
+struct DecodeArgs {
+    const LeafRec *leaves;
+    unsigned long long n_leaves;
+    const AtomRec *atoms;
+    uint32_t plane;
+    float *out;
+    long long out_pitch;
+    const float *basis[8];       // per level log2(b): [2][b][b] FP32 bases
+    int nf;                      // 2: DCT+Haar, 1: single family
+    int single_family;           // 0: DCT, 1: Haar (when nf == 1)
+};
+cudaError_t launch_decode(const DecodeArgs &a, int num_sms, cudaStream_t st);
+
+// Level-0 queue from the plane descriptors (gather.cu).
+cudaError_t launch_seed_roots(const PlaneDesc *planes, int n_planes, int max_block,
+                              unsigned total_roots, QueueEntry *queue, unsigned *count,
+                              cudaStream_t st);
+
+// Table construction on the device (tables.cu) from the FP64 1-D bases
+// basis_dev = [2][b][b] (DCT, Haar); fam0 selects the family of a
+// single-family dictionary (0 = DCT, 1 = Haar).
+cudaError_t build_fixed_tables_fam(DictDev &d, const double *basis_dev, int fam0, cudaStream_t st);
+
+}  // namespace aqmp

@@ -1,0 +1,94 @@
+// tables.cu -- fixed-point dictionary tables built on the device from the
+// FP64 1-D bases.
+//
+// Atom j of a family with 1-D matrix B is the 2-D atom (p, q) = (f mod b,
+// f div b), f = j - family * b^2, and its entry at v = m b + i is
+// B[p][i] B[q][m] (Section 2.1: outer products of 1-D rows; Appendix A:
+// columns concatenated).  Each entry is put in fixed point,
+// D_fix = round(D 2^48), and stored three ways: as 8 balanced base-64 BF16
+// digits for the tensor cores, as a (Dh, Dl) pair for the SIMT kernel, and
+// through its per-atom sum for the centring correction.
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace aqmp {
+
+__device__ __forceinline__ long long fixed_entry(const double *basis, int b, int n, int nf, int fam0,
+                                                 int j, int v) {
+    const int fam = nf == 2 ? j / n : fam0;
+    const int f = j - (nf == 2 ? (j / n) * n : 0);
+    const int p = f % b, q = f / b;
+    const int m = v / b, i = v - m * b;
+    const double *B = basis + (size_t)fam * b * b;
+    const double d = B[p * b + i] * B[q * b + m];
+    return __double2ll_rn(d * 281474976710656.0);      // exact scaling by 2^48, then round
+}
+
+__global__ void fixed_tables_kernel(int b, int n, int M, int nf, int fam0, const double *basis,
+                                    int Mpad, int Kpad, __nv_bfloat16 *limbs, int32_t *Dh,
+                                    int32_t *Dl) {
+    const long long total = (long long)M * n;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(idx / n), v = (int)(idx - (long long)j * n);
+        const long long x = fixed_entry(basis, b, n, nf, fam0, j, v);
+        const long long h = (x + (1ll << 23)) >> 24;
+        Dh[idx] = (int32_t)h;
+        Dl[idx] = (int32_t)(x - h * (1ll << 24));
+        long long r = x;
+#pragma unroll
+        for (int s = kLimbs - 1; s >= 1; --s) {
+            const long long dg = ((r + 32) & 63) - 32;          // balanced digit in [-32, 31]
+            limbs[((size_t)s * Mpad + j) * Kpad + v] = __float2bfloat16_rn((float)dg);
+            r = (r - dg) >> kDigitBits;
+        }
+        limbs[(size_t)j * Kpad + v] = __float2bfloat16_rn((float)r);   // top digit, |r| <= 32
+    }
+}
+
+// One warp per atom: S_j = sum_v D_fix[j][v], split canonically.
+__global__ void fixed_sums_kernel(int b, int n, int M, int nf, int fam0, const double *basis,
+                                  long long *Sh, long long *Sl) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < M; j += warps) {
+        long long s = 0;
+        for (int v = lane; v < n; v += 32) s += fixed_entry(basis, b, n, nf, fam0, j, v);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (lane == 0) {
+            const long long h = (s + (1ll << 23)) >> 24;
+            Sh[j] = h;
+            Sl[j] = s - h * (1ll << 24);
+        }
+    }
+}
+
+__global__ void basis_to_float_kernel(const double *basis, float *out, int count) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
+        out[i] = (float)basis[i];
+}
+
+// Host entry used by the library: fam0 = family of a single-family
+// dictionary (0 = DCT, 1 = Haar); ignored when nf == 2.
+cudaError_t build_fixed_tables_fam(DictDev &d, const double *basis_dev, int fam0, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(d.limbs, 0, sizeof(__nv_bfloat16) * (size_t)kLimbs * d.Mpad * d.Kpad, st);
+    if (e != cudaSuccess) return e;
+    const long long total = (long long)d.M * d.n;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 8192) blocks = 8192;
+    fixed_tables_kernel<<<blocks, 256, 0, st>>>(d.b, d.n, d.M, d.nf, fam0, basis_dev, d.Mpad, d.Kpad,
+                                                d.limbs, d.Dh, d.Dl);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    int sblocks = (d.M + 7) / 8;
+    if (sblocks > 4096) sblocks = 4096;
+    fixed_sums_kernel<<<sblocks, 256, 0, st>>>(d.b, d.n, d.M, d.nf, fam0, basis_dev, d.Sh, d.Sl);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    basis_to_float_kernel<<<(2 * d.b * d.b + 255) / 256, 256, 0, st>>>(basis_dev, d.basis, 2 * d.b * d.b);
+    return cudaGetLastError();
+}
+
+}  // namespace aqmp

@@ -1,0 +1,49 @@
+"""a2 on the GPU: the tcgen05 exact-limb correlation against the integer
+SIMT kernel (bit for bit) and against the FP64 oracle's D^T y."""
+import numpy as np
+import pytest
+
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2605_09190_gb300 import aqmp, build_lib
+    build_lib.build()
+    aqmp.load_library()
+    assert torch.cuda.is_available()
+    return aqmp
+
+
+def _blocks(L, b, seed):
+    rng = np.random.default_rng(seed)
+    x = rng.integers(0, 256, size=(L, b, b), dtype=np.uint8)
+    if L > 3:
+        x[0] = 0
+        x[1] = 255
+        x[2] = np.where(np.arange(b)[None, :] < b // 2, 255, 0)
+    return x
+
+
+@pytest.mark.parametrize("b,dict_id,L", [(4, 0, 1), (4, 0, 200), (8, 0, 65), (8, 1, 64), (16, 0, 130),
+                                         (16, 2, 7), (32, 0, 70), (64, 0, 66), (64, 1, 3)])
+def test_tensor_core_matches_simt_and_fp64(lib, b, dict_id, L):
+    host = _blocks(L, b, seed=b * 100 + L + dict_id)
+    dev = torch.from_numpy(host).cuda()
+    tc = lib.aqmp_correlate(b, dict_id, dev, gemm=0)
+    simt = lib.aqmp_correlate(b, dict_id, dev, gemm=1)
+    torch.cuda.synchronize()
+    tc_h, simt_h = tc.cpu().numpy(), simt.cpu().numpy()
+    # both kernels round the same exact integer once: identical bits
+    assert np.array_equal(tc_h.view(np.uint32), simt_h.view(np.uint32))
+    D = oracle.dictionary(b, dict_id)
+    for l in range(L):
+        y = oracle.unravel(host[l])
+        ref = D @ y
+        got = tc_h[l, :, 0].astype(np.float64) + tc_h[l, :, 1].astype(np.float64)
+        # fixed-point dictionary: |err| <= 2^-49 sum|y| + rounding of the result
+        bound = 2.0 ** -47 * np.sum(np.abs(y)) + 2.0 ** -46 * np.abs(ref) + 1e-12
+        assert np.all(np.abs(got - ref) <= bound), (l, np.max(np.abs(got - ref) - bound))

@@ -21,11 +21,16 @@ MUTANTS = [
     ("dct_half_sample", "(m + 0.5) * k", "(m + 1.0) * k"),
     ("haar_sign", "+ len / 2; ++m) H[row * b + m] = v;", "+ len / 2; ++m) H[row * b + m] = -v;"),
     ("residual_sign", "r[v] -= alpha * pb[v];", "r[v] += alpha * pb[v];"),
-    ("argmax_no_abs", "if (fabs(c[j]) > fabs(c[best])) best = j;", "if (c[j] > c[best]) best = j;"),
-    ("tie_highest", "if (fabs(c[j]) > fabs(c[best])) best = j;", "if (fabs(c[j]) >= fabs(c[best])) best = j;"),
-    ("stop_not_strict", "if (E < eps2) { *converged = 1; break; }", "if (E <= eps2) { *converged = 1; break; }"),
-    ("stop_after_budget_check", "if (E < eps2) { *converged = 1; break; }\n        if (t == k) break;",
-     "if (t == k) break;\n        if (E < eps2) { *converged = 1; break; }"),
+    ("argmax_no_abs", "if (fabs(c[j]) > cmax) cmax = fabs(c[j]);", "if (c[j] > cmax) cmax = c[j];"),
+    ("tie_highest", "int best = 0;\n        while (fabs(c[best]) < edge) ++best;",
+     "int best = M - 1;\n        while (fabs(c[best]) < edge) --best;"),
+    ("tie_band_dropped", "const double edge = cmax - tie_c;", "const double edge = cmax;"),
+    ("stop_band_dropped", "if (E < eps2 - tie_e) { *converged = 1; break; }",
+     "if (E < eps2) { *converged = 1; break; }"),
+    ("stop_band_sign", "if (E < eps2 - tie_e) { *converged = 1; break; }",
+     "if (E < eps2 + tie_e) { *converged = 1; break; }"),
+    ("stop_after_budget_check", "if (E < eps2 - tie_e) { *converged = 1; break; }\n        if (t == k) break;",
+     "if (t == k) break;\n        if (E < eps2 - tie_e) { *converged = 1; break; }"),
     ("budget_off_by_one", "if (t == k) break;", "if (t == k + 1) break;"),
     ("child_order", "rec(c, y0, x0 + h, h);\n        rec(c, y0 + h, x0, h);",
      "rec(c, y0 + h, x0, h);\n        rec(c, y0, x0 + h, h);"),
@@ -44,6 +49,7 @@ PINS = [
     lambda: pins.test_mp_energy_drops_by_alpha_squared(8, 1),
     lambda: [pins.test_mp_steps_are_brute_force_best_fits_4x4(s) for s in range(6)],
     pins.test_mp_stop_rule_is_strict_and_checked_before_each_step,
+    lambda: [pins.test_exact_ties_go_to_the_lowest_index(b) for b in (4, 8)],
     pins.test_constant_image_gives_one_dc_atom_per_root,
     pins.test_zero_image_takes_no_step,
     pins.test_huge_tolerance_keeps_roots_without_atoms,

@@ -177,22 +177,52 @@ def test_mp_stop_rule_is_strict_and_checked_before_each_step():
     y = oracle.unravel(synthetic.noise_plane(b, b, seed=3))
     full = oracle.mp(D, y, 0.0, 4)
     E = full["energy"]
+    band = 2.0 ** -32 * E[0]            # energies this close to eps^2 count as equal to it
     # a threshold exactly equal to E_2 does not stop at step 2 (strict '<')
     r = oracle.mp(D, y, E[2], 4)
     assert r["steps"] == 3 and r["converged"]
-    # a threshold just above E_2 stops after two steps
-    r = oracle.mp(D, y, np.nextafter(E[2], np.inf), 4)
+    # nor does one inside the equality band
+    r = oracle.mp(D, y, E[2] + 0.5 * band, 4)
+    assert r["steps"] == 3 and r["converged"]
+    # a threshold clearly above E_2 stops after two steps
+    r = oracle.mp(D, y, E[2] + 2.0 * band, 4)
     assert r["steps"] == 2 and r["converged"]
     # the test after the last budgeted step still counts: meeting the
     # tolerance exactly at step k is convergence, not a split
-    r = oracle.mp(D, y, np.nextafter(E[2], np.inf), 2)
+    r = oracle.mp(D, y, E[2] + 2.0 * band, 2)
     assert r["steps"] == 2 and r["converged"]
     # a threshold above E_0 takes no step at all
-    r = oracle.mp(D, y, np.nextafter(E[0], np.inf), 4)
+    r = oracle.mp(D, y, E[0] + 2.0 * band, 4)
     assert r["steps"] == 0 and r["converged"]
     # the budget ends an unconverged pursuit after exactly k steps
     r = oracle.mp(D, y, 0.0, 3)
     assert r["steps"] == 3 and not r["converged"]
+
+
+@pytest.mark.parametrize("b", [4, 8])
+def test_exact_ties_go_to_the_lowest_index(b):
+    """Symmetric blocks (Y = Y^T) have dctn(Y)[p, q] = dctn(Y)[q, p] exactly:
+    atoms q b + p and p b + q tie, and the lower index must be taken first
+    however the two correlations happen to round."""
+    rng = np.random.default_rng(40 + b)
+    lower_first = 0
+    for trial in range(40):
+        A = rng.integers(0, 128, size=(b, b)).astype(np.float64)
+        Y = A + A.T
+        res = oracle.mp(oracle.dictionary(b, 1), oracle.unravel(Y), 0.0, b * b)
+        coef = scipy.fft.dctn(Y, norm="ortho")
+        seen = set()
+        for j in res["j"]:
+            p, q = int(j) % b, int(j) // b
+            if p != q and abs(abs(coef[p, q]) - abs(coef[q, p])) <= 1e-9 * np.abs(coef).max():
+                partner = p * b + q
+                # the partner (same magnitude) must not have been taken first
+                # if its index is lower
+                if partner < j:
+                    assert partner in seen, (trial, int(j), partner)
+                lower_first += 1
+            seen.add(int(j))
+    assert lower_first > 100
 
 
 # ------------------------------------------------------------ quadtree
