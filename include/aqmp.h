@@ -181,6 +181,22 @@ void aqmp_profile_reset(void);
 /* Copies up to `max` entries into `out` (host); *n receives the count. */
 int  aqmp_profile_read(aqmp_kernel_time *out, int max, int *n);
 
+/* aqmp_correlate without any device allocation, for callers that may not
+ * allocate device memory (memory owned by another allocator or by a fixed
+ * budget, loops that reserve everything at start-up).  The paper has no
+ * counterpart: this is a deployment variant of the correlation above; it
+ * takes the same arguments except the kernel choice (it always runs the
+ * tensor-core kernel) and returns the same result bit for bit.  Its scratch and
+ * tables live in fixed-size static device arrays that every GPU loading the
+ * library holds until exit (about 10 MB).  Limits: b in {4, 8, 16} and at
+ * most 65536 blocks (b = 4, 8) or 16384 blocks (b = 16) per call; larger
+ * requests return AQMP_E_ARG.  The first call on a device looks up the
+ * arrays' device addresses and should come before any stream capture.
+ * Calls share the arrays and synchronise `stream` before returning; GPU work
+ * of two calls must not overlap (this function serialises its callers). */
+int aqmp_correlate_noalloc(int b, int dict_id, const uint8_t *blocks, int64_t L, float *corr,
+                           void *stream);
+
 /* Number of atoms M of a dictionary at side b (2 b^2 or b^2), or < 0. */
 int aqmp_num_atoms(int b, int dict_id);
 

@@ -60,7 +60,8 @@ ATOM_DTYPE = np.dtype([("j", np.uint32), ("alpha", np.float32)])
 # symbols declared in include/aqmp.h
 EXPORTS = ["aqmp_params_default", "aqmp_encode_planes", "aqmp_encode", "aqmp_code_stats", "aqmp_code_copy",
            "aqmp_decode", "aqmp_code_free", "aqmp_correlate", "aqmp_num_atoms", "aqmp_last_error",
-           "aqmp_version", "aqmp_profile_enable", "aqmp_profile_reset", "aqmp_profile_read"]
+           "aqmp_version", "aqmp_profile_enable", "aqmp_profile_reset", "aqmp_profile_read",
+           "aqmp_correlate_noalloc"]
 
 
 class aqmp_kernel_time(ctypes.Structure):
@@ -92,6 +93,7 @@ def load_library(path: str | None = None):
         lib.aqmp_code_free.argtypes = [V]
         lib.aqmp_code_free.restype = None
         lib.aqmp_correlate.argtypes = [I, I, V, I64, V, I, V]
+        lib.aqmp_correlate_noalloc.argtypes = [I, I, V, I64, V, V]
         lib.aqmp_num_atoms.argtypes = [I, I]
         lib.aqmp_last_error.restype = ctypes.c_char_p
         lib.aqmp_version.restype = ctypes.c_char_p

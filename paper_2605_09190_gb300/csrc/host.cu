@@ -318,6 +318,22 @@ int check_params(const aqmp_params *p) {
 
 }  // namespace
 
+// Internal helpers shared with other translation units of the library.
+namespace aqmp {
+int set_error(int code, const char *msg) { return fail(code, "%s", msg); }
+void fp64_bases(int b, std::vector<double> &basis) { make_bases(b, basis); }
+int bf16_tensor_map(void *map, const void *base, unsigned long long rows, unsigned long long cols,
+                    unsigned box_rows) {
+    return encode_bf16_map(reinterpret_cast<CUtensorMap *>(map), base, rows, cols, box_rows);
+}
+int device_sm_count(int *sms) {
+    Ctx *c;
+    const int rc = get_ctx(&c);
+    if (rc == AQMP_OK) *sms = c->num_sms;
+    return rc;
+}
+}  // namespace aqmp
+
 // ===================================================================== ABI
 
 struct aqmp_code {

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace aqmp {
@@ -90,5 +92,12 @@ cudaError_t launch_seed_roots(const PlaneDesc *planes, int n_planes, int max_blo
 // basis_dev = [2][b][b] (DCT, Haar); fam0 selects the family of a
 // single-family dictionary (0 = DCT, 1 = Haar).
 cudaError_t build_fixed_tables_fam(DictDev &d, const double *basis_dev, int fam0, cudaStream_t st);
+
+// Host helpers defined in host.cu for the library's other entry points.
+int set_error(int code, const char *msg);
+void fp64_bases(int b, std::vector<double> &basis);
+int bf16_tensor_map(void *map, const void *base, unsigned long long rows, unsigned long long cols,
+                    unsigned box_rows);
+int device_sm_count(int *sms);
 
 }  // namespace aqmp
