@@ -56,6 +56,7 @@ struct Counters {
     unsigned long long attempts[kMaxLevels];
     unsigned long long iterations[kMaxLevels];
     unsigned int queue_count[kMaxLevels + 1];
+    unsigned int work_next[kMaxLevels];     // dynamic leaf assignment per level
     unsigned int error;                // first AQMP_E_* code raised on the device
     unsigned int error_info;
 };

@@ -2,35 +2,41 @@
 // stop rule Eq. (3)) with the quadtree split / emit of Algorithm 2.
 //
 // One group of T threads owns one leaf for its whole pursuit.  The leaf's M
-// correlations c_j = <r, phi_j> live in registers as double-float pairs, E/T
-// of them per thread (element j = lane + T s).  Each step:
-//   (a3) argmax |c_j|, ties to the lowest j: a 64-bit order-preserving key
-//        per element, a shuffle reduction inside each warp and, for groups
-//        wider than a warp, one pass through shared memory;
+// correlations c_j = <r, phi_j> live in registers as double-float pairs, E of
+// them per thread (element j = lane + T s).  Each step:
+//   (a3) argmax |c_j|, lowest j among equals;
 //   (a4) alpha = c_j*; c <- c - alpha G[:, j*].  The dictionary is the union
 //        of two orthonormal separable bases (DCT-II and Haar), so its Gram
 //        matrix is [[I, X], [X^T, I]] with X = kron(W, W), W = C H^T (b x b):
 //        the own-family column is e_j* (c_j* <- 0) and the other family's
-//        column is the outer product W[p*, :] (x) W[q*, :].  It is generated
-//        from W in shared memory, so no Gram column is read from memory;
+//        column is the outer product W[p*, :] (x) W[q*, :], generated from W
+//        in shared memory -- no Gram column is read from memory;
 //   (a5) E <- E - alpha^2 (Pythagoras for unit-norm atoms): the residual
 //        vector itself is never needed, only its energy;
 //   (a6) converged iff E < eps^2 (strict), tested before every step; the
 //        budget ends the pursuit after k steps.
 // Then (a7) a converged leaf, or any leaf at the smallest side, is emitted
 // with its steps; any other leaf pushes its four quadrants (TL, TR, BL, BR)
-// onto the next level's queue.
+// onto the next level's queue.  Leaves are handed out through a device
+// counter, so a group that finishes a short pursuit takes the next leaf.
+//
+// Argmax cost.  Each thread keeps, per atom family, the top two |hi| keys of
+// its elements (with the top's index, sign and low word).  A step changes one
+// family (and zeroes one element of the other), so only that family's top-2
+// is recomputed.  The group reduction carries (top key, index | sign, second
+// key, low word): alpha arrives with the reduction, and whether any other
+// atom lies within the decision window of the best is read off the second
+// key, with no extra pass over the elements.
 //
 // Equality in finite precision: correlations within 2^-32 ||y|| of the
 // largest count as tied and the lowest index among them wins; an energy
 // within 2^-32 ||y||^2 of eps^2 counts as equal to it (not converged).  The
 // FP64 oracle applies the same rule, so exact mathematical ties resolve the
-// same way on both sides whatever their rounding.
+// same way on both sides whatever their rounding.  When another atom is in
+// the window, the step is decided in full precision over the candidates.
 //
 // Certification: the pursuit's state carries ~2^-46 relative error.  Any
 // decision within 2^-37 (of ||y||, resp. ||y||^2) of one of those boundaries
-// -- another atom (not identical to the chosen one, as the DCT DC and Haar
-// scaling atoms are) near the tie edge, or the energy near the threshold --
 // marks the leaf AQMP_LEAF_NEAR_TIE: it is then not certified to agree with
 // an exact evaluation.
 #include <cuda_runtime.h>
@@ -45,21 +51,58 @@ struct StepRec {
     float hi, lo;
 };
 
-// (key, index) max with the lowest index among equal keys.
-__device__ __forceinline__ void keep_better(uint32_t &bk, uint32_t &bj, uint32_t ok, uint32_t oj) {
-    if (ok > bk || (ok == bk && oj < bj)) {
-        bk = ok;
-        bj = oj;
-    }
+constexpr uint32_t kNone = 0xffffffffu;
+
+// Top-2 summary of a set of correlations.  P packs the largest |hi| (its
+// float bits, high word) with (0xffff - index) << 1 | sign(hi) (low word), so
+// the unsigned maximum of P picks the largest magnitude and, among equal
+// magnitudes, the lowest index; k2 is the second largest |hi| bits (equal to
+// the largest when two atoms share it) and lo1 the low word of the top.
+struct Top2 {
+    unsigned long long P;
+    uint32_t k2;
+    float lo1;
+};
+
+__device__ __forceinline__ Top2 top2_empty() { return Top2{0ull, 0u, 0.0f}; }
+
+__device__ __forceinline__ unsigned long long top2_key(float hi, uint32_t j) {
+    const uint32_t h = __float_as_uint(hi);
+    return ((unsigned long long)(h & 0x7fffffffu) << 32) | (((0xffffu - j) << 1) | (h >> 31));
 }
 
-__device__ __forceinline__ void warp_argmax32(uint32_t &bk, uint32_t &bj) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        const uint32_t ok = __shfl_xor_sync(0xffffffffu, bk, off);
-        const uint32_t oj = __shfl_xor_sync(0xffffffffu, bj, off);
-        keep_better(bk, bj, ok, oj);
-    }
+// Fold one element into a running top-2.
+__device__ __forceinline__ void top2_fold(Top2 &t, float hi, float lo, uint32_t j) {
+    const unsigned long long Pe = top2_key(hi, j);
+    t.k2 = max(t.k2, min((uint32_t)(t.P >> 32), (uint32_t)(Pe >> 32)));
+    const bool take = Pe > t.P;
+    t.P = take ? Pe : t.P;
+    t.lo1 = take ? lo : t.lo1;
+}
+
+__device__ __forceinline__ Top2 top2_merge(const Top2 &a, const Top2 &b) {
+    const bool aw = a.P > b.P;
+    const uint32_t ka = (uint32_t)(a.P >> 32), kb = (uint32_t)(b.P >> 32);
+    return Top2{aw ? a.P : b.P, max(max(a.k2, b.k2), min(ka, kb)), aw ? a.lo1 : b.lo1};
+}
+
+__device__ __forceinline__ uint32_t top2_index(const Top2 &t) { return 0xffffu - (((uint32_t)t.P & 0x1ffffu) >> 1); }
+__device__ __forceinline__ bool top2_negative(const Top2 &t) { return ((uint32_t)t.P & 1u) != 0u; }
+__device__ __forceinline__ float top2_amax(const Top2 &t) { return __uint_as_float((uint32_t)(t.P >> 32)); }
+
+// Warp-wide top-2 with three redux.sync maxima: the largest |hi| key, the
+// lowest index among the lanes holding it, and the second key (the other
+// lanes' tops and the winner's own second).  Every lane gets the result.
+__device__ __forceinline__ Top2 warp_top2(const Top2 &t) {
+    const uint32_t hk = (uint32_t)(t.P >> 32);
+    const uint32_t mhk = __reduce_max_sync(0xffffffffu, hk);
+    const uint32_t low = (uint32_t)t.P;
+    const uint32_t mlow = __reduce_max_sync(0xffffffffu, hk == mhk ? low : 0u);
+    const bool winner = hk == mhk && low == mlow;
+    const uint32_t mk2 = __reduce_max_sync(0xffffffffu, winner ? t.k2 : hk);
+    const unsigned who = __ballot_sync(0xffffffffu, winner);
+    const float lo1 = __shfl_sync(0xffffffffu, t.lo1, __ffs(who) - 1);
+    return Top2{((unsigned long long)mhk << 32) | mlow, mk2, lo1};
 }
 
 __device__ __forceinline__ void warp_argmax64(unsigned long long &bk, uint32_t &bj) {
@@ -80,27 +123,75 @@ __device__ __forceinline__ uint32_t warp_min(uint32_t v) {
     return v;
 }
 
+// Rank-1 update of the elements in slots [S0, S0 + G) (one atom family,
+// whose in-family index is j - FOFF) and their new top-2, folded into up to
+// four independent accumulators to keep the dependency chains short.
+template <int B, int T, int E, int G, int S0, int FOFF>
+__device__ __forceinline__ Top2 update_family(float (&ch)[E], float (&cl)[E], int lane, const df &u,
+                                              const float2 *Vq) {
+    constexpr int A = G >= 4 ? 4 : G;
+    Top2 acc[A];
+#pragma unroll
+    for (int i = 0; i < A; ++i) acc[i] = top2_empty();
+#pragma unroll
+    for (int s2 = 0; s2 < G; ++s2) {
+        const int s = S0 + s2;
+        const int j = lane + T * s;
+        const float2 w = Vq[(j - FOFF) / B];
+        const df r = df_sub_mul(df{ch[s], cl[s]}, u, df{w.x, w.y});
+        ch[s] = r.hi;
+        cl[s] = r.lo;
+        top2_fold(acc[s2 % A], r.hi, r.lo, (uint32_t)j);
+    }
+#pragma unroll
+    for (int i = 1; i < A; ++i) acc[0] = top2_merge(acc[0], acc[i]);
+    return acc[0];
+}
+
+// Zero element j1 among slots [S0, S0 + G) and recompute their top-2.
+template <int T, int E, int G, int S0>
+__device__ __forceinline__ Top2 zero_and_rescan(float (&ch)[E], float (&cl)[E], int lane, uint32_t j1) {
+    constexpr int A = G >= 4 ? 4 : G;
+    Top2 acc[A];
+#pragma unroll
+    for (int i = 0; i < A; ++i) acc[i] = top2_empty();
+#pragma unroll
+    for (int s2 = 0; s2 < G; ++s2) {
+        const int s = S0 + s2;
+        const int j = lane + T * s;
+        if ((uint32_t)j == j1) { ch[s] = 0.0f; cl[s] = 0.0f; }
+        top2_fold(acc[s2 % A], ch[s], cl[s], (uint32_t)j);
+    }
+#pragma unroll
+    for (int i = 1; i < A; ++i) acc[0] = top2_merge(acc[0], acc[i]);
+    return acc[0];
+}
+
 // B: block side; T: threads per leaf (32 = one warp per leaf, several
 // leaves per CTA; > 32 = one leaf per CTA); NF: atom families (2 = DCT+Haar,
 // 1 = a single orthonormal family).
 template <int B, int T, int NF>
-__global__ void __launch_bounds__(T > 32 ? T : 256)
+__global__ void __launch_bounds__(T > 32 ? T : 256, T > 32 ? 1 : 2)
 mp_kernel(MPArgs a) {
     constexpr int n = B * B;
     constexpr int M = NF * n;
     constexpr int E = (M + T - 1) / T;
     static_assert(T % B == 0, "thread count must be a multiple of the side");
     constexpr int NW = T / 32;               // warps per group (T > 32)
-    constexpr uint32_t NONE = 0xffffffffu;
+    // SPLIT: the first E/2 elements of every thread are DCT atoms and the
+    // rest Haar atoms, each family cached separately; otherwise one group.
+    constexpr bool SPLIT = NF == 2 && (n % T) == 0 && (E % 2) == 0;
+    constexpr int NG = SPLIT ? 2 : 1;
+    constexpr int G = E / NG;
+    constexpr bool FULL = (M % T) == 0;      // every (lane, s) is an atom
 
     extern __shared__ __align__(16) unsigned char smem[];
     float2 *sW = reinterpret_cast<float2 *>(smem);             // W[p][p'] (hi, lo)
     float2 *sWT = sW + B * B;                                    // W^T
     unsigned char *after_tables = smem + (NF == 2 ? 2 * B * B * sizeof(float2) : 0);
-    uint32_t *sPk = reinterpret_cast<uint32_t *>(after_tables);  // [2][NW] keys
-    uint32_t *sPj = sPk + 2 * NW;                                 // [2][NW] indices
-    uint32_t *sMisc = sPj + 2 * NW;                               // [8]
-    unsigned long long *sRk = reinterpret_cast<unsigned long long *>(sMisc + 8);   // [NW] (8-aligned)
+    uint4 *sPart = reinterpret_cast<uint4 *>(after_tables);      // [2][NW] top-2 partials
+    uint32_t *sMisc = reinterpret_cast<uint32_t *>(sPart + 2 * NW);               // [8]
+    unsigned long long *sRk = reinterpret_cast<unsigned long long *>(sMisc + 8);  // [NW]
     uint32_t *sRj = reinterpret_cast<uint32_t *>(sRk + NW);      // [NW]
     StepRec *sSteps = reinterpret_cast<StepRec *>(sRj + NW);
 
@@ -115,13 +206,26 @@ mp_kernel(MPArgs a) {
 
     const int lane = (T == 32) ? (threadIdx.x & 31) : threadIdx.x;
     const int group = (T == 32) ? (threadIdx.x >> 5) : 0;
-    const int groups = (T == 32) ? (blockDim.x >> 5) : 1;
     StepRec *steps = sSteps + (size_t)group * lv.k;
     const int p_own = lane % B;
     const unsigned count = *lv.count;
     const int k = lv.k;
+    unsigned *work = &a.ctr->work_next[lv.level];
 
-    for (unsigned leaf = blockIdx.x * groups + group; leaf < count; leaf += gridDim.x * groups) {
+    for (;;) {
+        // dynamic assignment: the next unclaimed leaf of this level
+        unsigned leaf;
+        if (T > 32) {
+            if (lane == 0) sMisc[7] = atomicAdd(work, 1u);
+            __syncthreads();
+            leaf = sMisc[7];
+            __syncthreads();
+        } else {
+            leaf = lane == 0 ? atomicAdd(work, 1u) : 0u;
+            leaf = __shfl_sync(0xffffffffu, leaf, 0);
+        }
+        if (leaf >= count) break;
+
         const QueueEntry qe = lv.queue[leaf];
         const float tol = a.planes[qe.plane].tol;
         const df eps2 = df_scale(df_two_prod(tol, tol), (float)n);     // exact
@@ -136,14 +240,18 @@ mp_kernel(MPArgs a) {
         const float pre = ldexpf(S_f, -32) * 1.05f + ldexpf(S_f, -37) * 1.05f;
 
         float ch[E], cl[E];
+        Top2 top[NG];
         const float2 *cp = a.c0 + (size_t)leaf * M;
+#pragma unroll
+        for (int g = 0; g < NG; ++g) top[g] = top2_empty();
 #pragma unroll
         for (int s = 0; s < E; ++s) {
             const int j = lane + T * s;
-            if (j < M) {
+            if (FULL || j < M) {
                 const float2 v = cp[j];
                 ch[s] = v.x;
                 cl[s] = v.y;
+                top2_fold(top[s / G], v.x, v.y, (uint32_t)j);
             } else {
                 ch[s] = 0.0f;
                 cl[s] = 0.0f;
@@ -161,73 +269,44 @@ mp_kernel(MPArgs a) {
             if (below) { conv = true; break; }
             if (t == k) break;
 
-            // (a3) argmax |c|.  Main pass on the high words (largest |hi|,
-            // lowest index among equal); a second pass in full precision only
-            // when another atom lies within `window` of it.
-            uint32_t bk = 0u, bj = NONE;
+            // (a3) argmax |c| on the cached top-2 summaries
+            Top2 best = top[0];
 #pragma unroll
-            for (int s = 0; s < E; ++s) {
-                const int j = lane + T * s;
-                if (j < M) {
-                    const uint32_t key = __float_as_uint(ch[s]) & 0x7fffffffu;
-                    if (key > bk) { bk = key; bj = (uint32_t)j; }
-                }
-            }
-            warp_argmax32(bk, bj);
-            const int par = t & 1;
+            for (int g = 1; g < NG; ++g) best = top2_merge(best, top[g]);
+            best = warp_top2(best);
             if (T > 32) {
-                if ((lane & 31) == 0) {
-                    sPk[par * NW + (lane >> 5)] = bk;
-                    sPj[par * NW + (lane >> 5)] = bj;
-                }
+                const int par = t & 1;
+                if ((lane & 31) == 0)
+                    sPart[par * NW + (lane >> 5)] = make_uint4((uint32_t)best.P, (uint32_t)(best.P >> 32), best.k2,
+                                                               __float_as_uint(best.lo1));
                 __syncthreads();
                 const int l = lane & 31;
-                bk = l < NW ? sPk[par * NW + l] : 0u;
-                bj = l < NW ? sPj[par * NW + l] : NONE;
-                warp_argmax32(bk, bj);
+                if (l < NW) {
+                    const uint4 v = sPart[par * NW + l];
+                    best = Top2{((unsigned long long)v.y << 32) | v.x, v.z, __uint_as_float(v.w)};
+                } else {
+                    best = top2_empty();
+                }
+                best = warp_top2(best);
             }
-            if (bk == 0u) break;                 // every correlation is exactly zero
-            uint32_t j1 = bj;
-            const float amax = __uint_as_float(bk);
+            if ((best.P >> 32) == 0ull) break;   // every correlation is exactly zero
+            uint32_t j1 = top2_index(best);
+            const float amax = top2_amax(best);
+            df alpha = df{top2_negative(best) ? -amax : amax, best.lo1};
             const float window = amax * 0x1p-20f + pre;
-            // candidates: atoms other than j1 whose |hi| is within the window
-            bool cand = false;
-            float vh = 0.0f, vl = 0.0f;
-#pragma unroll
-            for (int s = 0; s < E; ++s) {
-                const int j = lane + T * s;
-                if (j < M) {
-                    if ((uint32_t)j == j1) { vh = ch[s]; vl = cl[s]; }
-                    else if (fabsf(ch[s]) >= amax - window) cand = true;
-                }
-            }
-            bool any_cand;
-            df alpha;
-            if (T > 32) {
-                if ((uint32_t)lane == j1 % (uint32_t)T) {
-                    sMisc[2 * par] = __float_as_uint(vh);
-                    sMisc[2 * par + 1] = __float_as_uint(vl);
-                }
-                any_cand = __syncthreads_or(cand) != 0;
-                alpha = df{__uint_as_float(sMisc[2 * par]), __uint_as_float(sMisc[2 * par + 1])};
-            } else {
-                any_cand = __any_sync(0xffffffffu, cand);
-                const int src = (int)(j1 & 31u);
-                alpha = df{__shfl_sync(0xffffffffu, vh, src), __shfl_sync(0xffffffffu, vl, src)};
-            }
-            if (any_cand) {
-                // Full precision among the candidates (j1 included): the true
-                // largest magnitude, then the lowest index within 2^-32 ||y||
-                // of it; any candidate within 2^-37 ||y|| of that edge is not
-                // certified.
+            if (__uint_as_float(best.k2) >= amax - window) {
+                // Another atom is within the window: decide in full precision
+                // among the candidates -- the true largest magnitude, then the
+                // lowest index within 2^-32 ||y|| of it; any candidate within
+                // 2^-37 ||y|| of that edge is not certified.
                 const double tieC = ldexp((double)S_f, -32);
                 const double bandC = ldexp((double)S_f, -37);
                 unsigned long long mk = 0ull;
-                uint32_t mj = NONE;
+                uint32_t mj = kNone;
 #pragma unroll
                 for (int s = 0; s < E; ++s) {
                     const int j = lane + T * s;
-                    if (j < M && fabsf(ch[s]) >= amax - window) {
+                    if ((FULL || j < M) && fabsf(ch[s]) >= amax - window) {
                         const double m = fabs((double)ch[s] + (double)cl[s]);
                         const unsigned long long key = (unsigned long long)__double_as_longlong(m);
                         if (key > mk) { mk = key; mj = (uint32_t)j; }
@@ -242,16 +321,15 @@ mp_kernel(MPArgs a) {
                     __syncthreads();
                     const int l = lane & 31;
                     mk = l < NW ? sRk[l] : 0ull;
-                    mj = l < NW ? sRj[l] : NONE;
+                    mj = l < NW ? sRj[l] : kNone;
                     warp_argmax64(mk, mj);
                 }
-                const double mmax = __longlong_as_double((long long)mk);
-                const double edge = mmax - tieC;
-                uint32_t lower = NONE;
+                const double edge = __longlong_as_double((long long)mk) - tieC;
+                uint32_t lower = kNone;
 #pragma unroll
                 for (int s = 0; s < E; ++s) {
                     const int j = lane + T * s;
-                    if (j < M && fabsf(ch[s]) >= amax - window) {
+                    if ((FULL || j < M) && fabsf(ch[s]) >= amax - window) {
                         const double m = fabs((double)ch[s] + (double)cl[s]);
                         if (fabs(m - edge) < bandC) tie = true;
                         if (m >= edge && (uint32_t)j < lower) lower = (uint32_t)j;
@@ -259,9 +337,9 @@ mp_kernel(MPArgs a) {
                 }
                 float wh = 0.0f, wl = 0.0f;
                 if (T > 32) {
-                    if (lane == 0) sMisc[6] = NONE;
+                    if (lane == 0) sMisc[6] = kNone;
                     __syncthreads();
-                    if (lower != NONE) atomicMin(&sMisc[6], lower);
+                    if (lower != kNone) atomicMin(&sMisc[6], lower);
                     __syncthreads();
                     lower = sMisc[6];
 #pragma unroll
@@ -293,37 +371,57 @@ mp_kernel(MPArgs a) {
 
             // (a4) correlation update through the Gram matrix
             const int fam1 = (int)(j1 >= (uint32_t)n);
-            const int f1 = (int)j1 - fam1 * n;
+            const bool owner = (uint32_t)lane == j1 % (uint32_t)T;
             if (NF == 2) {
+                const int f1 = (int)j1 - fam1 * n;
                 const int p1 = f1 % B, q1 = f1 / B;
                 const float2 *V = fam1 ? sWT : sW;
                 const float2 vp = V[p1 * B + p_own];
                 const df u = df_mul(alpha, df{vp.x, vp.y});
+                const float2 *Vq = V + q1 * B;
+                if (SPLIT) {
+                    // the other family: rank-1 update and its new top-2; the
+                    // chosen atom's own family: only its owner changes
+                    if (fam1) {
+                        top[0] = update_family<B, T, E, G, 0, 0>(ch, cl, lane, u, Vq);
+                        if (owner) top[NG - 1] = zero_and_rescan<T, E, G, G>(ch, cl, lane, j1);
+                    } else {
+                        top[NG - 1] = update_family<B, T, E, G, G, n>(ch, cl, lane, u, Vq);
+                        if (owner) top[0] = zero_and_rescan<T, E, G, 0>(ch, cl, lane, j1);
+                    }
+                } else {
+                    Top2 nt = top2_empty();
+#pragma unroll
+                    for (int s = 0; s < E; ++s) {
+                        const int j = lane + T * s;
+                        if (FULL || j < M) {
+                            const int fam = (int)(j >= n);
+                            if (fam != fam1) {
+                                const int q = (j - fam * n) / B;
+                                const float2 w = Vq[q];
+                                const df r = df_sub_mul(df{ch[s], cl[s]}, u, df{w.x, w.y});
+                                ch[s] = r.hi;
+                                cl[s] = r.lo;
+                            } else if ((uint32_t)j == j1) {
+                                ch[s] = 0.0f;
+                                cl[s] = 0.0f;
+                            }
+                            top2_fold(nt, ch[s], cl[s], (uint32_t)j);
+                        }
+                    }
+                    top[0] = nt;
+                }
+            } else if (owner) {
+                Top2 nt = top2_empty();
 #pragma unroll
                 for (int s = 0; s < E; ++s) {
                     const int j = lane + T * s;
-                    if (j < M) {
-                        const int fam = (int)(j >= n);
-                        if (fam != fam1) {
-                            const int q = (j - fam * n) / B;
-                            const float2 w = V[q1 * B + q];
-                            const df r = df_sub_mul(df{ch[s], cl[s]}, u, df{w.x, w.y});
-                            ch[s] = r.hi;
-                            cl[s] = r.lo;
-                        } else if (j == (int)j1) {
-                            ch[s] = 0.0f;
-                            cl[s] = 0.0f;
-                        }
+                    if (FULL || j < M) {
+                        if ((uint32_t)j == j1) { ch[s] = 0.0f; cl[s] = 0.0f; }
+                        top2_fold(nt, ch[s], cl[s], (uint32_t)j);
                     }
                 }
-            } else {
-#pragma unroll
-                for (int s = 0; s < E; ++s) {
-                    if (lane + T * s == (int)j1) {
-                        ch[s] = 0.0f;
-                        cl[s] = 0.0f;
-                    }
-                }
+                top[0] = nt;
             }
             ++t;
         }
@@ -348,7 +446,7 @@ mp_kernel(MPArgs a) {
                 uint8_t flags = (uint8_t)((tie_any ? 1u : 0u) | (qe.flags & 2u));
                 if (slot >= a.leaf_cap || o + t > a.atom_cap) {
                     raise_error(a.ctr, kDevErrQueueOverflow, 1u);
-                    off = 0xffffffffu;
+                    off = kNone;
                 } else {
                     LeafRec rec;
                     rec.plane = qe.plane;
@@ -387,7 +485,7 @@ mp_kernel(MPArgs a) {
                 __syncwarp();
                 off = __shfl_sync(0xffffffffu, off, 0);
             }
-            if (off != 0xffffffffu) {
+            if (off != kNone) {
                 for (int i = lane; i < t; i += T) {
                     const StepRec st = steps[i];
                     a.atoms[off + i] = AtomRec{st.j, st.hi};
@@ -403,8 +501,8 @@ template <int B, int T, int NF>
 static size_t mp_smem_bytes(int k, int groups) {
     constexpr int NW = T / 32;
     size_t bytes = (NF == 2 ? 2 * B * B * sizeof(float2) : 0);
-    bytes += 4 * NW * sizeof(uint32_t) + 8 * sizeof(uint32_t);        // partials, misc
-    bytes += NW * sizeof(unsigned long long) + NW * sizeof(uint32_t);  // wide partials
+    bytes += 2 * NW * sizeof(uint4) + 8 * sizeof(uint32_t);            // partials, misc
+    bytes += NW * sizeof(unsigned long long) + NW * sizeof(uint32_t);  // full-precision partials
     bytes += (size_t)groups * k * sizeof(StepRec);
     return bytes;
 }
@@ -429,6 +527,15 @@ static cudaError_t launch_mp_t(const MPArgs &a, int num_sms, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Threads per leaf for the two largest sides (compile-time knobs; the other
+// sides use one warp per leaf).
+#ifndef AQMP_MP_T32
+#define AQMP_MP_T32 128
+#endif
+#ifndef AQMP_MP_T64
+#define AQMP_MP_T64 256
+#endif
+
 cudaError_t launch_mp(const MPArgs &a, int nf, int num_sms, cudaStream_t st) {
     const int b = a.lv.b;
     if (nf == 2) {
@@ -436,16 +543,16 @@ cudaError_t launch_mp(const MPArgs &a, int nf, int num_sms, cudaStream_t st) {
             case 4: return launch_mp_t<4, 32, 2>(a, num_sms, st);
             case 8: return launch_mp_t<8, 32, 2>(a, num_sms, st);
             case 16: return launch_mp_t<16, 32, 2>(a, num_sms, st);
-            case 32: return launch_mp_t<32, 128, 2>(a, num_sms, st);
-            case 64: return launch_mp_t<64, 512, 2>(a, num_sms, st);
+            case 32: return launch_mp_t<32, AQMP_MP_T32, 2>(a, num_sms, st);
+            case 64: return launch_mp_t<64, AQMP_MP_T64, 2>(a, num_sms, st);
         }
     } else {
         switch (b) {
             case 4: return launch_mp_t<4, 32, 1>(a, num_sms, st);
             case 8: return launch_mp_t<8, 32, 1>(a, num_sms, st);
             case 16: return launch_mp_t<16, 32, 1>(a, num_sms, st);
-            case 32: return launch_mp_t<32, 128, 1>(a, num_sms, st);
-            case 64: return launch_mp_t<64, 512, 1>(a, num_sms, st);
+            case 32: return launch_mp_t<32, AQMP_MP_T32, 1>(a, num_sms, st);
+            case 64: return launch_mp_t<64, AQMP_MP_T64, 1>(a, num_sms, st);
         }
     }
     return cudaErrorInvalidValue;
