@@ -206,8 +206,10 @@ struct Ctx {
     int cc_major = 0, cc_minor = 0;
     std::mutex mu;
     std::map<int, std::unique_ptr<Dict>> dicts;
-    DeviceBuf planes, staging, queues, Y, e0, c0, leaves, atoms, alpha_lo, counters;
+    DeviceBuf planes, staging, queues, Y, e0, c0, counters;
     Counters *host_ctr = nullptr;             // pinned
+    PlaneDesc *host_planes = nullptr;         // pinned staging for plane descriptors
+    int host_planes_cap = 0;
 };
 
 std::mutex g_ctx_mu;
@@ -229,6 +231,12 @@ int get_ctx(Ctx **out) {
             return fail(AQMP_E_CUDA, "device %d is sm_%d%d; this library is built for sm_103a only", dev,
                         c->cc_major, c->cc_minor);
         CK(cudaMallocHost(&c->host_ctr, sizeof(Counters)));
+        // keep freed output blocks cached in the stream-ordered pool
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            unsigned long long keep = ~0ull;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
         slot = std::move(c);
     }
     *out = slot.get();
@@ -433,9 +441,13 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
     if ((rc = c->Y.reserve(sizeof(__nv_bfloat16) * ymax))) return rc;
     if ((rc = c->e0.reserve(sizeof(uint32_t) * emax))) return rc;
     if ((rc = c->c0.reserve(sizeof(float2) * cmax))) return rc;
-    if ((rc = c->leaves.reserve(sizeof(LeafRec) * leaf_cap))) return rc;
-    if ((rc = c->atoms.reserve(sizeof(AtomRec) * atom_cap))) return rc;
-    if ((rc = c->alpha_lo.reserve(sizeof(float) * atom_cap))) return rc;
+    // outputs: allocated per call from the stream-ordered pool at their
+    // worst-case size and written by the kernels directly
+    auto code = std::make_unique<aqmp_code>();
+    code->device = c->device;
+    CK(cudaMallocAsync((void **)&code->leaves, sizeof(LeafRec) * std::max<unsigned long long>(1, leaf_cap), st));
+    CK(cudaMallocAsync((void **)&code->atoms, sizeof(AtomRec) * std::max<unsigned long long>(1, atom_cap), st));
+    CK(cudaMallocAsync((void **)&code->alpha_lo, sizeof(float) * std::max<unsigned long long>(1, atom_cap), st));
     if ((rc = c->counters.reserve(sizeof(Counters)))) return rc;
 
     // plane descriptors (and host pixels copied in)
@@ -462,7 +474,15 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
         d.pad = 0;
         roff += (unsigned long long)(pl.height / P.max_block) * (pl.width / P.max_block);
     }
-    CK(cudaMemcpyAsync(c->planes.p, pd.data(), sizeof(PlaneDesc) * n_planes, cudaMemcpyHostToDevice, st));
+    if (c->host_planes_cap < n_planes) {
+        if (c->host_planes) cudaFreeHost(c->host_planes);
+        c->host_planes = nullptr;
+        c->host_planes_cap = 0;
+        CK(cudaMallocHost(&c->host_planes, sizeof(PlaneDesc) * n_planes));
+        c->host_planes_cap = n_planes;
+    }
+    std::memcpy(c->host_planes, pd.data(), sizeof(PlaneDesc) * n_planes);
+    CK(cudaMemcpyAsync(c->planes.p, c->host_planes, sizeof(PlaneDesc) * n_planes, cudaMemcpyHostToDevice, st));
     Counters *ctr = (Counters *)c->counters.p;
     CK(cudaMemsetAsync(ctr, 0, sizeof(Counters), st));
     QueueEntry *q = (QueueEntry *)c->queues.p;
@@ -516,10 +536,10 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
         ma.planes = (const PlaneDesc *)c->planes.p;
         ma.W = d.W;
         ma.WT = d.WT;
-        ma.leaves = (LeafRec *)c->leaves.p;
+        ma.leaves = code->leaves;
         ma.leaf_cap = leaf_cap;
-        ma.atoms = (AtomRec *)c->atoms.p;
-        ma.alpha_lo = (float *)c->alpha_lo.p;
+        ma.atoms = code->atoms;
+        ma.alpha_lo = code->alpha_lo;
         ma.atom_cap = atom_cap;
         ma.ctr = ctr;
         CK(g_prof.run(kname("mp", b), st, [&] { return launch_mp(ma, d.nf, c->num_sms, st); }));
@@ -535,24 +555,12 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
     if (h.error == kDevErrTimeout) return fail(AQMP_E_TIMEOUT, "device wait timed out (site %u)", h.error_info);
     if (h.error) return fail(AQMP_E_CUDA, "device error %u (%u)", h.error, h.error_info);
 
-    auto code = std::make_unique<aqmp_code>();
-    code->device = c->device;
     code->dict_id = P.dict_id;
     code->min_block = P.min_block;
     code->max_block = P.max_block;
     for (int i = 0; i < n_planes; ++i) code->shapes.emplace_back(planes[i].height, planes[i].width);
     code->n_leaves = h.n_leaves;
     code->n_atoms = h.n_atoms;
-    CK(cudaMalloc(&code->leaves, sizeof(LeafRec) * std::max<unsigned long long>(1, h.n_leaves)));
-    CK(cudaMalloc(&code->atoms, sizeof(AtomRec) * std::max<unsigned long long>(1, h.n_atoms)));
-    CK(cudaMalloc(&code->alpha_lo, sizeof(float) * std::max<unsigned long long>(1, h.n_atoms)));
-    if (h.n_leaves)
-        CK(cudaMemcpyAsync(code->leaves, c->leaves.p, sizeof(LeafRec) * h.n_leaves, cudaMemcpyDeviceToDevice, st));
-    if (h.n_atoms) {
-        CK(cudaMemcpyAsync(code->atoms, c->atoms.p, sizeof(AtomRec) * h.n_atoms, cudaMemcpyDeviceToDevice, st));
-        CK(cudaMemcpyAsync(code->alpha_lo, c->alpha_lo.p, sizeof(float) * h.n_atoms, cudaMemcpyDeviceToDevice, st));
-    }
-    CK(cudaStreamSynchronize(st));
     aqmp_stats &s = code->stats;
     s.n_leaves = h.n_leaves;
     s.n_atoms = h.n_atoms;

@@ -170,8 +170,12 @@ __device__ __forceinline__ Top2 zero_and_rescan(float (&ch)[E], float (&cl)[E], 
 // B: block side; T: threads per leaf (32 = one warp per leaf, several
 // leaves per CTA; > 32 = one leaf per CTA); NF: atom families (2 = DCT+Haar,
 // 1 = a single orthonormal family).
+#ifndef AQMP_MP_MINB64
+#define AQMP_MP_MINB64 1            // resident CTAs per SM asked of the side-64 kernel
+#endif
+
 template <int B, int T, int NF>
-__global__ void __launch_bounds__(T > 32 ? T : 256, T > 32 ? 1 : 2)
+__global__ void __launch_bounds__(T > 32 ? T : 256, T > 32 ? (B == 64 ? AQMP_MP_MINB64 : 1) : 2)
 mp_kernel(MPArgs a) {
     constexpr int n = B * B;
     constexpr int M = NF * n;
