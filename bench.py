@@ -125,6 +125,24 @@ def load_peaks():
             "sm_max_mhz": 2070.0}, "fallback"
 
 
+def profiled_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
+    None when the kernel's sources changed since that capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        entry = json.load(f).get(kernel)
+    if not entry:
+        return None
+    h = hashlib.sha256()
+    for src in entry["sources"]:
+        with open(os.path.join(ROOT, "paper_2605_09190_gb300", "csrc", src), "rb") as f:
+            h.update(f.read())
+    return entry["dram_bytes_per_launch"] if h.hexdigest() == entry["sources_sha256"] else None
+
+
 def roofline(profile, stats_sum, steps, peaks, peak_kind, sm_mhz):
     """Roofline entry of the kernel with the largest share of device time."""
     if not profile:
@@ -159,6 +177,7 @@ def roofline(profile, stats_sum, steps, peaks, peak_kind, sm_mhz):
         r = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
              "traffic": None, "kernel": name, "peak_source": f"hbm_gbs ({peak_kind})"}
     r["launch_ms"] = per_launch_s * 1e3
+    r["traffic"] = profiled_traffic(name)
     return r, name
 
 
