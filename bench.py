@@ -293,6 +293,22 @@ def run_ours(args):
     value = world * npix * args.steps / 1e6 / total_s
     iters_per_s = world * stats_sum["atom_iterations"] / total_s
 
+    # the plain FP32 form on the same workload, for comparison (same timing rules)
+    fp32_ms = []
+    barrier()
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        code = aqmp.aqmp_encode_planes(dev, TOLS, min_block=MIN_BLOCK, max_block=MAX_BLOCK,
+                                       precision=aqmp.AQMP_PREC_FP32)
+        s1.record(stream)
+        code.free()
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            fp32_ms.append(s0.elapsed_time(s1))
+    fp32_value = world * npix * args.steps / 1e6 / (sum(fp32_ms) / 1e3)
+
     # end to end: pinned host input -> encode -> host copy of the result
     host = [torch.from_numpy(p).pin_memory() for p in planes]
     e2e_times, d2h = [], 0
@@ -342,6 +358,8 @@ def run_ours(args):
                 "atom_iterations_per_step": stats_sum["atom_iterations"] / args.steps,
                 "leaves_per_step": stats_sum["n_leaves"] / args.steps,
                 "near_tie_leaves": stats_sum["near_tie_leaves"],
+                "forms": {"exact (bf16-limb tensor GEMM + f32x2 certified pursuit)": value,
+                          "fp32 (same GEMM rounded to fp32 + fp32 pursuit, not certified)": fp32_value},
                 "roofline": roof, "kernels": kernels, "gpu_launches": launches,
                 "e2e": e2e, "clocks": clk, "cpu_baseline": cpu}
         print(json.dumps(line))

@@ -51,6 +51,10 @@ extern "C" {
                                       an FP64 evaluation except where a
                                       decision margin is below ~2^-36 of the
                                       block norm, and such leaves are flagged */
+#define AQMP_PREC_FP32      1      /* the plain FP32 form: the same correlation
+                                      rounded to FP32, FP32 pursuit state (one
+                                      FMA per Gram entry), FP32 energy and stop
+                                      test; faster, decisions not certified */
 
 /* aqmp_params.flags */
 #define AQMP_FLAG_INPUT_DEVICE  1u /* plane pointers are device addresses */

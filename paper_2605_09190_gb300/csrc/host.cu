@@ -320,7 +320,8 @@ int check_params(const aqmp_params *p) {
         return fail(AQMP_E_ARG, "block sizes must be powers of two with 4 <= min_block <= max_block");
     if (p->max_block > kMaxSide) return fail(AQMP_E_UNSUPPORTED, "max_block above %d is not built", kMaxSide);
     if (p->dict_id < 0 || p->dict_id > 2) return fail(AQMP_E_DICT, "unknown dictionary id %d", p->dict_id);
-    if (p->precision != AQMP_PREC_EXACT) return fail(AQMP_E_UNSUPPORTED, "unknown precision %d", p->precision);
+    if (p->precision != AQMP_PREC_EXACT && p->precision != AQMP_PREC_FP32)
+        return fail(AQMP_E_UNSUPPORTED, "unknown precision %d", p->precision);
     return AQMP_OK;
 }
 
@@ -542,7 +543,9 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
         ma.alpha_lo = code->alpha_lo;
         ma.atom_cap = atom_cap;
         ma.ctr = ctr;
-        CK(g_prof.run(kname("mp", b), st, [&] { return launch_mp(ma, d.nf, c->num_sms, st); }));
+        const bool exact = P.precision == AQMP_PREC_EXACT;
+        CK(g_prof.run(kname(exact ? "mp" : "mp_fp32", b), st,
+                      [&] { return launch_mp(ma, d.nf, exact, c->num_sms, st); }));
     }
     CK(cudaMemcpyAsync(c->host_ctr, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -606,19 +609,22 @@ int aqmp_code_copy(const aqmp_code *code, aqmp_leaf *leaves, aqmp_atom *atoms, f
         CK(cudaMemcpy(lo.data(), code->alpha_lo, sizeof(float) * lo.size(), cudaMemcpyDeviceToHost));
     }
     // canonical order: plane, root (row-major), then depth-first TL, TR, BL, BR
-    // = Z-order of the leaf's corner inside its root
+    // = Z-order of the leaf's corner inside its root.  One 64-bit key per
+    // leaf (plane: 12 bits, root: 28 bits, Z-order cell: 24 bits), sorted once.
     const unsigned mb = (unsigned)code->max_block, nb = (unsigned)code->min_block;
-    auto key = [&](const LeafRec &r) {
-        const unsigned long long rx = code->shapes[r.plane].second / mb;
+    std::vector<std::pair<unsigned long long, unsigned>> keyed(L.size());
+    for (size_t i = 0; i < L.size(); ++i) {
+        const LeafRec &r = L[i];
+        const unsigned long long rx = (unsigned long long)code->shapes[r.plane].second / mb;
         const unsigned long long root = (r.y / mb) * rx + (r.x / mb);
         const unsigned cy = (r.y % mb) / nb, cx = (r.x % mb) / nb;
         unsigned long long z = 0;
-        for (int bit = 15; bit >= 0; --bit) z = (z << 2) | (((cy >> bit) & 1u) << 1) | ((cx >> bit) & 1u);
-        return std::make_tuple((unsigned long long)r.plane, root, z);
-    };
+        for (int bit = 11; bit >= 0; --bit) z = (z << 2) | (((cy >> bit) & 1u) << 1) | ((cx >> bit) & 1u);
+        keyed[i] = {((unsigned long long)r.plane << 52) | (root << 24) | z, (unsigned)i};
+    }
+    std::sort(keyed.begin(), keyed.end());
     std::vector<size_t> order(L.size());
-    std::iota(order.begin(), order.end(), 0);
-    std::sort(order.begin(), order.end(), [&](size_t a, size_t b) { return key(L[a]) < key(L[b]); });
+    for (size_t i = 0; i < L.size(); ++i) order[i] = keyed[i].second;
     unsigned long long off = 0;
     for (size_t i = 0; i < order.size(); ++i) {
         LeafRec r = L[order[i]];

@@ -24,7 +24,7 @@ struct MPArgs {
     unsigned long long atom_cap;
     Counters *ctr;
 };
-cudaError_t launch_mp(const MPArgs &a, int nf, int num_sms, cudaStream_t st);
+cudaError_t launch_mp(const MPArgs &a, int nf, bool double_float, int num_sms, cudaStream_t st);
 
 // Block gather (gather.cu): queue entries -> centred BF16 leaf vectors
 // (column-major unravel, zero padded to Kpad) and sums of squares.

@@ -71,6 +71,35 @@ __device__ __forceinline__ unsigned long long top2_key(float hi, uint32_t j) {
     return ((unsigned long long)(h & 0x7fffffffu) << 32) | (((0xffffu - j) << 1) | (h >> 31));
 }
 
+// Running top-2 kept on float magnitudes inside element loops (cheaper per
+// element than the packed key); converted to a Top2 once per thread.
+struct Run2 {
+    float v1, lo1, m2;     // signed top value, its low word, second largest |value|
+    uint32_t j1;
+};
+
+__device__ __forceinline__ Run2 run2_empty() { return Run2{0.0f, 0.0f, 0.0f, 0xffffu}; }
+
+// Elements must be folded in ascending index order (strict > keeps the
+// lowest index among equal magnitudes).
+__device__ __forceinline__ void run2_fold(Run2 &r, float hi, float lo, uint32_t j) {
+    const float ah = fabsf(hi), a1 = fabsf(r.v1);
+    r.m2 = fmaxf(r.m2, fminf(a1, ah));
+    const bool take = ah > a1;
+    r.v1 = take ? hi : r.v1;
+    r.lo1 = take ? lo : r.lo1;
+    r.j1 = take ? j : r.j1;
+}
+
+__device__ __forceinline__ Top2 run2_top2(const Run2 &r) {
+    const uint32_t h = __float_as_uint(r.v1);
+    const unsigned long long P = r.v1 == 0.0f && r.j1 == 0xffffu
+                                     ? 0ull
+                                     : ((unsigned long long)(h & 0x7fffffffu) << 32) |
+                                           (((0xffffu - r.j1) << 1) | (h >> 31));
+    return Top2{P, __float_as_uint(r.m2), r.lo1};
+}
+
 // Fold one element into a running top-2.
 __device__ __forceinline__ void top2_fold(Top2 &t, float hi, float lo, uint32_t j) {
     const unsigned long long Pe = top2_key(hi, j);
@@ -126,55 +155,63 @@ __device__ __forceinline__ uint32_t warp_min(uint32_t v) {
 // Rank-1 update of the elements in slots [S0, S0 + G) (one atom family,
 // whose in-family index is j - FOFF) and their new top-2, folded into up to
 // four independent accumulators to keep the dependency chains short.
-template <int B, int T, int E, int G, int S0, int FOFF>
+template <int B, int T, int E, int G, int S0, int FOFF, bool DF>
 __device__ __forceinline__ Top2 update_family(float (&ch)[E], float (&cl)[E], int lane, const df &u,
                                               const float2 *Vq) {
     constexpr int A = G >= 4 ? 4 : G;
-    Top2 acc[A];
+    Run2 acc[A];
 #pragma unroll
-    for (int i = 0; i < A; ++i) acc[i] = top2_empty();
+    for (int i = 0; i < A; ++i) acc[i] = run2_empty();
 #pragma unroll
     for (int s2 = 0; s2 < G; ++s2) {
         const int s = S0 + s2;
         const int j = lane + T * s;
         const float2 w = Vq[(j - FOFF) / B];
-        const df r = df_sub_mul(df{ch[s], cl[s]}, u, df{w.x, w.y});
-        ch[s] = r.hi;
-        cl[s] = r.lo;
-        top2_fold(acc[s2 % A], r.hi, r.lo, (uint32_t)j);
+        if (DF) {
+            const df r = df_sub_mul(df{ch[s], cl[s]}, u, df{w.x, w.y});
+            ch[s] = r.hi;
+            cl[s] = r.lo;
+        } else {
+            ch[s] = __fmaf_rn(-u.hi, w.x, ch[s]);     // plain FP32 form: one FMA per entry
+        }
+        run2_fold(acc[s2 % A], ch[s], cl[s], (uint32_t)j);
     }
+    Top2 t = run2_top2(acc[0]);
 #pragma unroll
-    for (int i = 1; i < A; ++i) acc[0] = top2_merge(acc[0], acc[i]);
-    return acc[0];
+    for (int i = 1; i < A; ++i) t = top2_merge(t, run2_top2(acc[i]));
+    return t;
 }
 
 // Zero element j1 among slots [S0, S0 + G) and recompute their top-2.
 template <int T, int E, int G, int S0>
 __device__ __forceinline__ Top2 zero_and_rescan(float (&ch)[E], float (&cl)[E], int lane, uint32_t j1) {
     constexpr int A = G >= 4 ? 4 : G;
-    Top2 acc[A];
+    Run2 acc[A];
 #pragma unroll
-    for (int i = 0; i < A; ++i) acc[i] = top2_empty();
+    for (int i = 0; i < A; ++i) acc[i] = run2_empty();
 #pragma unroll
     for (int s2 = 0; s2 < G; ++s2) {
         const int s = S0 + s2;
         const int j = lane + T * s;
         if ((uint32_t)j == j1) { ch[s] = 0.0f; cl[s] = 0.0f; }
-        top2_fold(acc[s2 % A], ch[s], cl[s], (uint32_t)j);
+        run2_fold(acc[s2 % A], ch[s], cl[s], (uint32_t)j);
     }
+    Top2 t = run2_top2(acc[0]);
 #pragma unroll
-    for (int i = 1; i < A; ++i) acc[0] = top2_merge(acc[0], acc[i]);
-    return acc[0];
+    for (int i = 1; i < A; ++i) t = top2_merge(t, run2_top2(acc[i]));
+    return t;
 }
 
 // B: block side; T: threads per leaf (32 = one warp per leaf, several
 // leaves per CTA; > 32 = one leaf per CTA); NF: atom families (2 = DCT+Haar,
-// 1 = a single orthonormal family).
+// 1 = a single orthonormal family); DF: double-float state with certified
+// decisions (true) or the plain FP32 form (false: FP32 correlations, energy
+// and stop test, one FMA per Gram entry, no certification).
 #ifndef AQMP_MP_MINB64
 #define AQMP_MP_MINB64 1            // resident CTAs per SM asked of the side-64 kernel
 #endif
 
-template <int B, int T, int NF>
+template <int B, int T, int NF, bool DF>
 __global__ void __launch_bounds__(T > 32 ? T : 256, T > 32 ? (B == 64 ? AQMP_MP_MINB64 : 1) : 2)
 mp_kernel(MPArgs a) {
     constexpr int n = B * B;
@@ -238,6 +275,7 @@ mp_kernel(MPArgs a) {
         // accuracy threshold eps^2 - 2^-32 ||y||^2 and its certification band
         const df thrE = df_sub(eps2, df_scale(df_from_i64((long long)e0), 0x1p-32f));
         const float bandE_f = ldexpf((float)e0, -37);
+        const float eps2_f = __fmul_rn(__fmul_rn(tol, tol), (float)n);   // FP32 form's threshold
         const float S_f = sqrtf((float)e0);
         // window of |hi| below the largest within which the order or the tie
         // rule may depend on the low words: a few ulps plus the tie band
@@ -254,8 +292,8 @@ mp_kernel(MPArgs a) {
             if (FULL || j < M) {
                 const float2 v = cp[j];
                 ch[s] = v.x;
-                cl[s] = v.y;
-                top2_fold(top[s / G], v.x, v.y, (uint32_t)j);
+                cl[s] = DF ? v.y : 0.0f;
+                top2_fold(top[s / G], v.x, cl[s], (uint32_t)j);
             } else {
                 ch[s] = 0.0f;
                 cl[s] = 0.0f;
@@ -266,8 +304,8 @@ mp_kernel(MPArgs a) {
         bool conv = false, tie = false;
         for (;;) {
             // (a6) accuracy test before every step, strict
-            const bool below = df_lt(En, thrE);
-            if (fabsf(En.hi - thrE.hi) <= bandE_f * 1.01f + 0x1p-20f * fabsf(thrE.hi)) {
+            const bool below = DF ? df_lt(En, thrE) : (En.hi < eps2_f);
+            if (DF && fabsf(En.hi - thrE.hi) <= bandE_f * 1.01f + 0x1p-20f * fabsf(thrE.hi)) {
                 if (fabs(df_to_double(En) - df_to_double(thrE)) < ldexp((double)e0, -37)) tie = true;
             }
             if (below) { conv = true; break; }
@@ -298,7 +336,7 @@ mp_kernel(MPArgs a) {
             const float amax = top2_amax(best);
             df alpha = df{top2_negative(best) ? -amax : amax, best.lo1};
             const float window = amax * 0x1p-20f + pre;
-            if (__uint_as_float(best.k2) >= amax - window) {
+            if (DF && __uint_as_float(best.k2) >= amax - window) {
                 // Another atom is within the window: decide in full precision
                 // among the candidates -- the true largest magnitude, then the
                 // lowest index within 2^-32 ||y|| of it; any candidate within
@@ -371,7 +409,8 @@ mp_kernel(MPArgs a) {
             if (lane == 0) steps[t] = StepRec{j1, alpha.hi, alpha.lo};
 
             // (a5) energy
-            En = df_sub(En, df_mul(alpha, alpha));
+            if (DF) En = df_sub(En, df_mul(alpha, alpha));
+            else En = df{__fmaf_rn(-alpha.hi, alpha.hi, En.hi), 0.0f};
 
             // (a4) correlation update through the Gram matrix
             const int fam1 = (int)(j1 >= (uint32_t)n);
@@ -381,16 +420,16 @@ mp_kernel(MPArgs a) {
                 const int p1 = f1 % B, q1 = f1 / B;
                 const float2 *V = fam1 ? sWT : sW;
                 const float2 vp = V[p1 * B + p_own];
-                const df u = df_mul(alpha, df{vp.x, vp.y});
+                const df u = DF ? df_mul(alpha, df{vp.x, vp.y}) : df{__fmul_rn(alpha.hi, vp.x), 0.0f};
                 const float2 *Vq = V + q1 * B;
                 if (SPLIT) {
                     // the other family: rank-1 update and its new top-2; the
                     // chosen atom's own family: only its owner changes
                     if (fam1) {
-                        top[0] = update_family<B, T, E, G, 0, 0>(ch, cl, lane, u, Vq);
+                        top[0] = update_family<B, T, E, G, 0, 0, DF>(ch, cl, lane, u, Vq);
                         if (owner) top[NG - 1] = zero_and_rescan<T, E, G, G>(ch, cl, lane, j1);
                     } else {
-                        top[NG - 1] = update_family<B, T, E, G, G, n>(ch, cl, lane, u, Vq);
+                        top[NG - 1] = update_family<B, T, E, G, G, n, DF>(ch, cl, lane, u, Vq);
                         if (owner) top[0] = zero_and_rescan<T, E, G, 0>(ch, cl, lane, j1);
                     }
                 } else {
@@ -403,9 +442,13 @@ mp_kernel(MPArgs a) {
                             if (fam != fam1) {
                                 const int q = (j - fam * n) / B;
                                 const float2 w = Vq[q];
-                                const df r = df_sub_mul(df{ch[s], cl[s]}, u, df{w.x, w.y});
-                                ch[s] = r.hi;
-                                cl[s] = r.lo;
+                                if (DF) {
+                                    const df r = df_sub_mul(df{ch[s], cl[s]}, u, df{w.x, w.y});
+                                    ch[s] = r.hi;
+                                    cl[s] = r.lo;
+                                } else {
+                                    ch[s] = __fmaf_rn(-u.hi, w.x, ch[s]);
+                                }
                             } else if ((uint32_t)j == j1) {
                                 ch[s] = 0.0f;
                                 cl[s] = 0.0f;
@@ -511,12 +554,12 @@ static size_t mp_smem_bytes(int k, int groups) {
     return bytes;
 }
 
-template <int B, int T, int NF>
+template <int B, int T, int NF, bool DF>
 static cudaError_t launch_mp_t(const MPArgs &a, int num_sms, cudaStream_t st) {
     const int block = (T == 32) ? 256 : T;
     const int groups = (T == 32) ? block / 32 : 1;
     const size_t smem = mp_smem_bytes<B, T, NF>(a.lv.k, groups);
-    auto kern = mp_kernel<B, T, NF>;
+    auto kern = mp_kernel<B, T, NF, DF>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -540,26 +583,31 @@ static cudaError_t launch_mp_t(const MPArgs &a, int num_sms, cudaStream_t st) {
 #define AQMP_MP_T64 256
 #endif
 
-cudaError_t launch_mp(const MPArgs &a, int nf, int num_sms, cudaStream_t st) {
+template <bool DF>
+static cudaError_t launch_mp_prec(const MPArgs &a, int nf, int num_sms, cudaStream_t st) {
     const int b = a.lv.b;
     if (nf == 2) {
         switch (b) {
-            case 4: return launch_mp_t<4, 32, 2>(a, num_sms, st);
-            case 8: return launch_mp_t<8, 32, 2>(a, num_sms, st);
-            case 16: return launch_mp_t<16, 32, 2>(a, num_sms, st);
-            case 32: return launch_mp_t<32, AQMP_MP_T32, 2>(a, num_sms, st);
-            case 64: return launch_mp_t<64, AQMP_MP_T64, 2>(a, num_sms, st);
+            case 4: return launch_mp_t<4, 32, 2, DF>(a, num_sms, st);
+            case 8: return launch_mp_t<8, 32, 2, DF>(a, num_sms, st);
+            case 16: return launch_mp_t<16, 32, 2, DF>(a, num_sms, st);
+            case 32: return launch_mp_t<32, AQMP_MP_T32, 2, DF>(a, num_sms, st);
+            case 64: return launch_mp_t<64, AQMP_MP_T64, 2, DF>(a, num_sms, st);
         }
     } else {
         switch (b) {
-            case 4: return launch_mp_t<4, 32, 1>(a, num_sms, st);
-            case 8: return launch_mp_t<8, 32, 1>(a, num_sms, st);
-            case 16: return launch_mp_t<16, 32, 1>(a, num_sms, st);
-            case 32: return launch_mp_t<32, AQMP_MP_T32, 1>(a, num_sms, st);
-            case 64: return launch_mp_t<64, AQMP_MP_T64, 1>(a, num_sms, st);
+            case 4: return launch_mp_t<4, 32, 1, DF>(a, num_sms, st);
+            case 8: return launch_mp_t<8, 32, 1, DF>(a, num_sms, st);
+            case 16: return launch_mp_t<16, 32, 1, DF>(a, num_sms, st);
+            case 32: return launch_mp_t<32, AQMP_MP_T32, 1, DF>(a, num_sms, st);
+            case 64: return launch_mp_t<64, AQMP_MP_T64, 1, DF>(a, num_sms, st);
         }
     }
     return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_mp(const MPArgs &a, int nf, bool double_float, int num_sms, cudaStream_t st) {
+    return double_float ? launch_mp_prec<true>(a, nf, num_sms, st) : launch_mp_prec<false>(a, nf, num_sms, st);
 }
 
 }  // namespace aqmp
