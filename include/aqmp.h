@@ -201,6 +201,13 @@ int  aqmp_profile_read(aqmp_kernel_time *out, int max, int *n);
 int aqmp_correlate_noalloc(int b, int dict_id, const uint8_t *blocks, int64_t L, float *corr,
                            void *stream);
 
+/* Check of the failure path (no counterpart in the paper): runs one thread
+ * that waits, with the library's bounded device wait, on a barrier nothing
+ * ever arrives on.  It must give up after `limit_ms` (1..5000) and report it:
+ * the expected return is AQMP_E_TIMEOUT, after which the device stays usable.
+ * AQMP_OK would mean the wait was not bounded. */
+int aqmp_selftest_wait(int limit_ms, void *stream);
+
 /* Number of atoms M of a dictionary at side b (2 b^2 or b^2), or < 0. */
 int aqmp_num_atoms(int b, int dict_id);
 

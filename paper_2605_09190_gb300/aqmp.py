@@ -62,7 +62,7 @@ ATOM_DTYPE = np.dtype([("j", np.uint32), ("alpha", np.float32)])
 EXPORTS = ["aqmp_params_default", "aqmp_encode_planes", "aqmp_encode", "aqmp_code_stats", "aqmp_code_copy",
            "aqmp_decode", "aqmp_code_free", "aqmp_correlate", "aqmp_num_atoms", "aqmp_last_error",
            "aqmp_version", "aqmp_profile_enable", "aqmp_profile_reset", "aqmp_profile_read",
-           "aqmp_correlate_noalloc"]
+           "aqmp_correlate_noalloc", "aqmp_selftest_wait"]
 
 
 class aqmp_kernel_time(ctypes.Structure):
@@ -95,6 +95,7 @@ def load_library(path: str | None = None):
         lib.aqmp_code_free.restype = None
         lib.aqmp_correlate.argtypes = [I, I, V, I64, V, I, V]
         lib.aqmp_correlate_noalloc.argtypes = [I, I, V, I64, V, V]
+        lib.aqmp_selftest_wait.argtypes = [I, V]
         lib.aqmp_num_atoms.argtypes = [I, I]
         lib.aqmp_last_error.restype = ctypes.c_char_p
         lib.aqmp_version.restype = ctypes.c_char_p
@@ -276,3 +277,9 @@ def aqmp_profile_read() -> dict:
     n = ctypes.c_int(0)
     _check(load_library().aqmp_profile_read(arr, 64, ctypes.byref(n)))
     return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(n.value)}
+
+
+def aqmp_selftest_wait(limit_ms: int = 50, stream=None) -> int:
+    """Run the bounded-wait check; returns the library's status code
+    (AQMP_E_TIMEOUT, -7, is the expected outcome)."""
+    return load_library().aqmp_selftest_wait(int(limit_ms), _stream_handle(stream))

@@ -77,13 +77,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
 }
 
 // Bounded wait for the phase of parity `parity`; false on timeout or abort.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
+                                          unsigned long long limit_ns = kWaitNs) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = globaltimer();
     for (;;) {
         if (mbar_try_wait(bar, parity)) return true;
         if (*abort_flag) return false;
-        if (globaltimer() - t0 > kWaitNs) {
+        if (globaltimer() - t0 > limit_ns) {
             *abort_flag = 1;
             return false;
         }
@@ -264,6 +265,25 @@ corr_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 }
 
 bool corr_tc_available() { return true; }
+
+// Failure-path check: one thread waits, through the same bounded wait as the
+// correlation kernel, on an mbarrier that nothing ever arrives on, and must
+// give up after `limit_ns` and record AQMP_E_TIMEOUT in the error word.
+__global__ void wait_selftest_kernel(Counters *ctr, unsigned long long limit_ns) {
+    __shared__ __align__(8) unsigned long long bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x != 0) return;
+    const uint32_t b = tc::smem_u32(&bar);
+    tc::mbar_init(b, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (!tc::mbar_wait(b, 0u, &abort_flag, limit_ns)) raise_error(ctr, kDevErrTimeout, 99u);
+}
+
+cudaError_t launch_wait_selftest(Counters *ctr, unsigned long long limit_ns, cudaStream_t st) {
+    wait_selftest_kernel<<<1, 32, 0, st>>>(ctr, limit_ns);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_corr_tc(const CorrArgs &a, cudaStream_t st) {
     const DictDev &d = *a.d;

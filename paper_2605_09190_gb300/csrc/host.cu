@@ -688,6 +688,25 @@ int aqmp_decode(const aqmp_code *code, int plane, float *out, int64_t out_pitch,
 
 void aqmp_code_free(aqmp_code *code) { delete code; }
 
+int aqmp_selftest_wait(int limit_ms, void *stream) {
+    g_last_error.clear();
+    if (limit_ms < 1 || limit_ms > 5000) return fail(AQMP_E_ARG, "limit_ms must be in [1, 5000]");
+    Ctx *c;
+    int rc;
+    if ((rc = get_ctx(&c))) return rc;
+    std::lock_guard<std::mutex> lock(c->mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((rc = c->counters.reserve(sizeof(Counters)))) return rc;
+    Counters *ctr = (Counters *)c->counters.p;
+    CK(cudaMemsetAsync(ctr, 0, sizeof(Counters), st));
+    CK(launch_wait_selftest(ctr, (unsigned long long)limit_ms * 1000000ull, st));
+    CK(cudaMemcpyAsync(c->host_ctr, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (c->host_ctr->error == kDevErrTimeout)
+        return fail(AQMP_E_TIMEOUT, "bounded device wait gave up after %d ms (as intended)", limit_ms);
+    return AQMP_OK;
+}
+
 int aqmp_profile_enable(int on) {
     std::lock_guard<std::mutex> g(g_prof.mu);
     const int prev = g_prof.on ? 1 : 0;

@@ -68,6 +68,7 @@ struct CorrArgs {
 cudaError_t launch_corr_simt(const CorrArgs &a, cudaStream_t st);
 cudaError_t launch_corr_tc(const CorrArgs &a, cudaStream_t st);
 bool corr_tc_available();
+cudaError_t launch_wait_selftest(Counters *ctr, unsigned long long limit_ns, cudaStream_t st);
 
 // Decoder (decode.cu): one plane's leaves -> float image.
 struct DecodeArgs {

@@ -169,3 +169,27 @@ def test_piecewise_512_tolerance_sweep_sampled_roots(lib):
     for p in range(4):
         sel = leaves[leaves["plane"] == p]
         assert int(np.sum(sel["b"].astype(np.int64) ** 2)) == 512 * 512
+
+
+def test_uneven_rgb_batch_in_one_call(lib):
+    """Leaves of many images and sizes go through one batched encode; every
+    plane's sampled roots match the oracle."""
+    batch = synthetic.uneven_rgb_batch(4, seed=5, wmin=128, wmax=320, hmin=128, hmax=256)
+    planes = [p for (_, _, chans) in batch for p in chans]
+    code = lib.aqmp_encode_planes([torch.from_numpy(p).cuda() for p in planes], 1.5)
+    leaves, atoms, lo = code.copy()
+    samples = []
+    for p in planes:
+        nroots = (p.shape[0] // 64) * (p.shape[1] // 64)
+        samples.append(sorted({0, nroots // 2, nroots - 1}))
+    enc = oracle.encode(planes, [1.5] * len(planes), roots=samples)
+    parts = [parity.restrict_to_roots(leaves, atoms, lo, i, samples[i], 64, planes[i].shape[1])
+             for i in range(len(planes))]
+    gl = np.concatenate([q[0] for q in parts])
+    ga = np.concatenate([q[1] for q in parts])
+    glo = np.concatenate([q[2] for q in parts])
+    gl["atom_off"] = np.concatenate([[0], np.cumsum(gl["n_atoms"].astype(np.int64))[:-1]]).astype(np.uint32)
+    parity.compare(enc, gl, ga, glo, planes, allow_flagged=True)
+    for i, p in enumerate(planes):
+        sel = leaves[leaves["plane"] == i]
+        assert int(np.sum(sel["b"].astype(np.int64) ** 2)) == p.size
