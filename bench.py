@@ -56,6 +56,56 @@ UNEVEN_WORKLOAD = ("64 synthetic RGB images (gradient scenes, a seed per channel
                    "RMSE tol 2, quadtree 64->4, k=b^2/4, DCT-II+Haar")
 
 
+REFINE_WORKLOAD = ("16 synthetic 512x512 gray images (piecewise scenes, seeds 0..15), MP support fixed at RMSE "
+                   "tol 4 on 8x8..32x32 leaves, 50 Adam steps (lr 0.25) of SSIM ascent on the FP32 coefficients "
+                   "through the hand-written synthesis + 11x11 Gaussian SSIM backward")
+
+
+def run_refine(args):
+    """Coefficient refinement: one step = one Adam step over all 16 planes."""
+    import torch
+    from paper_2605_09190_gb300 import aqmp, build_lib, refine, synthetic
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local if world > 1 else 0)
+    dist_init("nccl")
+    build_lib.build()
+    imgs = [synthetic.piecewise_scene(512, 512, seed=s) for s in range(16)]
+    code = aqmp.aqmp_encode_planes([torch.from_numpy(i).cuda() for i in imgs], 4.0, min_block=8, max_block=32)
+    refs = [(p, torch.from_numpy(i.astype(np.float32)).cuda()) for p, i in enumerate(imgs)]
+    _, alpha0 = aqmp.aqmp_device_atoms(code)
+    alpha = alpha0.clone().requires_grad_(True)
+    opt = torch.optim.Adam([alpha], lr=0.25)
+    stream = torch.cuda.current_stream()
+    hist, ms = [], []
+    total_steps = args.warmup + args.steps
+    for it in range(total_steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        opt.zero_grad(set_to_none=True)
+        s = refine.synthesis_ssim(alpha, code, refs)
+        (-s).backward()
+        opt.step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        hist.append(float(s.detach()))
+        if it >= args.warmup:
+            ms.append(e0.elapsed_time(e1))
+    with torch.no_grad():
+        final = float(refine.synthesis_ssim(alpha, code, refs))
+    step_s = max_over_ranks(sum(ms) / 1e3 / len(ms), device="cuda")
+    if rank == 0:
+        st = code.stats()
+        print(json.dumps({"metric": "coefficient refinement Adam steps/s", "value": world / step_s,
+                          "unit": "steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": 1e3 * step_s, "higher_is_better": True, "scaling": "weak",
+                          "vs_baseline": None, "dtype": "f32 synthesis, f64 SSIM statistics", "data": "synthetic",
+                          "config": {"workload": REFINE_WORKLOAD, "planes": 16, "coefficients": int(st["n_atoms"]),
+                                     "leaves": int(st["n_leaves"])},
+                          "ssim_plain_mp": hist[0], "ssim_refined": final, "ssim_gain": final - hist[0],
+                          "adam_steps": total_steps}))
+    return 0
+
+
 def run_uneven(args):
     """The 64-image uneven batch: one step encodes all 192 planes at once."""
     import torch
@@ -444,13 +494,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["sweep512", "uneven64"], default="sweep512",
-                    help="sweep512: the 512x512 tolerance sweep (default); uneven64: 64 uneven RGB images")
+    ap.add_argument("--workload", choices=["sweep512", "uneven64", "refine16"], default="sweep512",
+                    help="sweep512: the 512x512 tolerance sweep (default); uneven64: 64 uneven RGB images; "
+                         "refine16: coefficient refinement on 16 images (steps = Adam steps)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "uneven64":
         return run_uneven(args)
+    if args.workload == "refine16":
+        return run_refine(args)
     return run_ours(args)
 
 

@@ -160,6 +160,38 @@ int aqmp_decode(const aqmp_code *code, int plane, float *out, int64_t out_pitch,
 
 void aqmp_code_free(aqmp_code *code);
 
+/* ---- Differentiable refinement of the coefficients on a fixed support ----
+ * The support (leaves and atom indices) of an encode is held fixed; the
+ * coefficients become variables of the synthesis of Algorithm 3 and of the
+ * SSIM of Section 3, so that they can be refined by gradient descent.  These
+ * calls work on device memory only, in the code's device atom order
+ * (aqmp_code_device), and enqueue on `stream` without synchronising. */
+
+/* Device views of an encode: leaf and atom arrays in emission order (the
+ * order the coefficient vectors below follow), and their counts. */
+int aqmp_code_device(const aqmp_code *code, const aqmp_leaf **leaves, const aqmp_atom **atoms,
+                     uint64_t *n_leaves, uint64_t *n_atoms);
+
+/* Synthesis (Algorithm 3) of one plane with caller coefficients: out[y][x]
+ * = sum over the plane's leaves of sum_t alpha[t] phi_{j_t}, where alpha has
+ * n_atoms entries (FP32); out is h x w with `out_pitch` elements per row. */
+int aqmp_synth_forward(const aqmp_code *code, int plane, const float *alpha, float *out,
+                       int64_t out_pitch, void *stream);
+
+/* Its adjoint: grad_alpha[t] = <grad_out restricted to the atom's leaf,
+ * phi_{j_t}> for the atoms of `plane` (other entries are left untouched). */
+int aqmp_synth_backward(const aqmp_code *code, int plane, const float *grad_out, int64_t pitch,
+                        float *grad_alpha, void *stream);
+
+/* Mean SSIM (Section 3; K1 = 0.01, K2 = 0.03, L = 255, 11x11 Gaussian
+ * window of sigma 1.5, valid region) of `y` against the reference `x`, both
+ * h x w FP32 images with `pitch` elements per row, h, w >= 11.  Window
+ * statistics are accumulated in FP64.  *ssim (device, FP64) receives the
+ * mean; with grad_y != NULL, grad_y (h x w, pitch) receives
+ * grad_scale * d(mean SSIM)/dy. */
+int aqmp_ssim(const float *x, const float *y, int h, int w, int64_t pitch, double *ssim,
+              float *grad_y, double grad_scale, void *stream);
+
 /* The initial correlation of Section 2.2 step (b) for a batch of L blocks
  * of side b: c[l][j] = <y_l, phi_j> for every atom j, with y_l the
  * column-major unravel of block l (Appendix A).  `blocks` is device memory

@@ -317,11 +317,14 @@ def gaussian_window(size: int = 11, sigma: float = 1.5) -> np.ndarray:
 
 
 def ssim(recon: np.ndarray, ref: np.ndarray, L: float = 255.0, K1: float = 0.01,
-         K2: float = 0.03, size: int = 11, sigma: float = 1.5) -> float:
+         K2: float = 0.03, size: int = 11, sigma: float = 1.5, clip: bool = True) -> float:
     """Mean SSIM (Section 3 equation) over the valid region of an 11x11
-    Gaussian window; the reconstruction is clipped to [0, 255] first."""
+    Gaussian window; the reconstruction is clipped to [0, 255] first unless
+    `clip` is False (the differentiable refinement's loss)."""
     x = np.asarray(ref, np.float64)
-    y = np.clip(np.asarray(recon, np.float64), 0.0, 255.0)
+    y = np.asarray(recon, np.float64)
+    if clip:
+        y = np.clip(y, 0.0, 255.0)
     w = gaussian_window(size, sigma)
     H, W = x.shape
     oh, ow = H - size + 1, W - size + 1

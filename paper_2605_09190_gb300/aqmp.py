@@ -62,7 +62,8 @@ ATOM_DTYPE = np.dtype([("j", np.uint32), ("alpha", np.float32)])
 EXPORTS = ["aqmp_params_default", "aqmp_encode_planes", "aqmp_encode", "aqmp_code_stats", "aqmp_code_copy",
            "aqmp_decode", "aqmp_code_free", "aqmp_correlate", "aqmp_num_atoms", "aqmp_last_error",
            "aqmp_version", "aqmp_profile_enable", "aqmp_profile_reset", "aqmp_profile_read",
-           "aqmp_correlate_noalloc", "aqmp_selftest_wait"]
+           "aqmp_correlate_noalloc", "aqmp_selftest_wait", "aqmp_code_device", "aqmp_synth_forward",
+           "aqmp_synth_backward", "aqmp_ssim"]
 
 
 class aqmp_kernel_time(ctypes.Structure):
@@ -96,6 +97,11 @@ def load_library(path: str | None = None):
         lib.aqmp_correlate.argtypes = [I, I, V, I64, V, I, V]
         lib.aqmp_correlate_noalloc.argtypes = [I, I, V, I64, V, V]
         lib.aqmp_selftest_wait.argtypes = [I, V]
+        U64P = ctypes.POINTER(ctypes.c_uint64)
+        lib.aqmp_code_device.argtypes = [V, ctypes.POINTER(V), ctypes.POINTER(V), U64P, U64P]
+        lib.aqmp_synth_forward.argtypes = [V, I, V, V, I64, V]
+        lib.aqmp_synth_backward.argtypes = [V, I, V, I64, V, V]
+        lib.aqmp_ssim.argtypes = [V, V, I, I, I64, V, V, ctypes.c_double, V]
         lib.aqmp_num_atoms.argtypes = [I, I]
         lib.aqmp_last_error.restype = ctypes.c_char_p
         lib.aqmp_version.restype = ctypes.c_char_p
@@ -283,3 +289,65 @@ def aqmp_selftest_wait(limit_ms: int = 50, stream=None) -> int:
     """Run the bounded-wait check; returns the library's status code
     (AQMP_E_TIMEOUT, -7, is the expected outcome)."""
     return load_library().aqmp_selftest_wait(int(limit_ms), _stream_handle(stream))
+
+
+def aqmp_code_device(code: Code):
+    """(leaf ptr, atom ptr, n_leaves, n_atoms): device arrays in emission order."""
+    lv, at = ctypes.c_void_p(), ctypes.c_void_p()
+    nl, na = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(load_library().aqmp_code_device(code.handle, ctypes.byref(lv), ctypes.byref(at), ctypes.byref(nl),
+                                           ctypes.byref(na)))
+    return lv.value, at.value, nl.value, na.value
+
+
+class _DeviceArray:
+    """Zero-copy view of library device memory for torch.as_tensor."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": shape, "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 3}
+
+
+def aqmp_device_atoms(code: Code):
+    """The code's atoms in emission order as new CUDA tensors
+    (j: int64, alpha: float32)."""
+    import torch
+    _, at, _, na = aqmp_code_device(code)
+    if na == 0:
+        return (torch.zeros(0, dtype=torch.int64, device="cuda"), torch.zeros(0, dtype=torch.float32, device="cuda"))
+    raw = torch.as_tensor(_DeviceArray(at, (na, 2), "<i4"), device="cuda").clone()
+    return raw[:, 0].to(torch.int64), raw[:, 1].contiguous().view(torch.float32).clone()
+
+
+def aqmp_device_leaves(code: Code):
+    """The code's leaves in emission order as a host structured array."""
+    import torch
+    lv, _, nl, _ = aqmp_code_device(code)
+    if nl == 0:
+        return np.zeros(0, LEAF_DTYPE)
+    raw = torch.as_tensor(_DeviceArray(lv, (nl, LEAF_DTYPE.itemsize), "|u1"), device="cuda").cpu().numpy()
+    return raw.view(LEAF_DTYPE).reshape(-1)
+
+
+def aqmp_synth_forward(code: Code, plane: int, alpha, out, stream=None):
+    _check(load_library().aqmp_synth_forward(code.handle, plane, ctypes.c_void_p(alpha.data_ptr()),
+                                             ctypes.c_void_p(out.data_ptr()), out.stride(0), _stream_handle(stream)))
+    return out
+
+
+def aqmp_synth_backward(code: Code, plane: int, grad_out, grad_alpha, stream=None):
+    _check(load_library().aqmp_synth_backward(code.handle, plane, ctypes.c_void_p(grad_out.data_ptr()),
+                                              grad_out.stride(0), ctypes.c_void_p(grad_alpha.data_ptr()),
+                                              _stream_handle(stream)))
+    return grad_alpha
+
+
+def aqmp_ssim(x, y, ssim_out, grad_y=None, grad_scale: float = 1.0, stream=None):
+    """Mean SSIM of y against x (CUDA float32 images) into ssim_out (a CUDA
+    float64 scalar tensor); with grad_y, also grad_scale * dSSIM/dy."""
+    h, w = x.shape
+    _check(load_library().aqmp_ssim(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), h, w, x.stride(0),
+                                    ctypes.c_void_p(ssim_out.data_ptr()),
+                                    ctypes.c_void_p(grad_y.data_ptr()) if grad_y is not None else None,
+                                    float(grad_scale), _stream_handle(stream)))
+    return ssim_out

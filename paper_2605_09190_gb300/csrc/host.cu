@@ -206,7 +206,8 @@ struct Ctx {
     int cc_major = 0, cc_minor = 0;
     std::mutex mu;
     std::map<int, std::unique_ptr<Dict>> dicts;
-    DeviceBuf planes, staging, queues, Y, e0, c0, counters;
+    DeviceBuf planes, staging, queues, Y, e0, c0, counters, ssim_ws;
+    bool gauss_ready = false;
     Counters *host_ctr = nullptr;             // pinned
     PlaneDesc *host_planes = nullptr;         // pinned staging for plane descriptors
     int host_planes_cap = 0;
@@ -687,6 +688,91 @@ int aqmp_decode(const aqmp_code *code, int plane, float *out, int64_t out_pitch,
 }
 
 void aqmp_code_free(aqmp_code *code) { delete code; }
+
+int aqmp_code_device(const aqmp_code *code, const aqmp_leaf **leaves, const aqmp_atom **atoms, uint64_t *n_leaves,
+                     uint64_t *n_atoms) {
+    if (!code || !leaves || !atoms || !n_leaves || !n_atoms) return fail(AQMP_E_ARG, "NULL argument");
+    *leaves = reinterpret_cast<const aqmp_leaf *>(code->leaves);
+    *atoms = reinterpret_cast<const aqmp_atom *>(code->atoms);
+    *n_leaves = code->n_leaves;
+    *n_atoms = code->n_atoms;
+    return AQMP_OK;
+}
+
+// Basis tables of every side a code uses, for the synthesis kernels.
+static int code_bases(Ctx *c, const aqmp_code *code, cudaStream_t st, DecodeArgs *a) {
+    *a = DecodeArgs{};
+    a->nf = num_families(code->dict_id);
+    a->single_family = 0;
+    for (int b = code->min_block; b <= code->max_block; b *= 2) {
+        Dict *d;
+        int rc = get_dict(c, b, code->dict_id, st, &d);
+        if (rc) return rc;
+        a->basis[ilog2(b)] = d->d.basis;
+    }
+    return AQMP_OK;
+}
+
+int aqmp_synth_forward(const aqmp_code *code, int plane, const float *alpha, float *out, int64_t out_pitch,
+                       void *stream) {
+    g_last_error.clear();
+    if (!code || !alpha || !out || plane < 0 || plane >= (int)code->shapes.size()) return fail(AQMP_E_ARG, "bad argument");
+    if (out_pitch < code->shapes[plane].second) return fail(AQMP_E_ARG, "out_pitch below width");
+    Ctx *c;
+    int rc;
+    if ((rc = get_ctx(&c))) return rc;
+    std::lock_guard<std::mutex> lock(c->mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    DecodeArgs bases;
+    if ((rc = code_bases(c, code, st, &bases))) return rc;
+    CK(g_prof.run(kname("synth_fwd", code->max_block), st, [&] {
+        return launch_synth_forward(code->leaves, code->n_leaves, code->atoms, alpha, (uint32_t)plane, out,
+                                    out_pitch, bases, c->num_sms, st);
+    }));
+    return AQMP_OK;
+}
+
+int aqmp_synth_backward(const aqmp_code *code, int plane, const float *grad_out, int64_t pitch, float *grad_alpha,
+                        void *stream) {
+    g_last_error.clear();
+    if (!code || !grad_out || !grad_alpha || plane < 0 || plane >= (int)code->shapes.size())
+        return fail(AQMP_E_ARG, "bad argument");
+    if (pitch < code->shapes[plane].second) return fail(AQMP_E_ARG, "pitch below width");
+    Ctx *c;
+    int rc;
+    if ((rc = get_ctx(&c))) return rc;
+    std::lock_guard<std::mutex> lock(c->mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    DecodeArgs bases;
+    if ((rc = code_bases(c, code, st, &bases))) return rc;
+    CK(g_prof.run(kname("synth_bwd", code->max_block), st, [&] {
+        return launch_synth_backward(code->leaves, code->n_leaves, code->atoms, (uint32_t)plane, grad_out, pitch,
+                                     grad_alpha, bases, code->max_block, c->num_sms, st);
+    }));
+    return AQMP_OK;
+}
+
+int aqmp_ssim(const float *x, const float *y, int h, int w, int64_t pitch, double *ssim, float *grad_y,
+              double grad_scale, void *stream) {
+    g_last_error.clear();
+    if (!x || !y || !ssim || h < 11 || w < 11 || pitch < w) return fail(AQMP_E_ARG, "bad argument");
+    Ctx *c;
+    int rc;
+    if ((rc = get_ctx(&c))) return rc;
+    std::lock_guard<std::mutex> lock(c->mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!c->gauss_ready) {
+        CK(upload_gauss11(st));
+        c->gauss_ready = true;
+    }
+    const size_t hw = (size_t)h * (w - 10), win = (size_t)(h - 10) * (w - 10);
+    if ((rc = c->ssim_ws.reserve(sizeof(double) * (5 * hw + 3 * win + 3 * hw)))) return rc;
+    double *H = (double *)c->ssim_ws.p, *P = H + 5 * hw, *V = P + 3 * win;
+    CK(cudaMemsetAsync(ssim, 0, sizeof(double), st));
+    CK(g_prof.run(grad_y ? "ssim_fwd_bwd" : "ssim_fwd", st,
+                  [&] { return launch_ssim(x, y, h, w, pitch, H, P, V, ssim, grad_y, grad_scale, c->num_sms, st); }));
+    return AQMP_OK;
+}
 
 int aqmp_selftest_wait(int limit_ms, void *stream) {
     g_last_error.clear();

@@ -84,6 +84,17 @@ struct DecodeArgs {
 };
 cudaError_t launch_decode(const DecodeArgs &a, int num_sms, cudaStream_t st);
 
+// Refinement on a fixed support (diff.cu).
+cudaError_t upload_gauss11(cudaStream_t st);
+cudaError_t launch_synth_forward(const LeafRec *leaves, unsigned long long n_leaves, const AtomRec *atoms,
+                                 const float *alpha, uint32_t plane, float *out, long long pitch,
+                                 const DecodeArgs &bases, int num_sms, cudaStream_t st);
+cudaError_t launch_synth_backward(const LeafRec *leaves, unsigned long long n_leaves, const AtomRec *atoms,
+                                  uint32_t plane, const float *grad, long long pitch, float *grad_alpha,
+                                  const DecodeArgs &bases, int max_side, int num_sms, cudaStream_t st);
+cudaError_t launch_ssim(const float *x, const float *y, int h, int w, long long pitch, double *H, double *P,
+                        double *V, double *sum, float *grad, double gscale, int num_sms, cudaStream_t st);
+
 // Level-0 queue from the plane descriptors (gather.cu).
 cudaError_t launch_seed_roots(const PlaneDesc *planes, int n_planes, int max_block,
                               unsigned total_roots, QueueEntry *queue, unsigned *count,

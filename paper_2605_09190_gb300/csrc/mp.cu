@@ -119,17 +119,21 @@ __device__ __forceinline__ uint32_t top2_index(const Top2 &t) { return 0xffffu -
 __device__ __forceinline__ bool top2_negative(const Top2 &t) { return ((uint32_t)t.P & 1u) != 0u; }
 __device__ __forceinline__ float top2_amax(const Top2 &t) { return __uint_as_float((uint32_t)(t.P >> 32)); }
 
-// Warp-wide top-2 with three redux.sync maxima: the largest |hi| key, the
-// lowest index among the lanes holding it, and the second key (the other
-// lanes' tops and the winner's own second).  Every lane gets the result.
+// Warp-wide top-2 from redux.sync maxima.  After the largest |hi| key, the
+// lowest index among the lanes holding it and the second key are reduced
+// side by side: when two lanes hold the largest key it is also the second
+// (ballot count); otherwise the second is the largest of the other lanes'
+// tops and the holder's own second.  Every lane gets the result.
 __device__ __forceinline__ Top2 warp_top2(const Top2 &t) {
     const uint32_t hk = (uint32_t)(t.P >> 32);
-    const uint32_t mhk = __reduce_max_sync(0xffffffffu, hk);
     const uint32_t low = (uint32_t)t.P;
-    const uint32_t mlow = __reduce_max_sync(0xffffffffu, hk == mhk ? low : 0u);
-    const bool winner = hk == mhk && low == mlow;
-    const uint32_t mk2 = __reduce_max_sync(0xffffffffu, winner ? t.k2 : hk);
-    const unsigned who = __ballot_sync(0xffffffffu, winner);
+    const uint32_t mhk = __reduce_max_sync(0xffffffffu, hk);
+    const bool holds = hk == mhk;
+    const unsigned holders = __ballot_sync(0xffffffffu, holds);
+    const uint32_t mlow = __reduce_max_sync(0xffffffffu, holds ? low : 0u);
+    const uint32_t k2c = __reduce_max_sync(0xffffffffu, holds ? t.k2 : hk);
+    const uint32_t mk2 = __popc(holders) > 1 ? mhk : k2c;
+    const unsigned who = __ballot_sync(0xffffffffu, holds && low == mlow);
     const float lo1 = __shfl_sync(0xffffffffu, t.lo1, __ffs(who) - 1);
     return Top2{((unsigned long long)mhk << 32) | mlow, mk2, lo1};
 }
