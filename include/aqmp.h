@@ -167,7 +167,7 @@ void aqmp_code_free(aqmp_code *code);
  * calls work on device memory only, in the code's device atom order
  * (aqmp_code_device), and enqueue on `stream` without synchronising. */
 
-/* Device views of an encode: leaf and atom arrays in emission order (the
+/* Device views of an encode: leaf and atom arrays in canonical order (the
  * order the coefficient vectors below follow), and their counts. */
 int aqmp_code_device(const aqmp_code *code, const aqmp_leaf **leaves, const aqmp_atom **atoms,
                      uint64_t *n_leaves, uint64_t *n_atoms);

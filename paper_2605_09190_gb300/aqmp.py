@@ -292,7 +292,7 @@ def aqmp_selftest_wait(limit_ms: int = 50, stream=None) -> int:
 
 
 def aqmp_code_device(code: Code):
-    """(leaf ptr, atom ptr, n_leaves, n_atoms): device arrays in emission order."""
+    """(leaf ptr, atom ptr, n_leaves, n_atoms): device arrays in canonical order (as aqmp_code_copy)."""
     lv, at = ctypes.c_void_p(), ctypes.c_void_p()
     nl, na = ctypes.c_uint64(), ctypes.c_uint64()
     _check(load_library().aqmp_code_device(code.handle, ctypes.byref(lv), ctypes.byref(at), ctypes.byref(nl),
@@ -309,7 +309,7 @@ class _DeviceArray:
 
 
 def aqmp_device_atoms(code: Code):
-    """The code's atoms in emission order as new CUDA tensors
+    """The code's atoms in canonical order as new CUDA tensors
     (j: int64, alpha: float32)."""
     import torch
     _, at, _, na = aqmp_code_device(code)
@@ -320,7 +320,7 @@ def aqmp_device_atoms(code: Code):
 
 
 def aqmp_device_leaves(code: Code):
-    """The code's leaves in emission order as a host structured array."""
+    """The code's leaves in canonical order as a host structured array."""
     import torch
     lv, _, nl, _ = aqmp_code_device(code)
     if nl == 0:

@@ -85,6 +85,29 @@ __device__ __forceinline__ df fixed_to_df(long long A, long long B) {
     return df_add_float(x, __ll2float_rn(B) * 0x1p-48f);
 }
 
+// Map of min-block cells in the canonical order of the output list:
+// planes ascending, roots in raster order, then the Z-order (TL, TR, BL, BR
+// recursively) of the cell inside its root.  The leaves of a root tile it,
+// so the depth-first position of a leaf is that of its top-left cell.  The
+// pursuit kernels store slot + 1 of every emitted leaf at its cell.
+struct CellMap {
+    uint32_t *cell;                    // n_cells words, zeroed before the encode
+    unsigned long long n_cells;
+    int max_block, min_block, zbits;   // zbits = 2 log2(max_block / min_block)
+};
+
+// Cell index of the block at (y, x) of plane p, or ~0 when it lies outside.
+__device__ __forceinline__ unsigned long long cell_of(const CellMap &m, const PlaneDesc &p, uint32_t y, uint32_t x) {
+    if (y >= (uint32_t)p.h || x >= (uint32_t)p.w) return ~0ull;
+    const uint32_t mb = (uint32_t)m.max_block, nb = (uint32_t)m.min_block;
+    const unsigned long long root = (unsigned long long)p.root_off + (y / mb) * p.roots_x + x / mb;
+    const uint32_t cy = (y % mb) / nb, cx = (x % mb) / nb;
+    uint32_t z = 0;
+    for (int bit = m.zbits / 2 - 1; bit >= 0; --bit) z = (z << 2) | (((cy >> bit) & 1u) << 1) | ((cx >> bit) & 1u);
+    const unsigned long long c = (root << m.zbits) | z;
+    return c < m.n_cells ? c : ~0ull;
+}
+
 __device__ __forceinline__ void raise_error(Counters *ctr, unsigned code, unsigned info) {
     if (atomicCAS(&ctr->error, 0u, code) == 0u) ctr->error_info = info;
 }

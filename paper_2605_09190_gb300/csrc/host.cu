@@ -207,6 +207,7 @@ struct Ctx {
     std::mutex mu;
     std::map<int, std::unique_ptr<Dict>> dicts;
     DeviceBuf planes, staging, queues, Y, e0, c0, counters, ssim_ws;
+    DeviceBuf leaves_ws, atoms_ws, lo_ws, atom_leaf, cells, perm, new_off, order_status;   // emission -> canonical order
     bool gauss_ready = false;
     Counters *host_ctr = nullptr;             // pinned
     PlaneDesc *host_planes = nullptr;         // pinned staging for plane descriptors
@@ -443,8 +444,20 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
     if ((rc = c->Y.reserve(sizeof(__nv_bfloat16) * ymax))) return rc;
     if ((rc = c->e0.reserve(sizeof(uint32_t) * emax))) return rc;
     if ((rc = c->c0.reserve(sizeof(float2) * cmax))) return rc;
-    // outputs: allocated per call from the stream-ordered pool at their
-    // worst-case size and written by the kernels directly
+    // the pursuit kernels emit into the workspace; the ordering pass writes
+    // the outputs, allocated per call from the stream-ordered pool at their
+    // worst-case size
+    const int zbits = 2 * (ilog2(P.max_block) - ilog2(P.min_block));
+    const unsigned long long n_cells = roots << zbits;
+    if ((rc = c->leaves_ws.reserve(sizeof(LeafRec) * leaf_cap))) return rc;
+    if ((rc = c->atoms_ws.reserve(sizeof(AtomRec) * atom_cap))) return rc;
+    if ((rc = c->lo_ws.reserve(sizeof(float) * atom_cap))) return rc;
+    if ((rc = c->cells.reserve(sizeof(uint32_t) * n_cells))) return rc;
+    if ((rc = c->perm.reserve(sizeof(uint32_t) * leaf_cap))) return rc;
+    if ((rc = c->new_off.reserve(sizeof(uint32_t) * leaf_cap))) return rc;
+    if ((rc = c->atom_leaf.reserve(sizeof(uint32_t) * atom_cap))) return rc;
+    const unsigned long long status_words = order_status_words(n_cells, leaf_cap);
+    if ((rc = c->order_status.reserve(sizeof(unsigned long long) * status_words))) return rc;
     auto code = std::make_unique<aqmp_code>();
     code->device = c->device;
     CK(cudaMallocAsync((void **)&code->leaves, sizeof(LeafRec) * std::max<unsigned long long>(1, leaf_cap), st));
@@ -487,6 +500,9 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
     CK(cudaMemcpyAsync(c->planes.p, c->host_planes, sizeof(PlaneDesc) * n_planes, cudaMemcpyHostToDevice, st));
     Counters *ctr = (Counters *)c->counters.p;
     CK(cudaMemsetAsync(ctr, 0, sizeof(Counters), st));
+    CK(cudaMemsetAsync(c->cells.p, 0, sizeof(uint32_t) * n_cells, st));
+    CK(cudaMemsetAsync(c->order_status.p, 0, sizeof(unsigned long long) * status_words, st));
+    const CellMap cells{(uint32_t *)c->cells.p, n_cells, P.max_block, P.min_block, zbits};
     QueueEntry *q = (QueueEntry *)c->queues.p;
     CK(launch_seed_roots((const PlaneDesc *)c->planes.p, n_planes, P.max_block, (unsigned)roots, q,
                          &ctr->queue_count[0], st));
@@ -538,16 +554,42 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
         ma.planes = (const PlaneDesc *)c->planes.p;
         ma.W = d.W;
         ma.WT = d.WT;
-        ma.leaves = code->leaves;
+        ma.leaves = (LeafRec *)c->leaves_ws.p;
         ma.leaf_cap = leaf_cap;
-        ma.atoms = code->atoms;
-        ma.alpha_lo = code->alpha_lo;
+        ma.atoms = (AtomRec *)c->atoms_ws.p;
+        ma.alpha_lo = (float *)c->lo_ws.p;
+        ma.atom_leaf = (uint32_t *)c->atom_leaf.p;
         ma.atom_cap = atom_cap;
+        ma.cells = cells;
         ma.ctr = ctr;
         const bool exact = P.precision == AQMP_PREC_EXACT;
         CK(g_prof.run(kname(exact ? "mp" : "mp_fp32", b), st,
                       [&] { return launch_mp(ma, d.nf, exact, c->num_sms, st); }));
     }
+
+    // canonical order of the output list: plane, root (raster), depth-first
+    OrderArgs oa{};
+    oa.cells = cells;
+    oa.leaves_in = (const LeafRec *)c->leaves_ws.p;
+    oa.atoms_in = (const AtomRec *)c->atoms_ws.p;
+    oa.lo_in = (const float *)c->lo_ws.p;
+    oa.atom_leaf = (const uint32_t *)c->atom_leaf.p;
+    oa.n_leaves = &ctr->n_leaves;
+    oa.n_atoms = &ctr->n_atoms;
+    oa.new_off = (uint32_t *)c->new_off.p;
+    oa.leaf_cap = leaf_cap;
+    oa.atom_cap = atom_cap;
+    oa.perm = (uint32_t *)c->perm.p;
+    oa.status = (unsigned long long *)c->order_status.p;
+    oa.leaves_out = code->leaves;
+    oa.atoms_out = code->atoms;
+    oa.lo_out = code->alpha_lo;
+    oa.ctr = ctr;
+    oa.limit_ns = 2000000000ull;
+    CK(g_prof.run("order_rank", st, [&] { return launch_order_phase(oa, 0, c->num_sms, st); }));
+    CK(g_prof.run("order_offsets", st, [&] { return launch_order_phase(oa, 1, c->num_sms, st); }));
+    CK(g_prof.run("order_copy", st, [&] { return launch_order_phase(oa, 2, c->num_sms, st); }));
+
     CK(cudaMemcpyAsync(c->host_ctr, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     {
@@ -601,42 +643,11 @@ int aqmp_code_stats(const aqmp_code *code, aqmp_stats *stats) {
 
 int aqmp_code_copy(const aqmp_code *code, aqmp_leaf *leaves, aqmp_atom *atoms, float *alpha_lo) {
     if (!code || (!leaves && code->n_leaves) || (!atoms && code->n_atoms)) return fail(AQMP_E_ARG, "NULL argument");
-    std::vector<LeafRec> L(code->n_leaves);
-    std::vector<AtomRec> A(code->n_atoms);
-    std::vector<float> lo(code->n_atoms);
-    if (code->n_leaves) CK(cudaMemcpy(L.data(), code->leaves, sizeof(LeafRec) * L.size(), cudaMemcpyDeviceToHost));
+    // the device arrays are already in canonical order (written so by the encode)
+    if (code->n_leaves) CK(cudaMemcpy(leaves, code->leaves, sizeof(LeafRec) * code->n_leaves, cudaMemcpyDeviceToHost));
     if (code->n_atoms) {
-        CK(cudaMemcpy(A.data(), code->atoms, sizeof(AtomRec) * A.size(), cudaMemcpyDeviceToHost));
-        CK(cudaMemcpy(lo.data(), code->alpha_lo, sizeof(float) * lo.size(), cudaMemcpyDeviceToHost));
-    }
-    // canonical order: plane, root (row-major), then depth-first TL, TR, BL, BR
-    // = Z-order of the leaf's corner inside its root.  One 64-bit key per
-    // leaf (plane: 12 bits, root: 28 bits, Z-order cell: 24 bits), sorted once.
-    const unsigned mb = (unsigned)code->max_block, nb = (unsigned)code->min_block;
-    std::vector<std::pair<unsigned long long, unsigned>> keyed(L.size());
-    for (size_t i = 0; i < L.size(); ++i) {
-        const LeafRec &r = L[i];
-        const unsigned long long rx = (unsigned long long)code->shapes[r.plane].second / mb;
-        const unsigned long long root = (r.y / mb) * rx + (r.x / mb);
-        const unsigned cy = (r.y % mb) / nb, cx = (r.x % mb) / nb;
-        unsigned long long z = 0;
-        for (int bit = 11; bit >= 0; --bit) z = (z << 2) | (((cy >> bit) & 1u) << 1) | ((cx >> bit) & 1u);
-        keyed[i] = {((unsigned long long)r.plane << 52) | (root << 24) | z, (unsigned)i};
-    }
-    std::sort(keyed.begin(), keyed.end());
-    std::vector<size_t> order(L.size());
-    for (size_t i = 0; i < L.size(); ++i) order[i] = keyed[i].second;
-    unsigned long long off = 0;
-    for (size_t i = 0; i < order.size(); ++i) {
-        LeafRec r = L[order[i]];
-        for (unsigned t = 0; t < r.n_atoms; ++t) {
-            atoms[off + t].j = A[r.atom_off + t].j;
-            atoms[off + t].alpha = A[r.atom_off + t].alpha;
-            if (alpha_lo) alpha_lo[off + t] = lo[r.atom_off + t];
-        }
-        r.atom_off = (uint32_t)off;
-        off += r.n_atoms;
-        std::memcpy(&leaves[i], &r, sizeof r);
+        CK(cudaMemcpy(atoms, code->atoms, sizeof(AtomRec) * code->n_atoms, cudaMemcpyDeviceToHost));
+        if (alpha_lo) CK(cudaMemcpy(alpha_lo, code->alpha_lo, sizeof(float) * code->n_atoms, cudaMemcpyDeviceToHost));
     }
     return AQMP_OK;
 }

@@ -21,7 +21,9 @@ struct MPArgs {
     unsigned long long leaf_cap;
     AtomRec *atoms;
     float *alpha_lo;
+    uint32_t *atom_leaf;         // emission slot of the leaf owning each atom
     unsigned long long atom_cap;
+    CellMap cells;               // emitted leaves are marked here
     Counters *ctr;
 };
 cudaError_t launch_mp(const MPArgs &a, int nf, bool double_float, int num_sms, cudaStream_t st);
@@ -99,6 +101,33 @@ cudaError_t launch_ssim(const float *x, const float *y, int h, int w, long long 
 cudaError_t launch_seed_roots(const PlaneDesc *planes, int n_planes, int max_block,
                               unsigned total_roots, QueueEntry *queue, unsigned *count,
                               cudaStream_t st);
+
+// Canonical (depth-first) order of the emitted leaves (order.cu), three
+// launches over the cell map the pursuit kernels filled: phase 0 ranks the
+// leaves (perm[rank] = slot), phase 1 writes the ordered records and each
+// slot's new atom offset, phase 2 moves every atom.  Phases 0 and 1 are
+// single-pass scans with decoupled look-back over tiles claimed in launch
+// order; `status` (order_status_words(n_cells, leaf_cap) 64-bit words) must
+// be zero before phase 0.
+struct OrderArgs {
+    CellMap cells;
+    const LeafRec *leaves_in;
+    const AtomRec *atoms_in;
+    const float *lo_in;
+    const uint32_t *atom_leaf;         // slot of each emitted atom's leaf
+    const unsigned long long *n_leaves, *n_atoms;
+    unsigned long long leaf_cap, atom_cap;
+    uint32_t *perm;                    // leaf_cap words
+    uint32_t *new_off;                 // leaf_cap words: new atom offset by slot
+    unsigned long long *status;
+    LeafRec *leaves_out;
+    AtomRec *atoms_out;
+    float *lo_out;
+    Counters *ctr;
+    unsigned long long limit_ns;       // bound on every look-back wait
+};
+unsigned long long order_status_words(unsigned long long n_cells, unsigned long long leaf_cap);
+cudaError_t launch_order_phase(const OrderArgs &a, int phase, int num_sms, cudaStream_t st);
 
 // Table construction on the device (tables.cu) from the FP64 1-D bases
 // basis_dev = [2][b][b] (DCT, Haar); fam0 selects the family of a

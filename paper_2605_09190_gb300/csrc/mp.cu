@@ -16,8 +16,9 @@
 //   (a6) converged iff E < eps^2 (strict), tested before every step; the
 //        budget ends the pursuit after k steps.
 // Then (a7) a converged leaf, or any leaf at the smallest side, is emitted
-// with its steps; any other leaf pushes its four quadrants (TL, TR, BL, BR)
-// onto the next level's queue.  Leaves are handed out through a device
+// with its steps (and marked in the cell map that restores the depth-first
+// order); any other leaf pushes its four quadrants (TL, TR, BL, BR) onto the
+// next level's queue.  Leaves are handed out through a device
 // counter, so a group that finishes a short pursuit takes the next leaf.
 //
 // Argmax cost.  Each thread keeps, per atom family, the top two |hi| keys of
@@ -489,7 +490,7 @@ mp_kernel(MPArgs a) {
             atomicAdd(&a.ctr->iterations[lv.level], (unsigned long long)t);
         }
         const bool emit = conv || lv.is_last;
-        uint32_t off = 0;
+        uint32_t off = 0, eslot = 0;
         if (emit) {
             if (lane == 0) {
                 const unsigned long long slot = atomicAdd(&a.ctr->n_leaves, 1ull);
@@ -511,6 +512,9 @@ mp_kernel(MPArgs a) {
                     rec.reserved = 0;
                     a.leaves[slot] = rec;
                     off = (uint32_t)o;
+                    eslot = (uint32_t)slot;
+                    const unsigned long long cell = cell_of(a.cells, a.planes[qe.plane], qe.y, qe.x);
+                    if (cell != ~0ull) a.cells.cell[cell] = (uint32_t)slot + 1u;
                     if (flags) atomicAdd(&a.ctr->near_tie_leaves, 1ull);
                 }
             }
@@ -529,18 +533,24 @@ mp_kernel(MPArgs a) {
         }
         if (emit) {
             if (T > 32) {
-                if (lane == 0) sMisc[0] = off;
+                if (lane == 0) {
+                    sMisc[0] = off;
+                    sMisc[1] = eslot;
+                }
                 __syncthreads();
                 off = sMisc[0];
+                eslot = sMisc[1];
             } else {
                 __syncwarp();
                 off = __shfl_sync(0xffffffffu, off, 0);
+                eslot = __shfl_sync(0xffffffffu, eslot, 0);
             }
             if (off != kNone) {
                 for (int i = lane; i < t; i += T) {
                     const StepRec st = steps[i];
                     a.atoms[off + i] = AtomRec{st.j, st.hi};
                     a.alpha_lo[off + i] = st.lo;
+                    a.atom_leaf[off + i] = eslot;
                 }
             }
         }

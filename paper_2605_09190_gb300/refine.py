@@ -18,7 +18,7 @@ from . import aqmp
 
 class SynthesisSSIM(torch.autograd.Function):
     """mean over planes of SSIM(ref_p, synthesis_p(alpha)); alpha is the
-    code's coefficient vector in emission order (float32, CUDA)."""
+    code's coefficient vector in canonical order (float32, CUDA)."""
 
     @staticmethod
     def forward(ctx, alpha, code, refs):

@@ -193,3 +193,47 @@ def test_uneven_rgb_batch_in_one_call(lib):
     for i, p in enumerate(planes):
         sel = leaves[leaves["plane"] == i]
         assert int(np.sum(sel["b"].astype(np.int64) ** 2)) == p.size
+
+
+def _dfs_keys(leaves, shapes, max_block, min_block):
+    """(plane, root in raster order, Z-order cell inside the root) of every
+    leaf: strictly increasing along the canonical depth-first order."""
+    levels = int(np.log2(max_block // min_block))
+    keys = []
+    for L in leaves:
+        p, y, x = int(L["plane"]), int(L["y"]), int(L["x"])
+        root = (y // max_block) * (shapes[p][1] // max_block) + x // max_block
+        cy, cx = (y % max_block) // min_block, (x % max_block) // min_block
+        z = 0
+        for bit in range(levels - 1, -1, -1):
+            z = (z << 2) | (((cy >> bit) & 1) << 1) | ((cx >> bit) & 1)
+        keys.append((p, root, z))
+    return keys
+
+
+@pytest.mark.parametrize("min_block,max_block", [(4, 64), (8, 32), (16, 16), (4, 8)])
+def test_device_arrays_are_in_canonical_order(lib, min_block, max_block):
+    """The encode writes its leaf and atom arrays in the canonical order on the
+    device: the device views equal the host copy, leaf keys increase
+    depth-first, atom offsets are the running sum of the step counts and the
+    leaves tile every plane."""
+    batch = synthetic.uneven_rgb_batch(3, seed=11, wmin=64, wmax=192, hmin=64, hmax=128)
+    planes = [p for (_, _, chans) in batch for p in chans] + [synthetic.uniform_plane(64, 128, 77)]
+    tols = [0.5 + 0.5 * (i % 4) for i in range(len(planes))]
+    code = lib.aqmp_encode_planes([torch.from_numpy(p).cuda() for p in planes], tols,
+                                  min_block=min_block, max_block=max_block)
+    leaves, atoms, lo = code.copy()
+    dl = lib.aqmp_device_leaves(code)
+    dj, da = lib.aqmp_device_atoms(code)
+    np.testing.assert_array_equal(dl.view(np.uint8), leaves.view(np.uint8))
+    np.testing.assert_array_equal(dj.cpu().numpy(), atoms["j"].astype(np.int64))
+    np.testing.assert_array_equal(da.cpu().numpy().view(np.uint32), atoms["alpha"].view(np.uint32))
+    keys = _dfs_keys(leaves, [p.shape for p in planes], max_block, min_block)
+    assert all(a < b for a, b in zip(keys, keys[1:]))
+    offs = np.concatenate([[0], np.cumsum(leaves["n_atoms"].astype(np.int64))[:-1]])
+    np.testing.assert_array_equal(leaves["atom_off"].astype(np.int64), offs)
+    assert int(leaves["n_atoms"].astype(np.int64).sum()) == len(atoms)
+    for i, p in enumerate(planes):
+        sel = leaves[leaves["plane"] == i]
+        assert int(np.sum(sel["b"].astype(np.int64) ** 2)) == p.size
+    code.free()
