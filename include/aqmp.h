@@ -240,6 +240,76 @@ int aqmp_correlate_noalloc(int b, int dict_id, const uint8_t *blocks, int64_t L,
  * AQMP_OK would mean the wait was not bounded. */
 int aqmp_selftest_wait(int limit_ms, void *stream);
 
+/* ---- Codec stages around the encoder (Section 2.3 and Appendix A) ----
+ * Step (i) converts the channels of an image to RGB or YCbCr and codes each
+ * channel on its own; step (iii) applies a lossless coder (DEFLATE) to the
+ * MP output; the decoder reverses the three steps.  The paper fixes neither
+ * the YCbCr variant nor the layout of the MP output; this library's choices:
+ *  - YCbCr is the full-range JFIF matrix (ITU-T T.871) evaluated exactly in
+ *    integers, each coefficient rounded to 16 fractional bits, rounding half
+ *    up and clamping to [0, 255]; greys map to themselves.
+ *  - The bitstream (the input of the lossless stage) lists, per plane, the
+ *    leaves in canonical (depth-first) order.  A leaf's position is implied by
+ *    that order and by the leaf sizes, as in the paper's decoder (set_block
+ *    places blocks by the quadtree traversal order), so only sizes, step
+ *    counts, atom indices and FP32 coefficients are stored.  Little-endian:
+ *      "AQMP", u8 version = 1, u8 color, u8 dict_id, u8 0, u16 min_block,
+ *      u16 max_block, u32 n_planes; per plane u32 h, w, n_leaves, n_atoms;
+ *      then per plane: n_leaves u8 levels log2(max_block / b), n_leaves
+ *      LEB128 step counts, n_atoms u16 atom indices, n_atoms f32 alpha.
+ *  - DEFLATE itself is applied by the caller (the Python package uses zlib). */
+
+#define AQMP_COLOR_PLANES 0       /* channels coded as given */
+#define AQMP_COLOR_RGB    1       /* interleaved RGB, coded as R, G, B planes */
+#define AQMP_COLOR_YCBCR  2       /* interleaved RGB, coded as Y, Cb, Cr planes */
+
+/* Step (i) on the device: `img` is h x w x channels interleaved bytes with
+ * `pitch` bytes per row; `planes` receives `channels` byte planes of h rows
+ * of `plane_pitch` bytes, plane c starting at planes + c h plane_pitch.
+ * AQMP_COLOR_YCBCR needs channels == 3 and converts RGB to Y, Cb, Cr; the
+ * other modes copy the channels.  Both pointers are device memory; the
+ * call enqueues on `stream` and returns.  Errors: AQMP_E_ARG. */
+int aqmp_image_to_planes(const uint8_t *img, int h, int w, int channels, int64_t pitch, int color,
+                         uint8_t *planes, int64_t plane_pitch, void *stream);
+
+/* Decoder step (iii) on the device: `planes` holds `channels` decoded FP32
+ * planes (as aqmp_decode writes them; plane c at planes + c h plane_pitch),
+ * each value rounded to the nearest integer (ties to even) and clamped to
+ * [0, 255]; AQMP_COLOR_YCBCR then converts Y, Cb, Cr to RGB.  `img`
+ * receives h x w x channels interleaved bytes with `pitch` bytes per row.
+ * Device memory; enqueues on `stream`.  Errors: AQMP_E_ARG. */
+int aqmp_planes_to_image(const float *planes, int h, int w, int channels, int64_t plane_pitch, int color,
+                         uint8_t *img, int64_t pitch, void *stream);
+
+/* Size in bytes of the bitstream of `code` (host value). */
+int aqmp_bitstream_size(const aqmp_code *code, uint64_t *bytes);
+
+/* Writes the bitstream of `code` into the host buffer `buf` of `cap` bytes
+ * (at least aqmp_bitstream_size); *len receives the bytes written; `color`
+ * (AQMP_COLOR_*) is recorded for the decoder.  Errors: AQMP_E_ARG (NULL, or
+ * cap too small), AQMP_E_UNSUPPORTED (a plane larger than 2^32 - 1 px). */
+int aqmp_bitstream_write(const aqmp_code *code, int color, uint8_t *buf, uint64_t cap, uint64_t *len);
+
+/* Header of a bitstream. */
+typedef struct {
+    int      version, color, dict_id, n_planes, min_block, max_block;
+    uint64_t n_leaves, n_atoms;   /* totals over the planes */
+} aqmp_bitstream_info;
+
+/* Host-only parse of a bitstream: fills *info; when not NULL, `shapes`
+ * (2 n_planes ints: h, w per plane), `leaves` (n_leaves) and `atoms`
+ * (n_atoms) receive the planes' sizes and the leaves, in canonical order,
+ * with their positions recovered from the traversal order (converged, flags
+ * and the low coefficient words are not stored: zero).  Call once with NULL
+ * arrays to learn the counts.  Errors: AQMP_E_ARG (malformed stream). */
+int aqmp_bitstream_parse(const uint8_t *buf, uint64_t len, aqmp_bitstream_info *info, int *shapes,
+                         aqmp_leaf *leaves, aqmp_atom *atoms);
+
+/* A code object rebuilt from a bitstream (device arrays uploaded on the
+ * current device), ready for aqmp_decode.  Errors: as aqmp_bitstream_parse,
+ * AQMP_E_OOM, AQMP_E_CUDA. */
+int aqmp_code_from_bitstream(const uint8_t *buf, uint64_t len, aqmp_code **out);
+
 /* Number of atoms M of a dictionary at side b (2 b^2 or b^2), or < 0. */
 int aqmp_num_atoms(int b, int dict_id);
 

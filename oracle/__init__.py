@@ -344,3 +344,54 @@ def ssim(recon: np.ndarray, ref: np.ndarray, L: float = 255.0, K1: float = 0.01,
     C2 = (K2 * L) ** 2
     smap = ((2 * mx * my + C1) * (2 * cxy + C2)) / ((mx * mx + my * my + C1) * (vx + vy + C2))
     return float(smap.mean())
+
+
+# ---------------------------------------------------------------- codec stages
+# Section 2.3 step (i) converts an image's channels to RGB or YCbCr and codes
+# each channel on its own; the decoder's step (iii) converts back.  The
+# paper fixes no YCbCr variant.  Reading: the full-range JFIF matrix (ITU-T
+# T.871), Y = 0.299 R + 0.587 G + 0.114 B, Cb = 128 - 0.168736 R -
+# 0.331264 G + 0.5 B, Cr = 128 + 0.5 R - 0.418688 G - 0.081312 B, with the
+# inverse R = Y + 1.402 (Cr - 128), G = Y - 0.344136 (Cb - 128) -
+# 0.714136 (Cr - 128), B = Y + 1.772 (Cb - 128); every coefficient taken in
+# 16-bit fixed point (round(c 2^16); the two pairs that must cancel on greys
+# are rounded to sum to 2^15), the sum rounded half up and clamped to
+# [0, 255].  Integer arithmetic, so the definition is exact.  Decoded
+# planes are real-valued and are first rounded to the nearest integer, ties
+# to even, and clamped.
+
+_YCC_FWD = np.array([[19595, 38470, 7471],
+                     [-11058, -21710, 32768],
+                     [32768, -27439, -5329]], np.int64)
+_YCC_INV = np.array([[0, 91881],            # R: (Cb - 128, Cr - 128)
+                     [-22553, -46802],      # G
+                     [116130, 0]], np.int64)  # B
+
+
+def rgb_to_ycbcr(img: np.ndarray) -> np.ndarray:
+    """(h, w, 3) uint8 RGB -> (3, h, w) uint8 Y, Cb, Cr."""
+    rgb = np.asarray(img).astype(np.int64)
+    out = np.empty((3,) + rgb.shape[:2], np.int64)
+    for c in range(3):
+        acc = (_YCC_FWD[c, 0] * rgb[..., 0] + _YCC_FWD[c, 1] * rgb[..., 1]
+               + _YCC_FWD[c, 2] * rgb[..., 2] + 32768)
+        if c > 0:
+            acc = acc + (128 << 16)
+        out[c] = acc >> 16                      # floor: with + 2^15, half up
+    return np.clip(out, 0, 255).astype(np.uint8)
+
+
+def ycbcr_to_rgb(planes: np.ndarray) -> np.ndarray:
+    """(3, h, w) uint8 Y, Cb, Cr -> (h, w, 3) uint8 RGB."""
+    p = np.asarray(planes).astype(np.int64)
+    y, db, dr = p[0], p[1] - 128, p[2] - 128
+    out = np.empty(p.shape[1:] + (3,), np.int64)
+    for c in range(3):
+        out[..., c] = y + ((_YCC_INV[c, 0] * db + _YCC_INV[c, 1] * dr + 32768) >> 16)
+    return np.clip(out, 0, 255).astype(np.uint8)
+
+
+def planes_to_u8(planes: np.ndarray) -> np.ndarray:
+    """Decoded real-valued planes -> uint8: nearest integer (ties to even),
+    clamped to [0, 255]."""
+    return np.clip(np.rint(np.asarray(planes, np.float64)), 0, 255).astype(np.uint8)

@@ -12,6 +12,7 @@ from __future__ import annotations
 import ctypes
 import os
 import threading
+import zlib
 
 import numpy as np
 
@@ -63,7 +64,18 @@ EXPORTS = ["aqmp_params_default", "aqmp_encode_planes", "aqmp_encode", "aqmp_cod
            "aqmp_decode", "aqmp_code_free", "aqmp_correlate", "aqmp_num_atoms", "aqmp_last_error",
            "aqmp_version", "aqmp_profile_enable", "aqmp_profile_reset", "aqmp_profile_read",
            "aqmp_correlate_noalloc", "aqmp_selftest_wait", "aqmp_code_device", "aqmp_synth_forward",
-           "aqmp_synth_backward", "aqmp_ssim"]
+           "aqmp_synth_backward", "aqmp_ssim", "aqmp_image_to_planes", "aqmp_planes_to_image",
+           "aqmp_bitstream_size", "aqmp_bitstream_write", "aqmp_bitstream_parse", "aqmp_code_from_bitstream"]
+
+AQMP_COLOR_PLANES, AQMP_COLOR_RGB, AQMP_COLOR_YCBCR = 0, 1, 2
+_COLOR_NAMES = {"planes": AQMP_COLOR_PLANES, "gray": AQMP_COLOR_PLANES, "rgb": AQMP_COLOR_RGB,
+                "ycbcr": AQMP_COLOR_YCBCR}
+
+
+class aqmp_bitstream_info(ctypes.Structure):
+    _fields_ = [("version", ctypes.c_int), ("color", ctypes.c_int), ("dict_id", ctypes.c_int),
+                ("n_planes", ctypes.c_int), ("min_block", ctypes.c_int), ("max_block", ctypes.c_int),
+                ("n_leaves", ctypes.c_uint64), ("n_atoms", ctypes.c_uint64)]
 
 
 class aqmp_kernel_time(ctypes.Structure):
@@ -109,6 +121,12 @@ def load_library(path: str | None = None):
         lib.aqmp_profile_reset.argtypes = []
         lib.aqmp_profile_reset.restype = None
         lib.aqmp_profile_read.argtypes = [V, I, ctypes.POINTER(I)]
+        lib.aqmp_image_to_planes.argtypes = [V, I, I, I, I64, I, V, I64, V]
+        lib.aqmp_planes_to_image.argtypes = [V, I, I, I, I64, I, V, I64, V]
+        lib.aqmp_bitstream_size.argtypes = [V, U64P]
+        lib.aqmp_bitstream_write.argtypes = [V, I, V, ctypes.c_uint64, U64P]
+        lib.aqmp_bitstream_parse.argtypes = [V, ctypes.c_uint64, ctypes.POINTER(aqmp_bitstream_info), V, V, V]
+        lib.aqmp_code_from_bitstream.argtypes = [V, ctypes.c_uint64, ctypes.POINTER(V)]
         if path is None:
             _lib = lib
         return lib
@@ -351,3 +369,115 @@ def aqmp_ssim(x, y, ssim_out, grad_y=None, grad_scale: float = 1.0, stream=None)
                                     ctypes.c_void_p(grad_y.data_ptr()) if grad_y is not None else None,
                                     float(grad_scale), _stream_handle(stream)))
     return ssim_out
+
+
+# ---------------------------------------------------------------- codec stages
+# Section 2.3: (i) colour conversion, (ii) the encoder above, (iii) DEFLATE of
+# the bitstream; the decoder reverses them.
+
+def _color_id(color) -> int:
+    return _COLOR_NAMES[color] if isinstance(color, str) else int(color)
+
+
+def aqmp_image_to_planes(img, color="ycbcr", stream=None):
+    """(h, w, C) or (h, w) uint8 CUDA tensor -> (C, h, w) uint8 CUDA planes."""
+    import torch
+    if img.dim() == 2:
+        img = img.unsqueeze(-1)
+    if img.dtype != torch.uint8 or not img.is_cuda or not img.is_contiguous():
+        raise ValueError("image must be a contiguous uint8 CUDA tensor (h, w[, C])")
+    h, w, ch = img.shape
+    planes = torch.empty((ch, h, w), dtype=torch.uint8, device=img.device)
+    _check(load_library().aqmp_image_to_planes(ctypes.c_void_p(img.data_ptr()), h, w, ch, img.stride(0),
+                                               _color_id(color), ctypes.c_void_p(planes.data_ptr()), w,
+                                               _stream_handle(stream)))
+    return planes
+
+
+def aqmp_planes_to_image(planes, color="ycbcr", stream=None):
+    """(C, h, w) float32 CUDA planes (decoder output) -> (h, w, C) uint8."""
+    import torch
+    if planes.dtype != torch.float32 or not planes.is_cuda or not planes.is_contiguous() or planes.dim() != 3:
+        raise ValueError("planes must be a contiguous (C, h, w) float32 CUDA tensor")
+    ch, h, w = planes.shape
+    img = torch.empty((h, w, ch), dtype=torch.uint8, device=planes.device)
+    _check(load_library().aqmp_planes_to_image(ctypes.c_void_p(planes.data_ptr()), h, w, ch, w, _color_id(color),
+                                               ctypes.c_void_p(img.data_ptr()), w * ch, _stream_handle(stream)))
+    return img
+
+
+def aqmp_bitstream(code: Code, color="planes") -> bytes:
+    """The serialised MP output (the lossless stage's input)."""
+    lib = load_library()
+    n = ctypes.c_uint64()
+    _check(lib.aqmp_bitstream_size(code.handle, ctypes.byref(n)))
+    buf = (ctypes.c_uint8 * max(1, n.value))()
+    ln = ctypes.c_uint64()
+    _check(lib.aqmp_bitstream_write(code.handle, _color_id(color), buf, n.value, ctypes.byref(ln)))
+    return bytes(buf)[:ln.value]
+
+
+def aqmp_bitstream_parse(data: bytes):
+    """Host parse: (info dict, shapes [(h, w)], leaves, atoms), leaves in
+    canonical order with positions recovered from the traversal."""
+    lib = load_library()
+    info = aqmp_bitstream_info()
+    _check(lib.aqmp_bitstream_parse(data, len(data), ctypes.byref(info), None, None, None))
+    shapes = np.zeros(2 * max(1, info.n_planes), np.int32)
+    leaves = np.zeros(info.n_leaves, LEAF_DTYPE)
+    atoms = np.zeros(info.n_atoms, ATOM_DTYPE)
+    _check(lib.aqmp_bitstream_parse(data, len(data), ctypes.byref(info), shapes.ctypes.data,
+                                    leaves.ctypes.data if len(leaves) else None,
+                                    atoms.ctypes.data if len(atoms) else None))
+    d = {k: getattr(info, k) for k, _ in aqmp_bitstream_info._fields_}
+    return d, [(int(shapes[2 * i]), int(shapes[2 * i + 1])) for i in range(info.n_planes)], leaves, atoms
+
+
+def aqmp_code_from_bitstream(data: bytes) -> Code:
+    out = ctypes.c_void_p()
+    _check(load_library().aqmp_code_from_bitstream(data, len(data), ctypes.byref(out)))
+    return Code(out.value)
+
+
+def compress(image, tol: float, color="ycbcr", level: int = 9, stream=None, **param_kw) -> bytes:
+    """The whole encoder of Section 2.3 / Appendix A: colour conversion,
+    AQMP, DEFLATE (zlib container).  `image` is an (h, w, 3) or (h, w)
+    uint8 array or CUDA tensor; h and w must be multiples of max_block."""
+    import torch
+    img = image if hasattr(image, "data_ptr") else torch.from_numpy(np.ascontiguousarray(image))
+    img = img.cuda() if not img.is_cuda else img
+    if img.dim() == 2:
+        color = "planes"
+    planes = aqmp_image_to_planes(img.contiguous(), color, stream)
+    code = aqmp_encode_planes([planes[c] for c in range(planes.shape[0])], tol, stream=stream, **param_kw)
+    try:
+        return zlib.compress(aqmp_bitstream(code, color), level)
+    finally:
+        code.free()
+
+
+def decompress(blob: bytes, stream=None):
+    """Inverse of `compress`: inflate, rebuild the code, decode every plane
+    (Algorithm 3), convert back to RGB when the stream says YCbCr.  Returns
+    an (h, w, C) uint8 CUDA tensor."""
+    import torch
+    data = zlib.decompress(blob)
+    info, shapes, _, _ = aqmp_bitstream_parse(data)
+    if len(set(shapes)) != 1:
+        raise ValueError("planes of different sizes do not form one image")
+    h, w = shapes[0]
+    code = aqmp_code_from_bitstream(data)
+    try:
+        planes = torch.empty((info["n_planes"], h, w), dtype=torch.float32, device="cuda")
+        for c in range(info["n_planes"]):
+            aqmp_decode(code, c, planes[c], stream)
+        return aqmp_planes_to_image(planes, info["color"], stream)
+    finally:
+        code.free()
+
+
+def compression_rate(image, blob: bytes) -> float:
+    """CR of Section 3: original size over compressed size, in bytes; the
+    original is taken as the raw 8-bit pixels (h w C bytes)."""
+    n = int(np.prod(image.shape))
+    return n / len(blob)

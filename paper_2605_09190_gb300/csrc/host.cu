@@ -21,6 +21,7 @@
 #include "../../include/aqmp.h"
 #include "common.cuh"
 #include "kernels.h"
+#include "code.h"
 
 using namespace aqmp;
 
@@ -347,21 +348,6 @@ int device_sm_count(int *sms) {
 
 // ===================================================================== ABI
 
-struct aqmp_code {
-    int device = 0;
-    int dict_id = 0, min_block = 4, max_block = 64;
-    std::vector<std::pair<int, int>> shapes;
-    LeafRec *leaves = nullptr;
-    AtomRec *atoms = nullptr;
-    float *alpha_lo = nullptr;
-    unsigned long long n_leaves = 0, n_atoms = 0;
-    aqmp_stats stats{};
-    ~aqmp_code() {
-        if (leaves) cudaFree(leaves);
-        if (atoms) cudaFree(atoms);
-        if (alpha_lo) cudaFree(alpha_lo);
-    }
-};
 
 extern "C" {
 

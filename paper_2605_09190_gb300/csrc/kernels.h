@@ -129,6 +129,21 @@ struct OrderArgs {
 unsigned long long order_status_words(unsigned long long n_cells, unsigned long long leaf_cap);
 cudaError_t launch_order_phase(const OrderArgs &a, int phase, int num_sms, cudaStream_t st);
 
+// Colour conversion of the codec (color.cu): an interleaved h x w x C byte
+// image <-> C planes (plane c at c h plane_pitch); color 2 = YCbCr <-> RGB
+// (C = 3), otherwise the channels are copied.  Planes going out are bytes,
+// planes coming back are the decoder's floats.
+struct ColorArgs {
+    const uint8_t *img;
+    uint8_t *img_out;
+    long long pitch;
+    uint8_t *planes_u8;
+    const float *planes_f32;
+    long long plane_pitch;
+    int h, w, channels, color;
+};
+cudaError_t launch_color(const ColorArgs &a, bool to_planes, int num_sms, cudaStream_t st);
+
 // Table construction on the device (tables.cu) from the FP64 1-D bases
 // basis_dev = [2][b][b] (DCT, Haar); fam0 selects the family of a
 // single-family dictionary (0 = DCT, 1 = Haar).
