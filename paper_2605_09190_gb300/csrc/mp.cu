@@ -255,8 +255,8 @@ mp_kernel(MPArgs a) {
     float2 *sWT = sW + B * B;                                    // W^T
     unsigned char *after_tables = smem + (NF == 2 ? 2 * B * B * sizeof(float2) : 0);
     uint4 *sPart = reinterpret_cast<uint4 *>(after_tables);      // [3][NW] top-2 partials
-    uint32_t *sMisc = reinterpret_cast<uint32_t *>(sPart + 3 * NW);               // [8]
-    unsigned long long *sRk = reinterpret_cast<unsigned long long *>(sMisc + 8);  // [NW]
+    uint32_t *sMisc = reinterpret_cast<uint32_t *>(sPart + 3 * NW);               // [12]
+    unsigned long long *sRk = reinterpret_cast<unsigned long long *>(sMisc + 12); // [NW]
     uint32_t *sRj = reinterpret_cast<uint32_t *>(sRk + NW);      // [NW]
     StepRec *sSteps = reinterpret_cast<StepRec *>(sRj + NW);
 
@@ -330,16 +330,31 @@ mp_kernel(MPArgs a) {
 
         int t = 0;
         bool conv = false, tie = false;
+        // With several warps per leaf, warp 0 alone keeps the residual energy
+        // and takes the accuracy test; its verdict travels with the step's
+        // argmax exchange (the test still decides before the step is used).
+        const bool energy_warp = T == 32 || lane < 32;
         for (;;) {
             // (a6) accuracy test before every step, strict
-            const bool below = DF ? df_lt(En, thrE) : (En.hi < eps2_f);
-            if (DF && fabsf(En.hi - thrE.hi) <= bandE_f * 1.01f + 0x1p-20f * fabsf(thrE.hi)) {
-                if (fabs(df_to_double(En) - df_to_double(thrE)) < ldexp((double)e0, -37)) tie = true;
+            bool below = false;
+            if (energy_warp) {
+                below = DF ? df_lt(En, thrE) : (En.hi < eps2_f);
+                if (DF && fabsf(En.hi - thrE.hi) <= bandE_f * 1.01f + 0x1p-20f * fabsf(thrE.hi)) {
+                    if (fabs(df_to_double(En) - df_to_double(thrE)) < ldexp((double)e0, -37)) tie = true;
+                }
             }
-            if (below) { conv = true; break; }
-            if (t == k) break;
+            if (T == 32) {
+                if (below) { conv = true; break; }
+                if (t == k) break;
+            } else if (t == k) {
+                if (lane == 0) sMisc[10] = below ? 1u : 0u;
+                __syncthreads();
+                conv = sMisc[10] != 0u;
+                break;
+            }
 
             // (a3) argmax |c| on the cached top-2 summaries
+            bool stop = false;
             auto group_best = [&](int buf) {
                 Top2 b = top[0];
 #pragma unroll
@@ -349,7 +364,9 @@ mp_kernel(MPArgs a) {
                     if ((lane & 31) == 0)
                         sPart[buf * NW + (lane >> 5)] =
                             make_uint4((uint32_t)b.P, (uint32_t)(b.P >> 32), b.k2, __float_as_uint(b.lo1));
+                    if (buf < 2 && lane == 0) sMisc[8 + buf] = below ? 1u : 0u;
                     __syncthreads();
+                    if (buf < 2) stop = sMisc[8 + buf] != 0u;
                     const int l = lane & 31;
                     if (l < NW) {
                         const uint4 v = sPart[buf * NW + l];
@@ -362,6 +379,7 @@ mp_kernel(MPArgs a) {
                 return b;
             };
             Top2 best = group_best(t & 1);
+            if (T > 32 && stop) { conv = true; break; }
             if (STALE && (best.P >> 32) != 0ull && (uint32_t)best.P == 0u) {
                 // a summary left stale by the last step holds the largest
                 // magnitude: its owners rescan and the group reduces again
@@ -452,8 +470,10 @@ mp_kernel(MPArgs a) {
             if (lane == 0) steps[t] = StepRec{j1, alpha.hi, alpha.lo};
 
             // (a5) energy
-            if (DF) En = df_sub(En, df_mul(alpha, alpha));
-            else En = df{__fmaf_rn(-alpha.hi, alpha.hi, En.hi), 0.0f};
+            if (energy_warp) {
+                if (DF) En = df_sub(En, df_mul(alpha, alpha));
+                else En = df{__fmaf_rn(-alpha.hi, alpha.hi, En.hi), 0.0f};
+            }
 
             // (a4) correlation update through the Gram matrix
             const int fam1 = (int)(j1 >= (uint32_t)n);
@@ -620,7 +640,7 @@ template <int B, int T, int NF>
 static size_t mp_smem_bytes(int k, int groups) {
     constexpr int NW = T / 32;
     size_t bytes = (NF == 2 ? 2 * B * B * sizeof(float2) : 0);
-    bytes += 3 * NW * sizeof(uint4) + 8 * sizeof(uint32_t);            // partials, misc
+    bytes += 3 * NW * sizeof(uint4) + 12 * sizeof(uint32_t);           // partials, misc
     bytes += NW * sizeof(unsigned long long) + NW * sizeof(uint32_t);  // full-precision partials
     bytes += (size_t)groups * k * sizeof(StepRec);
     return bytes;
