@@ -74,31 +74,36 @@ __device__ __forceinline__ unsigned long long top2_key(float hi, uint32_t j) {
 }
 
 // Running top-2 kept on float magnitudes inside element loops (cheaper per
-// element than the packed key); converted to a Top2 once per thread.
+// element than the packed key); the top is tracked by its register slot, a
+// compile-time constant in the unrolled loops (a thread's atom index grows
+// with the slot), and converted to a Top2 once per thread.
 struct Run2 {
     float v1, lo1, m2;     // signed top value, its low word, second largest |value|
-    uint32_t j1;
+    uint32_t s1;           // slot of the top (0xffff: none)
 };
 
 __device__ __forceinline__ Run2 run2_empty() { return Run2{0.0f, 0.0f, 0.0f, 0xffffu}; }
 
-// Elements must be folded in ascending index order (strict > keeps the
+// Elements must be folded in ascending slot order (strict > keeps the
 // lowest index among equal magnitudes).
-__device__ __forceinline__ void run2_fold(Run2 &r, float hi, float lo, uint32_t j) {
+__device__ __forceinline__ void run2_fold(Run2 &r, float hi, float lo, uint32_t slot) {
     const float ah = fabsf(hi), a1 = fabsf(r.v1);
     r.m2 = fmaxf(r.m2, fminf(a1, ah));
     const bool take = ah > a1;
     r.v1 = take ? hi : r.v1;
     r.lo1 = take ? lo : r.lo1;
-    r.j1 = take ? j : r.j1;
+    r.s1 = take ? slot : r.s1;
 }
 
-__device__ __forceinline__ Top2 run2_top2(const Run2 &r) {
+// Atom index of slot s for thread `lane` of a T-thread group: lane + T s.
+template <int T>
+__device__ __forceinline__ Top2 run2_top2(const Run2 &r, int lane) {
     const uint32_t h = __float_as_uint(r.v1);
-    const unsigned long long P = r.v1 == 0.0f && r.j1 == 0xffffu
+    const uint32_t j1 = (uint32_t)lane + (uint32_t)T * r.s1;
+    const unsigned long long P = r.v1 == 0.0f && r.s1 == 0xffffu
                                      ? 0ull
                                      : ((unsigned long long)(h & 0x7fffffffu) << 32) |
-                                           (((0xffffu - r.j1) << 1) | (h >> 31));
+                                           (((0xffffu - j1) << 1) | (h >> 31));
     return Top2{P, __float_as_uint(r.m2), r.lo1};
 }
 
@@ -172,12 +177,14 @@ __device__ __forceinline__ uint32_t warp_min(uint32_t v) {
 template <int B, int T, int E, int G, int S0, int FOFF, bool DF>
 __device__ __forceinline__ Top2 update_family(float (&ch)[E], float (&cl)[E], int lane, const df &u,
                                               const float2 *Vq) {
+    // element (lane, s) is atom lane + T s, in-family column q = (lane / B) +
+    // (T / B) s - FOFF / B (T and FOFF are multiples of B)
+    const float2 *Vl = Vq + (unsigned)lane / (unsigned)B;
     Run2 acc = run2_empty();
 #pragma unroll
     for (int s2 = 0; s2 < G; ++s2) {
         const int s = S0 + s2;
-        const int j = lane + T * s;
-        const float2 w = Vq[(j - FOFF) / B];
+        const float2 w = Vl[(T / B) * s - FOFF / B];
         if (DF) {
             const df r = df_sub_mul(df{ch[s], cl[s]}, u, df{w.x, w.y});
             ch[s] = r.hi;
@@ -185,9 +192,9 @@ __device__ __forceinline__ Top2 update_family(float (&ch)[E], float (&cl)[E], in
         } else {
             ch[s] = __fmaf_rn(-u.hi, w.x, ch[s]);     // plain FP32 form: one FMA per entry
         }
-        run2_fold(acc, ch[s], cl[s], (uint32_t)j);
+        run2_fold(acc, ch[s], cl[s], (uint32_t)s);
     }
-    return run2_top2(acc);
+    return run2_top2<T>(acc, lane);
 }
 
 // Zero element j1 among slots [S0, S0 + G) (none if j1 is not one of them)
@@ -200,9 +207,9 @@ __device__ __forceinline__ Top2 zero_and_rescan(float (&ch)[E], float (&cl)[E], 
         const int s = S0 + s2;
         const int j = lane + T * s;
         if ((uint32_t)j == j1) { ch[s] = 0.0f; cl[s] = 0.0f; }
-        run2_fold(acc, ch[s], cl[s], (uint32_t)j);
+        run2_fold(acc, ch[s], cl[s], (uint32_t)s);
     }
-    return run2_top2(acc);
+    return run2_top2<T>(acc, lane);
 }
 
 // Zero slot S0 + s2 (0 <= s2 < G); the registers stay statically indexed.
