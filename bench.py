@@ -477,6 +477,7 @@ def run_ours(args):
                 "atom_iterations_per_step": stats_sum["atom_iterations"] / args.steps,
                 "leaves_per_step": stats_sum["n_leaves"] / args.steps,
                 "near_tie_leaves": stats_sum["near_tie_leaves"],
+                "window_step_fraction": sum(stats_sum["window_steps_per_level"]) / max(1, stats_sum["atom_iterations"]),
                 "forms": {"exact (bf16-limb tensor GEMM + f32x2 certified pursuit)": value,
                           "fp32 (same GEMM rounded to fp32 + fp32 pursuit, not certified)": fp32_value},
                 "roofline": roof, "kernels": kernels, "gpu_launches": launches,

@@ -123,6 +123,9 @@ typedef struct {
     uint64_t near_tie_leaves;   /* leaves with any AQMP_LEAF_* flag */
     uint64_t attempts_per_level[8];
     uint64_t iterations_per_level[8];
+    uint64_t window_steps_per_level[8];   /* steps decided in full precision because
+                                           * another atom lay within the decision
+                                           * window of the largest (exact form) */
 } aqmp_stats;
 
 typedef struct aqmp_code aqmp_code;   /* opaque, library-owned result */

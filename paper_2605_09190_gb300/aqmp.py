@@ -51,7 +51,8 @@ class aqmp_plane(ctypes.Structure):
 class aqmp_stats(ctypes.Structure):
     _fields_ = [("n_leaves", ctypes.c_uint64), ("n_atoms", ctypes.c_uint64), ("attempts", ctypes.c_uint64),
                 ("atom_iterations", ctypes.c_uint64), ("near_tie_leaves", ctypes.c_uint64),
-                ("attempts_per_level", ctypes.c_uint64 * 8), ("iterations_per_level", ctypes.c_uint64 * 8)]
+                ("attempts_per_level", ctypes.c_uint64 * 8), ("iterations_per_level", ctypes.c_uint64 * 8),
+                ("window_steps_per_level", ctypes.c_uint64 * 8)]
 
 
 LEAF_DTYPE = np.dtype([("plane", np.uint32), ("y", np.uint32), ("x", np.uint32), ("atom_off", np.uint32),
@@ -232,7 +233,8 @@ def aqmp_code_stats(code: Code) -> dict:
     return {"n_leaves": s.n_leaves, "n_atoms": s.n_atoms, "attempts": s.attempts,
             "atom_iterations": s.atom_iterations, "near_tie_leaves": s.near_tie_leaves,
             "attempts_per_level": list(s.attempts_per_level),
-            "iterations_per_level": list(s.iterations_per_level)}
+            "iterations_per_level": list(s.iterations_per_level),
+            "window_steps_per_level": list(s.window_steps_per_level)}
 
 
 def aqmp_code_copy(code: Code):

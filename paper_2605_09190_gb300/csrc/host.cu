@@ -600,6 +600,7 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
     for (int l = 0; l < nlev && l < 8; ++l) {
         s.attempts_per_level[l] = h.attempts[l];
         s.iterations_per_level[l] = h.iterations[l];
+        s.window_steps_per_level[l] = h.window_steps[l];
         s.attempts += h.attempts[l];
         s.atom_iterations += h.iterations[l];
     }

@@ -335,7 +335,7 @@ mp_kernel(MPArgs a) {
             }
         }
 
-        int t = 0;
+        int t = 0, windows = 0;
         bool conv = false, tie = false;
         // With several warps per leaf, warp 0 alone keeps the residual energy
         // and takes the accuracy test; its verdict travels with the step's
@@ -405,6 +405,7 @@ mp_kernel(MPArgs a) {
             bool rare = false;
             if (DF && __uint_as_float(best.k2) >= amax - window) {
                 rare = true;
+                ++windows;
                 // Another atom is within the window: decide in full precision
                 // among the candidates -- the true largest magnitude, then the
                 // lowest index within 2^-32 ||y|| of it; any candidate within
@@ -573,6 +574,7 @@ mp_kernel(MPArgs a) {
         if (lane == 0) {
             atomicAdd(&a.ctr->attempts[lv.level], 1ull);
             atomicAdd(&a.ctr->iterations[lv.level], (unsigned long long)t);
+            if (windows) atomicAdd(&a.ctr->window_steps[lv.level], (unsigned long long)windows);
         }
         const bool emit = conv || lv.is_last;
         uint32_t off = 0, eslot = 0;
