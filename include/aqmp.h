@@ -61,6 +61,18 @@ extern "C" {
 #define AQMP_FLAG_SIMT_GEMM     2u /* compute the initial correlation with the
                                       integer SIMT kernel instead of tcgen05
                                       (bit-identical result; for validation) */
+#define AQMP_FLAG_NO_AUTOTUNE   4u /* use the default kernel at every side instead
+                                      of the autotuned choice */
+#define AQMP_FLAG_ALT_THREADS   8u /* run the pursuit with the alternate number of
+                                      threads per leaf at sides 16, 32 and 64
+                                      (bit-identical result; for validation) */
+/* Autotuning: kernel choices that leave the result unchanged bit for bit
+ * are measured on the first calls of each configuration and the fastest
+ * is kept for the life of the process: the initial correlation on the
+ * tensor cores or on the integer SIMT path (both are timed, twice each, on
+ * the first encode that meets a side, dictionary, precision and capacity),
+ * and the pursuit's threads per leaf at sides 16, 32 and 64 (the two
+ * candidates alternate over the first four such encodes). */
 
 typedef struct {
     float   rmse_tol;     /* per-block RMSE tolerance on the 0-255 scale:
@@ -219,6 +231,22 @@ int  aqmp_profile_enable(int on);                 /* returns the previous state 
 void aqmp_profile_reset(void);
 /* Copies up to `max` entries into `out` (host); *n receives the count. */
 int  aqmp_profile_read(aqmp_kernel_time *out, int max, int *n);
+
+/* Autotuner state of the current device (see AQMP_FLAG_NO_AUTOTUNE): one
+ * entry per choice point met so far.  kind 0 = initial correlation
+ * (candidate 0 tcgen05, 1 integer SIMT); kind 1 = pursuit (candidate 0 the
+ * default threads per leaf, 1 the alternate).  chosen is -1 while the
+ * candidates are still being timed; best_ms is each candidate's lowest
+ * timing.  Copies up to `max` entries into `out`; *n receives the count. */
+typedef struct {
+    int    kind, side, dict_id, precision, capacity_log2;
+    int    chosen;
+    int    samples[2];
+    double best_ms[2];
+} aqmp_tune_entry;
+
+int  aqmp_autotune_read(aqmp_tune_entry *out, int max, int *n);
+void aqmp_autotune_reset(void);   /* forget every choice (they are measured again) */
 
 /* aqmp_correlate without any device allocation, for callers that may not
  * allocate device memory (memory owned by another allocator or by a fixed

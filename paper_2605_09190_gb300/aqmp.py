@@ -27,6 +27,8 @@ AQMP_PREC_EXACT = 0
 AQMP_PREC_FP32 = 1
 AQMP_FLAG_INPUT_DEVICE = 1
 AQMP_FLAG_SIMT_GEMM = 2
+AQMP_FLAG_NO_AUTOTUNE = 4
+AQMP_FLAG_ALT_THREADS = 8
 AQMP_LEAF_NEAR_TIE = 1
 AQMP_LEAF_NEAR_TIE_PARENT = 2
 
@@ -66,7 +68,14 @@ EXPORTS = ["aqmp_params_default", "aqmp_encode_planes", "aqmp_encode", "aqmp_cod
            "aqmp_version", "aqmp_profile_enable", "aqmp_profile_reset", "aqmp_profile_read",
            "aqmp_correlate_noalloc", "aqmp_selftest_wait", "aqmp_code_device", "aqmp_synth_forward",
            "aqmp_synth_backward", "aqmp_ssim", "aqmp_image_to_planes", "aqmp_planes_to_image",
-           "aqmp_bitstream_size", "aqmp_bitstream_write", "aqmp_bitstream_parse", "aqmp_code_from_bitstream"]
+           "aqmp_bitstream_size", "aqmp_bitstream_write", "aqmp_bitstream_parse", "aqmp_code_from_bitstream",
+           "aqmp_autotune_read", "aqmp_autotune_reset"]
+
+
+class aqmp_tune_entry(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("side", ctypes.c_int), ("dict_id", ctypes.c_int),
+                ("precision", ctypes.c_int), ("capacity_log2", ctypes.c_int), ("chosen", ctypes.c_int),
+                ("samples", ctypes.c_int * 2), ("best_ms", ctypes.c_double * 2)]
 
 AQMP_COLOR_PLANES, AQMP_COLOR_RGB, AQMP_COLOR_YCBCR = 0, 1, 2
 _COLOR_NAMES = {"planes": AQMP_COLOR_PLANES, "gray": AQMP_COLOR_PLANES, "rgb": AQMP_COLOR_RGB,
@@ -122,6 +131,9 @@ def load_library(path: str | None = None):
         lib.aqmp_profile_reset.argtypes = []
         lib.aqmp_profile_reset.restype = None
         lib.aqmp_profile_read.argtypes = [V, I, ctypes.POINTER(I)]
+        lib.aqmp_autotune_read.argtypes = [V, I, ctypes.POINTER(I)]
+        lib.aqmp_autotune_reset.argtypes = []
+        lib.aqmp_autotune_reset.restype = None
         lib.aqmp_image_to_planes.argtypes = [V, I, I, I, I64, I, V, I64, V]
         lib.aqmp_planes_to_image.argtypes = [V, I, I, I, I64, I, V, I64, V]
         lib.aqmp_bitstream_size.argtypes = [V, U64P]
@@ -199,7 +211,7 @@ def _as_plane(x, tol, device_input):
 
 
 def aqmp_encode_planes(planes, tols=None, params: aqmp_params | None = None, stream=None, simt_gemm=False,
-                       **param_kw) -> Code:
+                       autotune=True, alt_threads=False, **param_kw) -> Code:
     """Encode a list of 2-D uint8 planes (torch CUDA tensors, or host numpy
     arrays / CPU tensors), one optional tolerance per plane."""
     if params is None:
@@ -215,7 +227,8 @@ def aqmp_encode_planes(planes, tols=None, params: aqmp_params | None = None, str
         keep.append(ref)
     p = aqmp_params.from_buffer_copy(params)
     p.flags = (p.flags | (AQMP_FLAG_INPUT_DEVICE if device_input else 0)
-               | (AQMP_FLAG_SIMT_GEMM if simt_gemm else 0))
+               | (AQMP_FLAG_SIMT_GEMM if simt_gemm else 0) | (0 if autotune else AQMP_FLAG_NO_AUTOTUNE)
+               | (AQMP_FLAG_ALT_THREADS if alt_threads else 0))
     out = ctypes.c_void_p()
     _check(load_library().aqmp_encode_planes(ctypes.byref(p), arr, len(planes), _stream_handle(stream),
                                              ctypes.byref(out)))
@@ -303,6 +316,23 @@ def aqmp_profile_read() -> dict:
     n = ctypes.c_int(0)
     _check(load_library().aqmp_profile_read(arr, 64, ctypes.byref(n)))
     return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(n.value)}
+
+
+def aqmp_autotune_read() -> list:
+    """The autotuner's choice points on the current device: dicts with kind
+    ("corr": 0 tcgen05 / 1 SIMT, "mp": 0 default / 1 alternate threads per
+    leaf), side, dict_id, precision, capacity_log2, chosen (-1 while
+    measuring), samples and best_ms per candidate."""
+    arr = (aqmp_tune_entry * 64)()
+    n = ctypes.c_int(0)
+    _check(load_library().aqmp_autotune_read(arr, 64, ctypes.byref(n)))
+    return [{"kind": ("corr", "mp")[e.kind], "side": e.side, "dict_id": e.dict_id, "precision": e.precision,
+             "capacity_log2": e.capacity_log2, "chosen": e.chosen, "samples": list(e.samples),
+             "best_ms": list(e.best_ms)} for e in arr[:min(n.value, 64)]]
+
+
+def aqmp_autotune_reset() -> None:
+    load_library().aqmp_autotune_reset()
 
 
 def aqmp_selftest_wait(limit_ms: int = 50, stream=None) -> int:

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -195,6 +196,67 @@ Profiler g_prof;
 
 std::string kname(const char *k, int b) { return std::string(k) + "_b" + std::to_string(b); }
 
+// ------------------------------------------------------------ autotuner
+//
+// Choice points whose candidates give the same result bit for bit: the
+// initial correlation on the tensor cores or the integer SIMT path (K1), and
+// the pursuit's threads per leaf (K2).  Each is keyed by (kind, side,
+// dictionary, precision, log2 capacity); its candidates are timed with CUDA
+// events on the first calls (K1: both, twice each, within one encode, since
+// recomputing the correlation is harmless; K2: alternately over encodes),
+// and the one with the lowest timing is kept.  The lowest of two timings
+// discards a kernel's first, cold launch.
+struct Tuner {
+    enum Kind { CORR = 0, MP = 1 };
+    static constexpr int kSamples = 2;
+    struct Slot {
+        double best_ms[2] = {1e30, 1e30};
+        int samples[2] = {0, 0};
+        int chosen = -1;
+    };
+    struct Pending { Slot *slot; int cand; cudaEvent_t a, b; };
+    std::map<std::array<int, 5>, Slot> slots;
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> pool;
+    Slot &slot(int kind, int b, int dict, int prec, unsigned long long cap) {
+        int lg = 0;
+        while ((1ull << lg) < cap) ++lg;
+        return slots[{kind, b, dict, prec, lg}];
+    }
+    static int next(const Slot &s) { return s.samples[1] < s.samples[0] ? 1 : 0; }
+    cudaEvent_t get() {
+        if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    template <class F>
+    cudaError_t timed(Slot &s, int cand, cudaStream_t st, F &&launch) {
+        cudaEvent_t a = get(), b = get();
+        cudaEventRecord(a, st);
+        cudaError_t e = launch();
+        cudaEventRecord(b, st);
+        pending.push_back({&s, cand, a, b});
+        return e;
+    }
+    // After the stream has been synchronised.
+    void resolve() {
+        for (auto &p : pending) {
+            float ms = 0.0f;
+            if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+                Slot &s = *p.slot;
+                s.best_ms[p.cand] = std::min(s.best_ms[p.cand], (double)ms);
+                s.samples[p.cand] += 1;
+                if (s.chosen < 0 && s.samples[0] >= kSamples && s.samples[1] >= kSamples)
+                    s.chosen = s.best_ms[1] < s.best_ms[0] ? 1 : 0;
+            }
+            pool.push_back(p.a);
+            pool.push_back(p.b);
+        }
+        pending.clear();
+    }
+};
+
 struct Dict {
     DictDev d{};
     DeviceBuf limbs, dh, dl, sh, sl, w, basis, basis64;
@@ -210,6 +272,7 @@ struct Ctx {
     DeviceBuf planes, staging, queues, Y, e0, c0, counters, ssim_ws;
     DeviceBuf leaves_ws, atoms_ws, lo_ws, atom_leaf, cells, perm, new_off, order_status;   // emission -> canonical order
     bool gauss_ready = false;
+    Tuner tuner;
     Counters *host_ctr = nullptr;             // pinned
     PlaneDesc *host_planes = nullptr;         // pinned staging for plane descriptors
     int host_planes_cap = 0;
@@ -352,6 +415,41 @@ int device_sm_count(int *sms) {
 extern "C" {
 
 const char *aqmp_last_error(void) { return g_last_error.c_str(); }
+
+int aqmp_autotune_read(aqmp_tune_entry *out, int max, int *n) {
+    if (!n || (max > 0 && !out)) return fail(AQMP_E_ARG, "NULL argument");
+    Ctx *c;
+    int rc;
+    if ((rc = get_ctx(&c))) return rc;
+    std::lock_guard<std::mutex> lock(c->mu);
+    int k = 0;
+    for (const auto &kv : c->tuner.slots) {
+        if (k < max) {
+            aqmp_tune_entry &e = out[k];
+            e.kind = kv.first[0];
+            e.side = kv.first[1];
+            e.dict_id = kv.first[2];
+            e.precision = kv.first[3];
+            e.capacity_log2 = kv.first[4];
+            e.chosen = kv.second.chosen;
+            for (int i = 0; i < 2; ++i) {
+                e.samples[i] = kv.second.samples[i];
+                e.best_ms[i] = kv.second.samples[i] ? kv.second.best_ms[i] : 0.0;
+            }
+        }
+        ++k;
+    }
+    *n = k;
+    return AQMP_OK;
+}
+
+void aqmp_autotune_reset(void) {
+    Ctx *c;
+    if (get_ctx(&c)) return;
+    std::lock_guard<std::mutex> lock(c->mu);
+    c->tuner.slots.clear();
+    c->tuner.pending.clear();
+}
 const char *aqmp_version(void) { return "aqmp-gb300 0.1 (sm_103a)"; }
 
 void aqmp_params_default(aqmp_params *p) {
@@ -382,6 +480,8 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
     const aqmp_params P = *params;
     const bool dev_in = (P.flags & AQMP_FLAG_INPUT_DEVICE) != 0;
     const bool simt = (P.flags & AQMP_FLAG_SIMT_GEMM) != 0;
+    const bool tune = (P.flags & AQMP_FLAG_NO_AUTOTUNE) == 0;
+    const bool alt_threads = (P.flags & AQMP_FLAG_ALT_THREADS) != 0;
     unsigned long long npix = 0, roots = 0, staged = 0;
     for (int i = 0; i < n_planes; ++i) {
         const aqmp_plane &pl = planes[i];
@@ -525,12 +625,26 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
         ca.capacity = lv.capacity;
         ca.c0 = (float2 *)c->c0.p;
         ca.ctr = ctr;
+        if ((rc = encode_bf16_map(&ymaps[l], c->Y.p, cap[l], d.Kpad, 64))) return rc;
+        ca.tmap_Y = &ymaps[l];
+        auto corr_tc = [&] { return g_prof.run(kname("corr_tc", b), st, [&] { return launch_corr_tc(ca, st); }); };
+        auto corr_simt = [&] {
+            return g_prof.run(kname("corr_simt", b), st, [&] { return launch_corr_simt(ca, st); });
+        };
         if (simt) {
-            CK(g_prof.run(kname("corr_simt", b), st, [&] { return launch_corr_simt(ca, st); }));
+            CK(corr_simt());
+        } else if (!tune) {
+            CK(corr_tc());
         } else {
-            if ((rc = encode_bf16_map(&ymaps[l], c->Y.p, cap[l], d.Kpad, 64))) return rc;
-            ca.tmap_Y = &ymaps[l];
-            CK(g_prof.run(kname("corr_tc", b), st, [&] { return launch_corr_tc(ca, st); }));
+            Tuner::Slot &ts = c->tuner.slot(Tuner::CORR, b, P.dict_id, P.precision, cap[l]);
+            if (ts.chosen >= 0) {
+                CK(ts.chosen ? corr_simt() : corr_tc());
+            } else {
+                for (int rep = 0; rep < Tuner::kSamples; ++rep) {
+                    CK(c->tuner.timed(ts, 0, st, corr_tc));
+                    CK(c->tuner.timed(ts, 1, st, corr_simt));
+                }
+            }
         }
 
         MPArgs ma{};
@@ -549,8 +663,21 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
         ma.cells = cells;
         ma.ctr = ctr;
         const bool exact = P.precision == AQMP_PREC_EXACT;
-        CK(g_prof.run(kname(exact ? "mp" : "mp_fp32", b), st,
-                      [&] { return launch_mp(ma, d.nf, exact, c->num_sms, st); }));
+        auto mp = [&](int v) {
+            return g_prof.run(kname(exact ? "mp" : "mp_fp32", b), st,
+                              [&] { return launch_mp(ma, d.nf, exact, v, c->num_sms, st); });
+        };
+        if (alt_threads || !tune || !mp_has_variant(b, d.nf)) {
+            CK(mp(alt_threads ? 1 : 0));
+        } else {
+            Tuner::Slot &ts = c->tuner.slot(Tuner::MP, b, P.dict_id, P.precision, cap[l]);
+            if (ts.chosen >= 0) {
+                CK(mp(ts.chosen));
+            } else {
+                const int v = Tuner::next(ts);
+                CK(c->tuner.timed(ts, v, st, [&] { return mp(v); }));
+            }
+        }
     }
 
     // canonical order of the output list: plane, root (raster), depth-first
@@ -582,6 +709,7 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
         std::lock_guard<std::mutex> pl(g_prof.mu);
         g_prof.resolve();
     }
+    c->tuner.resolve();
     const Counters &h = *c->host_ctr;
     if (h.error == kDevErrQueueOverflow) return fail(AQMP_E_QUEUE_OVERFLOW, "device queue overflow (site %u)", h.error_info);
     if (h.error == kDevErrTimeout) return fail(AQMP_E_TIMEOUT, "device wait timed out (site %u)", h.error_info);

@@ -26,7 +26,11 @@ struct MPArgs {
     CellMap cells;               // emitted leaves are marked here
     Counters *ctr;
 };
-cudaError_t launch_mp(const MPArgs &a, int nf, bool double_float, int num_sms, cudaStream_t st);
+// variant 0: the default threads per leaf; 1: the alternate one (sides 16,
+// 32, 64 with two families; the same as 0 elsewhere).  Both give the same
+// result bit for bit.
+cudaError_t launch_mp(const MPArgs &a, int nf, bool double_float, int variant, int num_sms, cudaStream_t st);
+bool mp_has_variant(int b, int nf);
 
 // Block gather (gather.cu): queue entries -> centred BF16 leaf vectors
 // (column-major unravel, zero padded to Kpad) and sums of squares.

@@ -684,16 +684,33 @@ static cudaError_t launch_mp_t(const MPArgs &a, int num_sms, cudaStream_t st) {
 #define AQMP_MP_T64 256
 #endif
 
+// Alternate threads per leaf, chosen between by the host's autotuner.
+#ifndef AQMP_MP_T16_ALT
+#define AQMP_MP_T16_ALT 64
+#endif
+#ifndef AQMP_MP_T32_ALT
+#define AQMP_MP_T32_ALT 64
+#endif
+#ifndef AQMP_MP_T64_ALT
+#define AQMP_MP_T64_ALT 512
+#endif
+
 template <bool DF>
-static cudaError_t launch_mp_prec(const MPArgs &a, int nf, int num_sms, cudaStream_t st) {
+static cudaError_t launch_mp_prec(const MPArgs &a, int nf, int variant, int num_sms, cudaStream_t st) {
     const int b = a.lv.b;
     if (nf == 2) {
         switch (b) {
             case 4: return launch_mp_t<4, 32, 2, DF>(a, num_sms, st);
             case 8: return launch_mp_t<8, 32, 2, DF>(a, num_sms, st);
-            case 16: return launch_mp_t<16, 32, 2, DF>(a, num_sms, st);
-            case 32: return launch_mp_t<32, AQMP_MP_T32, 2, DF>(a, num_sms, st);
-            case 64: return launch_mp_t<64, AQMP_MP_T64, 2, DF>(a, num_sms, st);
+            case 16:
+                return variant ? launch_mp_t<16, AQMP_MP_T16_ALT, 2, DF>(a, num_sms, st)
+                               : launch_mp_t<16, 32, 2, DF>(a, num_sms, st);
+            case 32:
+                return variant ? launch_mp_t<32, AQMP_MP_T32_ALT, 2, DF>(a, num_sms, st)
+                               : launch_mp_t<32, AQMP_MP_T32, 2, DF>(a, num_sms, st);
+            case 64:
+                return variant ? launch_mp_t<64, AQMP_MP_T64_ALT, 2, DF>(a, num_sms, st)
+                               : launch_mp_t<64, AQMP_MP_T64, 2, DF>(a, num_sms, st);
         }
     } else {
         switch (b) {
@@ -707,8 +724,11 @@ static cudaError_t launch_mp_prec(const MPArgs &a, int nf, int num_sms, cudaStre
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_mp(const MPArgs &a, int nf, bool double_float, int num_sms, cudaStream_t st) {
-    return double_float ? launch_mp_prec<true>(a, nf, num_sms, st) : launch_mp_prec<false>(a, nf, num_sms, st);
+bool mp_has_variant(int b, int nf) { return nf == 2 && (b == 16 || b == 32 || b == 64); }
+
+cudaError_t launch_mp(const MPArgs &a, int nf, bool double_float, int variant, int num_sms, cudaStream_t st) {
+    return double_float ? launch_mp_prec<true>(a, nf, variant, num_sms, st)
+                        : launch_mp_prec<false>(a, nf, variant, num_sms, st);
 }
 
 }  // namespace aqmp

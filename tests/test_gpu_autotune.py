@@ -1,0 +1,61 @@
+"""The autotuner's candidates give the same result bit for bit, and its
+choices settle after the documented number of calls."""
+import numpy as np
+import pytest
+
+from paper_2605_09190_gb300 import synthetic
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2605_09190_gb300 import aqmp, build_lib
+    build_lib.build()
+    aqmp.load_library()
+    assert torch.cuda.is_available()
+    return aqmp
+
+
+def _planes():
+    return [torch.from_numpy(synthetic.piecewise_scene(256, 256, seed=7)).cuda(),
+            torch.from_numpy(synthetic.gradient_scene(128, 256, seed=8)).cuda()]
+
+
+def _result(lib, **kw):
+    code = lib.aqmp_encode_planes(_planes(), [1.0, 3.0], **kw)
+    out = code.copy()
+    code.free()
+    return out
+
+
+def _same(a, b):
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x.view(np.uint8), y.view(np.uint8))
+
+
+def test_alternate_threads_per_leaf_give_the_same_result(lib):
+    ref = _result(lib, autotune=False)
+    assert len(ref[0]) > 0 and set(np.unique(ref[0]["b"])) >= {16, 32, 64}
+    _same(_result(lib, autotune=False, alt_threads=True), ref)
+    _same(_result(lib, autotune=False, simt_gemm=True, alt_threads=True), ref)
+
+
+def test_autotuned_calls_match_and_settle(lib):
+    ref = _result(lib, autotune=False)
+    lib.aqmp_autotune_reset()
+    for _ in range(5):
+        _same(_result(lib), ref)
+    entries = lib.aqmp_autotune_read()
+    corr = {e["side"]: e for e in entries if e["kind"] == "corr"}
+    mp = {e["side"]: e for e in entries if e["kind"] == "mp"}
+    assert set(corr) == {4, 8, 16, 32, 64}
+    assert all(e["chosen"] in (0, 1) and min(e["samples"]) >= 2 for e in corr.values())
+    assert set(mp) == {16, 32, 64}
+    assert all(e["chosen"] in (0, 1) and min(e["samples"]) >= 2 for e in mp.values())
+    # a decided choice point is not measured again
+    before = {(e["kind"], e["side"]): e["samples"] for e in entries}
+    _same(_result(lib), ref)
+    after = {(e["kind"], e["side"]): e["samples"] for e in lib.aqmp_autotune_read()}
+    assert after == before
