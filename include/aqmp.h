@@ -231,6 +231,9 @@ int  aqmp_profile_enable(int on);                 /* returns the previous state 
 void aqmp_profile_reset(void);
 /* Copies up to `max` entries into `out` (host); *n receives the count. */
 int  aqmp_profile_read(aqmp_kernel_time *out, int max, int *n);
+/* Time only the kernels whose name starts with `prefix` (NULL or "": all);
+ * each timed launch adds two event records to the stream's timeline. */
+int  aqmp_profile_filter(const char *prefix);
 
 /* Autotuner state of the current device (see AQMP_FLAG_NO_AUTOTUNE): one
  * entry per choice point met so far.  kind 0 = initial correlation

@@ -69,7 +69,7 @@ EXPORTS = ["aqmp_params_default", "aqmp_encode_planes", "aqmp_encode", "aqmp_cod
            "aqmp_correlate_noalloc", "aqmp_selftest_wait", "aqmp_code_device", "aqmp_synth_forward",
            "aqmp_synth_backward", "aqmp_ssim", "aqmp_image_to_planes", "aqmp_planes_to_image",
            "aqmp_bitstream_size", "aqmp_bitstream_write", "aqmp_bitstream_parse", "aqmp_code_from_bitstream",
-           "aqmp_autotune_read", "aqmp_autotune_reset"]
+           "aqmp_autotune_read", "aqmp_autotune_reset", "aqmp_profile_filter"]
 
 
 class aqmp_tune_entry(ctypes.Structure):
@@ -131,6 +131,7 @@ def load_library(path: str | None = None):
         lib.aqmp_profile_reset.argtypes = []
         lib.aqmp_profile_reset.restype = None
         lib.aqmp_profile_read.argtypes = [V, I, ctypes.POINTER(I)]
+        lib.aqmp_profile_filter.argtypes = [ctypes.c_char_p]
         lib.aqmp_autotune_read.argtypes = [V, I, ctypes.POINTER(I)]
         lib.aqmp_autotune_reset.argtypes = []
         lib.aqmp_autotune_reset.restype = None
@@ -316,6 +317,11 @@ def aqmp_profile_read() -> dict:
     n = ctypes.c_int(0)
     _check(load_library().aqmp_profile_read(arr, 64, ctypes.byref(n)))
     return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(n.value)}
+
+
+def aqmp_profile_filter(prefix: str | None = None) -> None:
+    """Time only kernels whose name starts with `prefix` (None: all)."""
+    _check(load_library().aqmp_profile_filter(prefix.encode() if prefix else None))
 
 
 def aqmp_autotune_read() -> list:

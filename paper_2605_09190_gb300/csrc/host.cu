@@ -8,6 +8,8 @@
 
 #include <algorithm>
 #include <array>
+#include <atomic>
+#include <cstdlib>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -136,12 +138,17 @@ int encode_bf16_map(CUtensorMap *map, const void *base, unsigned long long rows,
 
 // ------------------------------------------------------------ context
 
+// Bumped whenever a workspace buffer moves: captured graphs hold its
+// addresses and are rebuilt after a move.
+std::atomic<unsigned long long> g_ws_generation{0};
+
 struct DeviceBuf {
     void *p = nullptr;
     size_t bytes = 0;
     ~DeviceBuf() { if (p) cudaFree(p); }
     int reserve(size_t want) {
         if (want <= bytes) return AQMP_OK;
+        g_ws_generation.fetch_add(1);
         if (p) { cudaFree(p); p = nullptr; bytes = 0; }
         want = std::max<size_t>(want, 256);
         cudaError_t e = cudaMalloc(&p, want);
@@ -156,8 +163,13 @@ struct DeviceBuf {
 struct Profiler {
     std::mutex mu;
     bool on = false;
-    struct Pending { std::string name; cudaEvent_t a, b; };
+    struct Pending { std::string name; cudaEvent_t a, b; bool owned = false; };
     std::vector<Pending> pending;
+    // While this thread captures a graph its events are the graph's own
+    // (created here, kept by the graph, queued again at every replay, never
+    // pooled).
+    static thread_local std::vector<Pending> *capture_to;
+    std::string filter;                // time only kernels whose name starts with this
     std::vector<cudaEvent_t> pool;
     std::map<std::string, std::pair<unsigned long long, double>> totals;
     cudaEvent_t get() {
@@ -169,12 +181,23 @@ struct Profiler {
     // Events around one launch; `launch` returns the launch's cudaError_t.
     template <class F>
     cudaError_t run(const std::string &name, cudaStream_t st, F &&launch) {
-        if (!on) return launch();
-        cudaEvent_t a = get(), b = get();
-        cudaEventRecord(a, st);
+        if (!on || name.compare(0, filter.size(), filter) != 0) return launch();
+        cudaEvent_t a = nullptr, b = nullptr;
+        if (capture_to) {
+            cudaEventCreate(&a);
+            cudaEventCreate(&b);
+        } else {
+            a = get();
+            b = get();
+        }
+        // in a graph, external event-record nodes: real records of the
+        // events each time the node runs, so replays can be timed
+        const unsigned flags = capture_to ? cudaEventRecordExternal : cudaEventRecordDefault;
+        cudaEventRecordWithFlags(a, st, flags);
         cudaError_t e = launch();
-        cudaEventRecord(b, st);
-        pending.push_back({name, a, b});
+        cudaEventRecordWithFlags(b, st, flags);
+        if (capture_to) capture_to->push_back({name, a, b, true});
+        else pending.push_back({name, a, b, false});
         return e;
     }
     // After the stream has been synchronised.
@@ -186,12 +209,15 @@ struct Profiler {
                 t.first += 1;
                 t.second += ms;
             }
-            pool.push_back(p.a);
-            pool.push_back(p.b);
+            if (!p.owned) {
+                pool.push_back(p.a);
+                pool.push_back(p.b);
+            }
         }
         pending.clear();
     }
 };
+thread_local std::vector<Profiler::Pending> *Profiler::capture_to = nullptr;
 Profiler g_prof;
 
 std::string kname(const char *k, int b) { return std::string(k) + "_b" + std::to_string(b); }
@@ -274,8 +300,28 @@ struct Ctx {
     bool gauss_ready = false;
     Tuner tuner;
     Counters *host_ctr = nullptr;             // pinned
-    PlaneDesc *host_planes = nullptr;         // pinned staging for plane descriptors
-    int host_planes_cap = 0;
+    unsigned char *host_call = nullptr;       // pinned: plane descriptors + output pointers
+    size_t host_call_cap = 0;
+    // Captured encodes, one per configuration (see aqmp_encode_planes).
+    struct Graph {
+        cudaGraphExec_t exec = nullptr;
+        unsigned long long generation = 0;
+        std::vector<Profiler::Pending> prof;
+    };
+    std::map<std::vector<long long>, Graph> graphs;
+    std::map<std::vector<long long>, int> seen;     // direct runs per configuration (-1: capture failed)
+    cudaStream_t graph_stream = nullptr;            // graphs run here (capture needs a non-legacy stream)
+    cudaEvent_t graph_in = nullptr, graph_out = nullptr;
+    void drop_graphs() {
+        for (auto &kv : graphs) {
+            if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+            for (auto &p : kv.second.prof) {
+                cudaEventDestroy(p.a);
+                cudaEventDestroy(p.b);
+            }
+        }
+        graphs.clear();
+    }
 };
 
 std::mutex g_ctx_mu;
@@ -449,6 +495,8 @@ void aqmp_autotune_reset(void) {
     std::lock_guard<std::mutex> lock(c->mu);
     c->tuner.slots.clear();
     c->tuner.pending.clear();
+    c->drop_graphs();                 // they embed the forgotten choices
+    c->seen.clear();
 }
 const char *aqmp_version(void) { return "aqmp-gb300 0.1 (sm_103a)"; }
 
@@ -524,7 +572,9 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
     const unsigned long long atom_cap =
         (npix * (unsigned long long)P.cap_num + P.cap_den - 1) / P.cap_den + leaf_cap;
 
-    if ((rc = c->planes.reserve(sizeof(PlaneDesc) * n_planes))) return rc;
+    const size_t out_off = (sizeof(PlaneDesc) * n_planes + 15) & ~(size_t)15;
+    const size_t call_bytes = out_off + sizeof(OrderOut);
+    if ((rc = c->planes.reserve(call_bytes))) return rc;
     if (!dev_in && (rc = c->staging.reserve(staged))) return rc;
     if ((rc = c->queues.reserve(sizeof(QueueEntry) * qoff[nlev]))) return rc;
     if ((rc = c->Y.reserve(sizeof(__nv_bfloat16) * ymax))) return rc;
@@ -575,16 +625,50 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
         d.pad = 0;
         roff += (unsigned long long)(pl.height / P.max_block) * (pl.width / P.max_block);
     }
-    if (c->host_planes_cap < n_planes) {
-        if (c->host_planes) cudaFreeHost(c->host_planes);
-        c->host_planes = nullptr;
-        c->host_planes_cap = 0;
-        CK(cudaMallocHost(&c->host_planes, sizeof(PlaneDesc) * n_planes));
-        c->host_planes_cap = n_planes;
+    if (c->host_call_cap < call_bytes) {
+        if (c->host_call) cudaFreeHost(c->host_call);
+        c->host_call = nullptr;
+        c->host_call_cap = 0;
+        g_ws_generation.fetch_add(1);
+        CK(cudaMallocHost((void **)&c->host_call, std::max<size_t>(call_bytes, 4096)));
+        c->host_call_cap = std::max<size_t>(call_bytes, 4096);
     }
-    std::memcpy(c->host_planes, pd.data(), sizeof(PlaneDesc) * n_planes);
-    CK(cudaMemcpyAsync(c->planes.p, c->host_planes, sizeof(PlaneDesc) * n_planes, cudaMemcpyHostToDevice, st));
+    std::memcpy(c->host_call, pd.data(), sizeof(PlaneDesc) * n_planes);
+    const OrderOut outs{code->leaves, code->atoms, code->alpha_lo};
+    std::memcpy(c->host_call + out_off, &outs, sizeof outs);
     Counters *ctr = (Counters *)c->counters.p;
+    const bool exact = P.precision == AQMP_PREC_EXACT;
+
+    // A configuration whose kernel choices are settled is captured as a CUDA
+    // graph on its second call and replayed from then on: everything from
+    // the upload of this block to the read-back of the counters (the block
+    // carries what changes between calls: plane addresses, tolerances and
+    // output arrays).  AQMP_GRAPHS=0 in the environment turns this off.
+    auto settled = [&]() {
+        if (!tune) return true;
+        for (int l = 0; l < nlev; ++l) {
+            const int b = P.max_block >> l;
+            if (!simt && c->tuner.slot(Tuner::CORR, b, P.dict_id, P.precision, cap[l]).chosen < 0) return false;
+            if (!alt_threads && mp_has_variant(b, dicts[l]->d.nf) &&
+                c->tuner.slot(Tuner::MP, b, P.dict_id, P.precision, cap[l]).chosen < 0)
+                return false;
+        }
+        return true;
+    };
+    std::vector<long long> key{n_planes, P.cap_num, P.cap_den, P.min_block, P.max_block, P.dict_id, P.precision,
+                               (long long)(P.flags & ~AQMP_FLAG_INPUT_DEVICE), dev_in ? 1 : 0, g_prof.on ? 1 : 0,
+                               g_prof.on ? (long long)std::hash<std::string>{}(g_prof.filter) : 0};
+    for (int i = 0; i < n_planes; ++i) {
+        key.push_back(planes[i].height);
+        key.push_back(planes[i].width);
+    }
+    static const bool graphs_on = [] {
+        const char *v = std::getenv("AQMP_GRAPHS");
+        return !(v && v[0] == '0');
+    }();
+
+    auto body = [&](cudaStream_t st) -> int {
+    CK(cudaMemcpyAsync(c->planes.p, c->host_call, call_bytes, cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(ctr, 0, sizeof(Counters), st));
     CK(cudaMemsetAsync(c->cells.p, 0, sizeof(uint32_t) * n_cells, st));
     CK(cudaMemsetAsync(c->order_status.p, 0, sizeof(unsigned long long) * status_words, st));
@@ -662,7 +746,6 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
         ma.atom_cap = atom_cap;
         ma.cells = cells;
         ma.ctr = ctr;
-        const bool exact = P.precision == AQMP_PREC_EXACT;
         auto mp = [&](int v) {
             return g_prof.run(kname(exact ? "mp" : "mp_fp32", b), st,
                               [&] { return launch_mp(ma, d.nf, exact, v, c->num_sms, st); });
@@ -694,9 +777,7 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
     oa.atom_cap = atom_cap;
     oa.perm = (uint32_t *)c->perm.p;
     oa.status = (unsigned long long *)c->order_status.p;
-    oa.leaves_out = code->leaves;
-    oa.atoms_out = code->atoms;
-    oa.lo_out = code->alpha_lo;
+    oa.out = (const OrderOut *)((unsigned char *)c->planes.p + out_off);
     oa.ctr = ctr;
     oa.limit_ns = 2000000000ull;
     CK(g_prof.run("order_rank", st, [&] { return launch_order_phase(oa, 0, c->num_sms, st); }));
@@ -704,6 +785,73 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
     CK(g_prof.run("order_copy", st, [&] { return launch_order_phase(oa, 2, c->num_sms, st); }));
 
     CK(cudaMemcpyAsync(c->host_ctr, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+    return AQMP_OK;
+    };
+
+    // a graph runs on the library's own stream, ordered after the caller's
+    // prior work and before its later work
+    auto replay = [&](Ctx::Graph &gr) -> int {
+        CK(cudaEventRecord(c->graph_in, st));
+        CK(cudaStreamWaitEvent(c->graph_stream, c->graph_in, 0));
+        CK(cudaGraphLaunch(gr.exec, c->graph_stream));
+        CK(cudaEventRecord(c->graph_out, c->graph_stream));
+        CK(cudaStreamWaitEvent(st, c->graph_out, 0));
+        if (!gr.prof.empty()) {
+            std::lock_guard<std::mutex> pl(g_prof.mu);
+            for (const auto &p : gr.prof) g_prof.pending.push_back(p);
+        }
+        return AQMP_OK;
+    };
+    auto git = c->graphs.find(key);
+    if (git != c->graphs.end() && git->second.generation != g_ws_generation.load()) {
+        c->drop_graphs();
+        git = c->graphs.end();
+    }
+    if (graphs_on && git != c->graphs.end()) {
+        if ((rc = replay(git->second))) return rc;
+    } else {
+        if (c->seen.size() > 1024) c->seen.clear();
+        int &runs = c->seen[key];
+        bool done = false;
+        if (graphs_on && runs >= 1 && settled()) {
+            runs = -1;                            // unless the capture below succeeds
+            if (c->graphs.size() >= 32) c->drop_graphs();
+            if (!c->graph_stream) {
+                CK(cudaStreamCreateWithFlags(&c->graph_stream, cudaStreamNonBlocking));
+                CK(cudaEventCreateWithFlags(&c->graph_in, cudaEventDisableTiming));
+                CK(cudaEventCreateWithFlags(&c->graph_out, cudaEventDisableTiming));
+            }
+            Ctx::Graph gr;
+            gr.generation = g_ws_generation.load();
+            cudaGraph_t graph = nullptr;
+            if (cudaStreamBeginCapture(c->graph_stream, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+                Profiler::capture_to = &gr.prof;
+                const int brc = body(c->graph_stream);
+                Profiler::capture_to = nullptr;
+                const cudaError_t ec = cudaStreamEndCapture(c->graph_stream, &graph);
+                if (brc == AQMP_OK && ec == cudaSuccess && graph &&
+                    cudaGraphInstantiate(&gr.exec, graph, 0) == cudaSuccess) {
+                    cudaGraphDestroy(graph);
+                    auto &slot = c->graphs[key];
+                    slot = std::move(gr);
+                    if ((rc = replay(slot))) return rc;
+                    runs = 1;
+                    done = true;
+                } else {
+                    if (graph) cudaGraphDestroy(graph);
+                    for (auto &p : gr.prof) {
+                        cudaEventDestroy(p.a);
+                        cudaEventDestroy(p.b);
+                    }
+                }
+            }
+            cudaGetLastError();
+        }
+        if (!done) {
+            if ((rc = body(st))) return rc;
+            if (runs >= 0) ++runs;
+        }
+    }
     CK(cudaStreamSynchronize(st));
     {
         std::lock_guard<std::mutex> pl(g_prof.mu);
@@ -929,6 +1077,12 @@ int aqmp_profile_enable(int on) {
 void aqmp_profile_reset(void) {
     std::lock_guard<std::mutex> g(g_prof.mu);
     g_prof.totals.clear();
+}
+
+int aqmp_profile_filter(const char *prefix) {
+    std::lock_guard<std::mutex> g(g_prof.mu);
+    g_prof.filter = prefix ? prefix : "";
+    return AQMP_OK;
 }
 
 int aqmp_profile_read(aqmp_kernel_time *out, int max, int *n) {

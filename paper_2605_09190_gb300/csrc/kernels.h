@@ -113,6 +113,11 @@ cudaError_t launch_seed_roots(const PlaneDesc *planes, int n_planes, int max_blo
 // single-pass scans with decoupled look-back over tiles claimed in launch
 // order; `status` (order_status_words(n_cells, leaf_cap) 64-bit words) must
 // be zero before phase 0.
+struct OrderOut {                      // read from device memory, so that a captured
+    LeafRec *leaves;                   // graph serves calls with different outputs
+    AtomRec *atoms;
+    float *lo;
+};
 struct OrderArgs {
     CellMap cells;
     const LeafRec *leaves_in;
@@ -124,9 +129,7 @@ struct OrderArgs {
     uint32_t *perm;                    // leaf_cap words
     uint32_t *new_off;                 // leaf_cap words: new atom offset by slot
     unsigned long long *status;
-    LeafRec *leaves_out;
-    AtomRec *atoms_out;
-    float *lo_out;
+    const OrderOut *out;               // device: the call's output arrays
     Counters *ctr;
     unsigned long long limit_ns;       // bound on every look-back wait
 };

@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(kOrderThreads) order_offsets_kernel(OrderArgs 
     if (ok && dst + x <= a.atom_cap) {
         a.new_off[i] = (uint32_t)dst;
         rec.atom_off = (uint32_t)dst;
-        a.leaves_out[r] = rec;
+        a.out->leaves[r] = rec;
     }
 }
 
@@ -214,6 +214,8 @@ __global__ void __launch_bounds__(kOrderThreads) order_copy_kernel(OrderArgs a) 
     if (n > a.atom_cap) n = a.atom_cap;
     unsigned long long nl = *a.n_leaves;
     if (nl > a.leaf_cap) nl = a.leaf_cap;
+    AtomRec *atoms_out = a.out->atoms;
+    float *lo_out = a.out->lo;
     for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < n;
          k += (unsigned long long)gridDim.x * blockDim.x) {
         const uint32_t slot = a.atom_leaf[k];
@@ -222,8 +224,8 @@ __global__ void __launch_bounds__(kOrderThreads) order_copy_kernel(OrderArgs a) 
         if (k < src0) continue;
         const unsigned long long to = (unsigned long long)a.new_off[slot] + (k - src0);
         if (to < a.atom_cap) {
-            a.atoms_out[to] = a.atoms_in[k];
-            a.lo_out[to] = a.lo_in[k];
+            atoms_out[to] = a.atoms_in[k];
+            lo_out[to] = a.lo_in[k];
         }
     }
 }
