@@ -62,8 +62,10 @@ def _configure(lib):
     lib.oracle_dictionary.restype = I
     lib.oracle_mp.argtypes = [P, I, I, P, Dbl, I, P, P, P, P, P]
     lib.oracle_mp.restype = I
+    lib.oracle_omp.argtypes = [P, I, I, P, Dbl, I, P, P, P, P, P]
+    lib.oracle_omp.restype = I
     lib.oracle_encode_roots.argtypes = [P, L, I, I, I, Dbl, I, I, I, I, I, P, L, L,
-                                        P, L, P, P, P, L, P, P, P]
+                                        P, L, P, P, P, L, P, P, P, I]
     lib.oracle_encode_roots.restype = I
     lib.oracle_decode_leaf.argtypes = [P, I, I, I, P, P, I, P, L]
     return lib
@@ -168,8 +170,10 @@ def unravel(block: np.ndarray) -> np.ndarray:
     return np.ascontiguousarray(np.asarray(block, np.float64).T).reshape(-1)
 
 
-def mp(D: np.ndarray, y: np.ndarray, eps2: float, k: int) -> dict:
-    """Matching Pursuit on one vector (Section 2.2 with Eq. (3))."""
+def mp(D: np.ndarray, y: np.ndarray, eps2: float, k: int, algorithm: str = "mp") -> dict:
+    """Matching Pursuit on one vector (Section 2.2 with Eq. (3)); with
+    algorithm="omp", Orthogonal Matching Pursuit (least-squares re-fit of the
+    support after every selection; `alpha` holds the final coefficients)."""
     D = np.ascontiguousarray(D, np.float64)
     y = np.ascontiguousarray(y, np.float64)
     M, n = D.shape
@@ -178,10 +182,11 @@ def mp(D: np.ndarray, y: np.ndarray, eps2: float, k: int) -> dict:
     mg = np.zeros(max(k, 1), np.float64)
     en = np.zeros(k + 1, np.float64)
     conv = ctypes.c_int(0)
-    t = _load().oracle_mp(_ptr(D), n, M, _ptr(y), float(eps2), int(k), _ptr(j), _ptr(al),
-                          _ptr(mg), _ptr(en), ctypes.byref(conv))
+    fn = _load().oracle_omp if algorithm == "omp" else _load().oracle_mp
+    t = fn(_ptr(D), n, M, _ptr(y), float(eps2), int(k), _ptr(j), _ptr(al), _ptr(mg), _ptr(en),
+           ctypes.byref(conv))
     if t < 0:
-        raise MemoryError("oracle_mp allocation failed")
+        raise MemoryError("oracle pursuit allocation failed")
     return {"j": j[:t].copy(), "alpha": al[:t].copy(), "margin": mg[:t].copy(),
             "energy": en[:t + 1].copy(), "converged": bool(conv.value), "steps": t}
 
@@ -217,7 +222,7 @@ def _dict_ptrs(min_block, max_block, dict_id):
 
 
 def encode(planes, tols, cap_num=1, cap_den=4, min_block=4, max_block=64, dict_id=0,
-           roots=None, threads=None) -> Encoding:
+           roots=None, threads=None, algorithm: str = "mp") -> Encoding:
     """Algorithms 1-2 over a list of 2-D uint8 planes, one tolerance per plane.
 
     ``roots`` optionally restricts plane p to the root indices ``roots[p]``
@@ -255,7 +260,7 @@ def encode(planes, tols, cap_num=1, cap_den=4, min_block=4, max_block=64, dict_i
                                      min_block, max_block, dict_id, ptrs, r, r + 1,
                                      _ptr(lv), cap_leaves, ctypes.byref(nl), _ptr(aj), _ptr(aa),
                                      cap_atoms, ctypes.byref(na), ctypes.byref(att),
-                                     ctypes.byref(st))
+                                     ctypes.byref(st), 1 if algorithm == "omp" else 0)
         if rc != 0:
             raise RuntimeError(f"oracle_encode_roots failed with {rc}")
         return lv[:nl.value], aj[:na.value], aa[:na.value], att.value, st.value

@@ -18,6 +18,8 @@
  *   - unravel = concatenation of the block's columns (Appendix A).
  *   - Matching Pursuit steps (a)-(d) of Section 2.2 with the stopping rule
  *     Eq. (3): stop when ||Dx - y||_2 < eps or after k steps.
+ *   - Orthogonal Matching Pursuit (the solver the authors ran, Section 2.2):
+ *     the same selection, with a least-squares re-fit of the support.
  *   - mp_encoder_rec, Algorithm 2: a block that misses the tolerance within
  *     its budget is replaced by its four quadrants of the ORIGINAL pixels.
  *   - mp_decoder, Algorithm 3: y = D_N x, un-ravel, place.
@@ -207,6 +209,126 @@ int oracle_mp(const double *D, int n, int M, const double *y, double eps2, int k
     return t;
 }
 
+/* OMP(D, y, eps, k): Orthogonal Matching Pursuit, the solver the authors
+ * ran (Section 2.2 names it in place of plain MP and cites the
+ * scikit-learn implementation).  Selection, tie rule and stop rule are those
+ * of oracle_mp; after each selection every coefficient on the support S is
+ * re-fitted by least squares, x_S = argmin ||y - D_S x||, through the normal
+ * equations G_SS x = D_S^T y (G_SS = D_S^T D_S), solved by a Cholesky
+ * factorisation computed afresh each step; the residual r = y - D_S x_S is
+ * then formed explicitly.  Readings: a new atom whose Cholesky pivot (the
+ * squared norm of its part outside span(D_S)) is <= 2^-40 ends the pursuit
+ * unconverged (scikit-learn also stops on linear dependence); so does a
+ * residual whose largest |correlation| is <= TIE_REL ||y|| (zero to the
+ * precision of the tie rule).  Outputs: the support in selection order
+ * (out_j) and the final coefficients (out_alpha[t] belongs to out_j[t]),
+ * per-step margins and energies as oracle_mp.  Returns |S|. */
+#define PIVOT_MIN 0x1p-40
+
+int oracle_omp(const double *D, int n, int M, const double *y, double eps2, int k,
+               int32_t *out_j, double *out_alpha, double *out_margin,
+               double *out_energy, int *converged)
+{
+    double *r = malloc(sizeof(double) * n);
+    double *c = malloc(sizeof(double) * M);
+    double *G = malloc(sizeof(double) * (size_t)(k + 1) * (k + 1));
+    double *L = malloc(sizeof(double) * (size_t)(k + 1) * (k + 1));
+    double *rhs = malloc(sizeof(double) * (k + 1));
+    double *x = malloc(sizeof(double) * (k + 1));
+    int32_t *S = malloc(sizeof(int32_t) * (k + 1));
+    if (!r || !c || !G || !L || !rhs || !x || !S) {
+        free(r); free(c); free(G); free(L); free(rhs); free(x); free(S);
+        return -2;
+    }
+    memcpy(r, y, sizeof(double) * n);
+    double S2 = 0.0;
+    for (int v = 0; v < n; ++v) S2 += y[v] * y[v];
+    const double tie_c = TIE_REL * sqrt(S2), tie_e = TIE_REL * S2;
+    int t = 0;
+    *converged = 0;
+    for (;;) {
+        double E = 0.0;
+        for (int v = 0; v < n; ++v) E += r[v] * r[v];
+        if (out_energy) out_energy[t] = E;
+        if (E < eps2 - tie_e) { *converged = 1; break; }
+        if (t == k) break;
+        for (int j = 0; j < M; ++j) {                 /* c = D^T r */
+            const double *phi = D + (size_t)j * n;
+            double s = 0.0;
+            for (int v = 0; v < n; ++v) s += phi[v] * r[v];
+            c[j] = s;
+        }
+        double cmax = 0.0;
+        for (int j = 0; j < M; ++j)
+            if (fabs(c[j]) > cmax) cmax = fabs(c[j]);
+        if (cmax <= tie_c) break;
+        const double edge = cmax - tie_c;
+        int best = 0;
+        while (fabs(c[best]) < edge) ++best;
+        const double *pb = D + (size_t)best * n;
+        double margin = INFINITY;
+        for (int j = 0; j < M; ++j) {
+            if (j == best) continue;
+            double d = fabs(fabs(c[j]) - edge);
+            if (d >= margin) continue;
+            if (memcmp(D + (size_t)j * n, pb, sizeof(double) * n) == 0) continue;
+            margin = d;
+        }
+        /* normal equations of the enlarged support, factorised afresh */
+        S[t] = best;
+        const int m = t + 1;
+        for (int a = 0; a < m; ++a) {
+            const double *pa = D + (size_t)S[a] * n;
+            for (int b = 0; b < m; ++b) {
+                const double *pbb = D + (size_t)S[b] * n;
+                double s = 0.0;
+                for (int v = 0; v < n; ++v) s += pa[v] * pbb[v];
+                G[a * m + b] = s;
+            }
+            double s = 0.0;
+            for (int v = 0; v < n; ++v) s += pa[v] * y[v];
+            rhs[a] = s;
+        }
+        int dependent = 0;
+        for (int a = 0; a < m && !dependent; ++a) {   /* G = L L^T */
+            for (int b = 0; b <= a; ++b) {
+                double s = G[a * m + b];
+                for (int q = 0; q < b; ++q) s -= L[a * m + q] * L[b * m + q];
+                if (a == b) {
+                    if (s <= PIVOT_MIN) { dependent = 1; break; }
+                    L[a * m + a] = sqrt(s);
+                } else {
+                    L[a * m + b] = s / L[b * m + b];
+                }
+            }
+        }
+        if (dependent) break;
+        for (int a = 0; a < m; ++a) {                 /* L z = rhs */
+            double s = rhs[a];
+            for (int q = 0; q < a; ++q) s -= L[a * m + q] * x[q];
+            x[a] = s / L[a * m + a];
+        }
+        for (int a = m - 1; a >= 0; --a) {            /* L^T x = z */
+            double s = x[a];
+            for (int q = a + 1; q < m; ++q) s -= L[q * m + a] * x[q];
+            x[a] = s / L[a * m + a];
+        }
+        for (int v = 0; v < n; ++v) {                 /* r = y - D_S x_S */
+            double s = y[v];
+            for (int a = 0; a < m; ++a) s -= x[a] * D[(size_t)S[a] * n + v];
+            r[v] = s;
+        }
+        if (out_margin) out_margin[t] = margin;
+        ++t;
+    }
+    for (int a = 0; a < t; ++a) {
+        if (out_j) out_j[a] = S[a];
+        if (out_alpha) out_alpha[a] = x[a];
+    }
+    free(r); free(c); free(G); free(L); free(rhs); free(x); free(S);
+    return t;
+}
+
 /* ----------------------------------------------------- quadtree encoder */
 
 typedef struct {
@@ -218,7 +340,7 @@ typedef struct {
 
 typedef struct {
     const uint8_t *pix; long pitch;
-    double tol; int cap_num, cap_den, min_block, dict_id, plane;
+    double tol; int cap_num, cap_den, min_block, dict_id, plane, alg;   /* alg: 0 MP, 1 OMP */
     double *const *dicts;        /* dicts[log2 b] */
     oracle_leaf *leaves; long n_leaves, cap_leaves;
     int32_t *atom_j; double *atom_alpha; long n_atoms, cap_atoms;
@@ -246,7 +368,9 @@ static void rec(enc_ctx *c, int y0, int x0, int b)
         for (int i = 0; i < b; ++i)
             y[m * b + i] = (double)c->pix[(long)(y0 + i) * c->pitch + x0 + m];
     int conv = 0;
-    int steps = oracle_mp(D, n, M, y, eps2, k, js, al, mg, NULL, &conv);
+    int steps = c->alg ? oracle_omp(D, n, M, y, eps2, k, js, al, mg, NULL, &conv)
+                       : oracle_mp(D, n, M, y, eps2, k, js, al, mg, NULL, &conv);
+    if (steps < 0) { c->err = steps; goto out; }
     c->attempts += 1;
     c->steps += steps;
     if (!conv && b > c->min_block) {               /* split: original pixels */
@@ -284,11 +408,11 @@ int oracle_encode_roots(const uint8_t *pix, long pitch, int h, int w, int plane,
                         long root_begin, long root_end,
                         oracle_leaf *leaves, long cap_leaves, long *n_leaves,
                         int32_t *atom_j, double *atom_alpha, long cap_atoms,
-                        long *n_atoms, long *attempts, long *steps)
+                        long *n_atoms, long *attempts, long *steps, int alg)
 {
     if (max_block < min_block || h % max_block || w % max_block || cap_den <= 0)
         return -1;
-    enc_ctx c = {pix, pitch, tol, cap_num, cap_den, min_block, dict_id, plane, dicts,
+    enc_ctx c = {pix, pitch, tol, cap_num, cap_den, min_block, dict_id, plane, alg, dicts,
                  leaves, 0, cap_leaves, atom_j, atom_alpha, 0, cap_atoms, 0, 0, 0};
     long roots_x = w / max_block;
     for (long r = root_begin; r < root_end && !c.err; ++r)
