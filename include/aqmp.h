@@ -66,6 +66,15 @@ extern "C" {
 #define AQMP_FLAG_ALT_THREADS   8u /* run the pursuit with the alternate number of
                                       threads per leaf at sides 16, 32 and 64
                                       (bit-identical result; for validation) */
+#define AQMP_FLAG_OMP          16u /* Orthogonal Matching Pursuit (the solver the
+                                      paper's authors ran, Section 2.2) instead
+                                      of MP: after each selection the support's
+                                      coefficients are re-fitted by least
+                                      squares (FP64 Cholesky); the emitted
+                                      coefficients are the final fit.  Needs
+                                      max_block <= 16, AQMP_PREC_EXACT and a
+                                      budget of at most 64 atoms per leaf
+                                      (else AQMP_E_UNSUPPORTED) */
 /* Autotuning: kernel choices that leave the result unchanged bit for bit
  * are measured on the first calls of each configuration and the fastest
  * is kept for the life of the process: the initial correlation on the

@@ -29,6 +29,7 @@ AQMP_FLAG_INPUT_DEVICE = 1
 AQMP_FLAG_SIMT_GEMM = 2
 AQMP_FLAG_NO_AUTOTUNE = 4
 AQMP_FLAG_ALT_THREADS = 8
+AQMP_FLAG_OMP = 16
 AQMP_LEAF_NEAR_TIE = 1
 AQMP_LEAF_NEAR_TIE_PARENT = 2
 
@@ -212,7 +213,7 @@ def _as_plane(x, tol, device_input):
 
 
 def aqmp_encode_planes(planes, tols=None, params: aqmp_params | None = None, stream=None, simt_gemm=False,
-                       autotune=True, alt_threads=False, **param_kw) -> Code:
+                       autotune=True, alt_threads=False, omp=False, **param_kw) -> Code:
     """Encode a list of 2-D uint8 planes (torch CUDA tensors, or host numpy
     arrays / CPU tensors), one optional tolerance per plane."""
     if params is None:
@@ -229,7 +230,7 @@ def aqmp_encode_planes(planes, tols=None, params: aqmp_params | None = None, str
     p = aqmp_params.from_buffer_copy(params)
     p.flags = (p.flags | (AQMP_FLAG_INPUT_DEVICE if device_input else 0)
                | (AQMP_FLAG_SIMT_GEMM if simt_gemm else 0) | (0 if autotune else AQMP_FLAG_NO_AUTOTUNE)
-               | (AQMP_FLAG_ALT_THREADS if alt_threads else 0))
+               | (AQMP_FLAG_ALT_THREADS if alt_threads else 0) | (AQMP_FLAG_OMP if omp else 0))
     out = ctypes.c_void_p()
     _check(load_library().aqmp_encode_planes(ctypes.byref(p), arr, len(planes), _stream_handle(stream),
                                              ctypes.byref(out)))

@@ -530,6 +530,13 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
     const bool simt = (P.flags & AQMP_FLAG_SIMT_GEMM) != 0;
     const bool tune = (P.flags & AQMP_FLAG_NO_AUTOTUNE) == 0;
     const bool alt_threads = (P.flags & AQMP_FLAG_ALT_THREADS) != 0;
+    const bool omp = (P.flags & AQMP_FLAG_OMP) != 0;
+    if (omp) {
+        if (P.max_block > 16 || P.precision != AQMP_PREC_EXACT)
+            return fail(AQMP_E_UNSUPPORTED, "OMP needs max_block <= 16 and the exact precision");
+        if ((long long)P.max_block * P.max_block * P.cap_num / P.cap_den > omp_max_budget())
+            return fail(AQMP_E_UNSUPPORTED, "OMP budget above %d atoms per leaf", omp_max_budget());
+    }
     unsigned long long npix = 0, roots = 0, staged = 0;
     for (int i = 0; i < n_planes; ++i) {
         const aqmp_plane &pl = planes[i];
@@ -649,7 +656,7 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
         for (int l = 0; l < nlev; ++l) {
             const int b = P.max_block >> l;
             if (!simt && c->tuner.slot(Tuner::CORR, b, P.dict_id, P.precision, cap[l]).chosen < 0) return false;
-            if (!alt_threads && mp_has_variant(b, dicts[l]->d.nf) &&
+            if (!alt_threads && !omp && mp_has_variant(b, dicts[l]->d.nf) &&
                 c->tuner.slot(Tuner::MP, b, P.dict_id, P.precision, cap[l]).chosen < 0)
                 return false;
         }
@@ -750,7 +757,9 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
             return g_prof.run(kname(exact ? "mp" : "mp_fp32", b), st,
                               [&] { return launch_mp(ma, d.nf, exact, v, c->num_sms, st); });
         };
-        if (alt_threads || !tune || !mp_has_variant(b, d.nf)) {
+        if (omp) {
+            CK(g_prof.run(kname("omp", b), st, [&] { return launch_omp(ma, d.nf, c->num_sms, st); }));
+        } else if (alt_threads || !tune || !mp_has_variant(b, d.nf)) {
             CK(mp(alt_threads ? 1 : 0));
         } else {
             Tuner::Slot &ts = c->tuner.slot(Tuner::MP, b, P.dict_id, P.precision, cap[l]);

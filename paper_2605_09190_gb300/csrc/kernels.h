@@ -32,6 +32,12 @@ struct MPArgs {
 cudaError_t launch_mp(const MPArgs &a, int nf, bool double_float, int variant, int num_sms, cudaStream_t st);
 bool mp_has_variant(int b, int nf);
 
+// Orthogonal Matching Pursuit of one level (omp.cu): sides 4, 8, 16, budget
+// k <= omp_max_budget(); same arguments and outputs as the MP kernel (the
+// coefficients emitted are the final least-squares values).
+int omp_max_budget();
+cudaError_t launch_omp(const MPArgs &a, int nf, int num_sms, cudaStream_t st);
+
 // Block gather (gather.cu): queue entries -> centred BF16 leaf vectors
 // (column-major unravel, zero padded to Kpad) and sums of squares.
 struct GatherArgs {
