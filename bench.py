@@ -193,6 +193,65 @@ def run_uneven(args):
     return 0
 
 
+OMP_WORKLOAD = ("piecewise-planar synthetic 512x512 gray, RMSE tol sweep {1,2,4,8} batched as 4 planes, "
+                "quadtree 16->4, k=b^2/4, DCT-II+Haar, Orthogonal Matching Pursuit (FP64 least-squares re-fit)")
+
+
+def run_omp(args):
+    """OMP (the authors' solver) on the sweep's planes with 16x16 roots,
+    and MP on the same configuration for comparison."""
+    import torch
+    from paper_2605_09190_gb300 import aqmp, build_lib
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local if world > 1 else 0)
+    dist_init("nccl")
+    build_lib.build()
+    dev = [torch.from_numpy(p).cuda() for p in workload_planes()]
+    npix = sum(int(p.numel()) for p in dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(omp):
+        encode = lambda: aqmp.aqmp_encode_planes(dev, TOLS, min_block=MIN_BLOCK, max_block=16, omp=omp)  # noqa: E731
+        settle_autotuner(aqmp, encode)
+        breakdown, top, per_call = kernel_breakdown(aqmp, encode, lambda: flush.zero_())
+        for _ in range(args.warmup):
+            flush.zero_()
+            encode().free()
+        ms, stats = [], None
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            code = encode()
+            e1.record(stream)
+            stats = code.stats()
+            code.free()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return max_over_ranks(sum(ms) / 1e3, device="cuda"), breakdown, per_call, stats
+
+    with ClockSampler(local) as clocks:
+        omp_s, breakdown, per_call, st = timed(True)
+        mp_s, _, _, mst = timed(False)
+    if rank == 0:
+        tot = sum(v[1] for v in breakdown.values())
+        print(json.dumps({"metric": METRIC, "value": weak_scaling_value(npix, args.steps, omp_s, world),
+                          "unit": "MP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": 1e3 * omp_s / args.steps, "higher_is_better": True, "scaling": "weak",
+                          "vs_baseline": None, "dtype": "fp64 pursuit + bf16-limb tensor GEMM", "data": "synthetic",
+                          "config": {"workload": OMP_WORKLOAD, "planes_per_step": len(dev), "pixels_per_step": npix,
+                                     "input": "device-resident", "l2": "flushed between steps (256 MB write)"},
+                          "atoms_per_step": st["n_atoms"], "leaves_per_step": st["n_leaves"],
+                          "mp_same_config": {"value": weak_scaling_value(npix, args.steps, mp_s, world),
+                                             "atoms_per_step": mst["n_atoms"], "leaves_per_step": mst["n_leaves"]},
+                          "kernels": {k: {"launches": v[0], "ms": round(v[1], 4), "share": round(v[1] / tot, 4)}
+                                      for k, v in sorted(breakdown.items(), key=lambda kv: -kv[1][1])},
+                          "gpu_launches": int(round(per_call * args.steps)),
+                          "clocks": clocks.summary()}))
+    return 0
+
+
 def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
         int(os.environ.get("LOCAL_RANK", "0"))
@@ -543,9 +602,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["sweep512", "uneven64", "refine16"], default="sweep512",
+    ap.add_argument("--workload", choices=["sweep512", "uneven64", "refine16", "omp512"], default="sweep512",
                     help="sweep512: the 512x512 tolerance sweep (default); uneven64: 64 uneven RGB images; "
-                         "refine16: coefficient refinement on 16 images (steps = Adam steps)")
+                         "refine16: coefficient refinement on 16 images (steps = Adam steps); "
+                         "omp512: the sweep's planes with 16x16 roots, Orthogonal Matching Pursuit")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -553,6 +613,8 @@ def main():
         return run_uneven(args)
     if args.workload == "refine16":
         return run_refine(args)
+    if args.workload == "omp512":
+        return run_omp(args)
     return run_ours(args)
 
 

@@ -66,17 +66,23 @@ __global__ void __launch_bounds__(256, 1) omp_kernel(MPArgs a) {
     constexpr int n = B * B;
     constexpr int M = NF * n;
     constexpr int E = (M + 31) / 32;
+    // SLOTS: with two families and n a multiple of 32, element (lane, s) is
+    // atom lane + 32 s, DCT for s < E/2, and its in-family (p, q) is
+    // (lane mod B, lane / B + (32 / B) s, less B for the Haar slots)
+    constexpr bool SLOTS = NF == 2 && (n % 32) == 0;
 
     extern __shared__ __align__(16) unsigned char smem[];
     double *sW = reinterpret_cast<double *>(smem);
     const int k = a.lv.k;
-    const int per = tri(k) + 2 * k;                      // L, x_S, c0_S (doubles)
+    const int per = tri(k) + 3 * k + M;                  // L, x_S, c0_S, 1 / L_ii, dense x (doubles)
     const int warps = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double *base = sW + (NF == 2 ? B * B : 0);
     double *L = base + (size_t)warp * per;
     double *xs = L + tri(k);
     double *c0s = xs + k;
+    double *rdiag = c0s + k;
+    double *xd = rdiag + k;                              // x_S scattered over all M atoms
     uint32_t *Sj = reinterpret_cast<uint32_t *>(base + (size_t)warps * per) + (size_t)warp * k;
 
     if (NF == 2)
@@ -86,6 +92,7 @@ __global__ void __launch_bounds__(256, 1) omp_kernel(MPArgs a) {
     const LevelArgs &lv = a.lv;
     const unsigned count = *lv.count;
     unsigned *work = &a.ctr->work_next[lv.level];
+    const uint32_t p_own = (uint32_t)lane % B, q_own = (uint32_t)lane / B;
 
     for (;;) {
         unsigned leaf = lane == 0 ? atomicAdd(work, 1u) : 0u;
@@ -108,6 +115,8 @@ __global__ void __launch_bounds__(256, 1) omp_kernel(MPArgs a) {
             c0r[s] = j < M ? (double)cp[j].x + (double)cp[j].y : 0.0;
         }
 
+        for (int i = lane; i < M; i += 32) xd[i] = 0.0;
+        __syncwarp();
         int nS = 0;
         bool conv = false, tie = false;
         for (;;) {
@@ -119,20 +128,48 @@ __global__ void __launch_bounds__(256, 1) omp_kernel(MPArgs a) {
             if (En < thr_e) { conv = true; break; }
             if (nS == k) break;
 
-            // residual correlations and their largest magnitude
+            // residual correlations c = c0 - G[:, S] x_S
             double cv[E];
+#pragma unroll
+            for (int s = 0; s < E; ++s) cv[s] = c0r[s];
+            if (SLOTS) {
+                // slots [0, E/2) hold DCT atoms, [E/2, E) Haar atoms, and a
+                // lane's atoms share p = lane mod B: a support atom of one
+                // family reaches the other family's slots through
+                // W[p_d][p_h] (one factor per lane) times W[q_d][q_h]
+                for (int i = 0; i < nS; ++i) {
+                    const uint32_t sa = Sj[i];
+                    const double x = xs[i];
+                    if (sa < (uint32_t)n) {
+                        const uint32_t ps = sa % B, qs = sa / B;
+                        const double ax = x * sW[ps * B + p_own];
+#pragma unroll
+                        for (int s = E / 2; s < E; ++s) cv[s] -= ax * sW[qs * B + q_own + (32 / B) * s - B];
+                    } else {
+                        const uint32_t ps = (sa - n) % B, qs = (sa - n) / B;
+                        const double ax = x * sW[p_own * B + ps];
+#pragma unroll
+                        for (int s = 0; s < E / 2; ++s) cv[s] -= ax * sW[(q_own + (32 / B) * s) * B + qs];
+                    }
+                }
+            } else if (NF == 2) {
+#pragma unroll
+                for (int s = 0; s < E; ++s) {
+                    const uint32_t j = lane + 32 * s;
+                    if (j >= (uint32_t)M) continue;
+                    for (int i = 0; i < nS; ++i)
+                        if ((Sj[i] >= (uint32_t)n) != (j >= (uint32_t)n)) cv[s] -= gram<B, NF>(sW, j, Sj[i]) * xs[i];
+                }
+            }
+            // the diagonal: each support atom's own coefficient, kept dense
+#pragma unroll
+            for (int s = 0; s < E; ++s)
+                if (lane + 32 * s < M) cv[s] -= xd[lane + 32 * s];
             double amax = 0.0;
 #pragma unroll
             for (int s = 0; s < E; ++s) {
-                const uint32_t j = lane + 32 * s;
-                double c = c0r[s];
-                if (j < (uint32_t)M) {
-                    for (int i = 0; i < nS; ++i) c -= gram<B, NF>(sW, j, Sj[i]) * xs[i];
-                } else {
-                    c = 0.0;
-                }
-                cv[s] = c;
-                amax = fmax(amax, fabs(c));
+                if ((uint32_t)(lane + 32 * s) >= (uint32_t)M) cv[s] = 0.0;
+                amax = fmax(amax, fabs(cv[s]));
             }
             amax = warp_max(amax);
             if (amax <= tie_c) break;                        // nothing left to remove
@@ -158,7 +195,7 @@ __global__ void __launch_bounds__(256, 1) omp_kernel(MPArgs a) {
             double g1 = lane + 32 < nS ? gram<B, NF>(sW, Sj[lane + 32], jb) : 0.0;
             for (int i = 0; i < nS; ++i) {
                 double wi = 0.0;
-                if (lane == (i & 31)) wi = (i < 32 ? g0 : g1) / L[tri(i) + i];
+                if (lane == (i & 31)) wi = (i < 32 ? g0 : g1) * rdiag[i];
                 wi = __shfl_sync(0xffffffffu, wi, i & 31);
                 if (lane == (i & 31)) {
                     if (i < 32) g0 = wi; else g1 = wi;
@@ -174,7 +211,9 @@ __global__ void __launch_bounds__(256, 1) omp_kernel(MPArgs a) {
             if (lane < nS) L[rb + lane] = g0;
             if (lane + 32 < nS) L[rb + lane + 32] = g1;
             if (lane == 0) {
-                L[rb + nS] = sqrt(d);
+                const double ld = sqrt(d);
+                L[rb + nS] = ld;
+                rdiag[nS] = 1.0 / ld;
                 Sj[nS] = jb;
                 c0s[nS] = c0b;
             }
@@ -186,7 +225,7 @@ __global__ void __launch_bounds__(256, 1) omp_kernel(MPArgs a) {
             double z1 = lane + 32 < nS ? c0s[lane + 32] : 0.0;
             for (int i = 0; i < nS; ++i) {
                 double zi = 0.0;
-                if (lane == (i & 31)) zi = (i < 32 ? z0 : z1) / L[tri(i) + i];
+                if (lane == (i & 31)) zi = (i < 32 ? z0 : z1) * rdiag[i];
                 zi = __shfl_sync(0xffffffffu, zi, i & 31);
                 if (lane == (i & 31)) {
                     if (i < 32) z0 = zi; else z1 = zi;
@@ -196,7 +235,7 @@ __global__ void __launch_bounds__(256, 1) omp_kernel(MPArgs a) {
             }
             for (int i = nS - 1; i >= 0; --i) {
                 double xi = 0.0;
-                if (lane == (i & 31)) xi = (i < 32 ? z0 : z1) / L[tri(i) + i];
+                if (lane == (i & 31)) xi = (i < 32 ? z0 : z1) * rdiag[i];
                 xi = __shfl_sync(0xffffffffu, xi, i & 31);
                 if (lane == (i & 31)) {
                     if (i < 32) z0 = xi; else z1 = xi;
@@ -204,8 +243,14 @@ __global__ void __launch_bounds__(256, 1) omp_kernel(MPArgs a) {
                 if (lane < i) z0 -= L[tri(i) + lane] * xi;
                 if (lane + 32 < i) z1 -= L[tri(i) + lane + 32] * xi;
             }
-            if (lane < nS) xs[lane] = z0;
-            if (lane + 32 < nS) xs[lane + 32] = z1;
+            if (lane < nS) {
+                xs[lane] = z0;
+                xd[Sj[lane]] = z0;
+            }
+            if (lane + 32 < nS) {
+                xs[lane + 32] = z1;
+                xd[Sj[lane + 32]] = z1;
+            }
             __syncwarp();
         }
 
@@ -276,7 +321,7 @@ static cudaError_t launch_omp_t(const MPArgs &a, int num_sms, cudaStream_t st) {
     constexpr int warps = 8;
     const int k = a.lv.k;
     const size_t bytes = (NF == 2 ? sizeof(double) * B * B : 0) +
-                         warps * (sizeof(double) * (size_t)(tri(k) + 2 * k) + sizeof(uint32_t) * (size_t)k);
+                         warps * (sizeof(double) * (size_t)(tri(k) + 3 * k + NF * B * B) + sizeof(uint32_t) * (size_t)k);
     auto kern = omp_kernel<B, NF>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
