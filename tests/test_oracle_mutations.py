@@ -8,6 +8,7 @@ import sys
 import pytest
 
 import oracle
+import test_oracle_omp as omp_pins
 import test_oracle_pins as pins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "aqmp_oracle.c")
@@ -36,6 +37,16 @@ MUTANTS = [
      "rec(c, y0 + h, x0, h);\n        rec(c, y0, x0 + h, h);"),
     ("split_no_min_check", "if (!conv && b > c->min_block)", "if (!conv && b >= c->min_block && b > 2)"),
     ("decode_transposed", "out[(long)(y0 + i) * pitch + x0 + m] = s;", "out[(long)(y0 + m) * pitch + x0 + i] = s;"),
+    # Orthogonal Matching Pursuit
+    ("omp_backsub_transposed", "for (int q = a + 1; q < m; ++q) s -= L[q * m + a] * x[q];",
+     "for (int q = a + 1; q < m; ++q) s -= L[a * m + q] * x[q];"),
+    ("omp_rhs_from_residual", "for (int v = 0; v < n; ++v) s += pa[v] * y[v];",
+     "for (int v = 0; v < n; ++v) s += pa[v] * r[v];"),
+    ("omp_residual_sign", "for (int a = 0; a < m; ++a) s -= x[a] * D[(size_t)S[a] * n + v];",
+     "for (int a = 0; a < m; ++a) s += x[a] * D[(size_t)S[a] * n + v];"),
+    ("omp_pivot_no_sqrt", "L[a * m + a] = sqrt(s);", "L[a * m + a] = s;"),
+    ("omp_cholesky_sign", "for (int q = 0; q < b; ++q) s -= L[a * m + q] * L[b * m + q];",
+     "for (int q = 0; q < b; ++q) s += L[a * m + q] * L[b * m + q];"),
 ]
 
 PINS = [
@@ -58,6 +69,9 @@ PINS = [
     pins.test_depth_first_leaf_order,
     pins.test_decoder_reconstructs_exactly_with_full_orthonormal_budget,
     pins.test_decoder_places_each_leaf_as_d_times_x,
+    lambda: [omp_pins.test_matches_scikit_learn(t) for t in (4, 12)],
+    omp_pins.test_reduces_to_mp_on_an_orthonormal_dictionary,
+    omp_pins.test_each_refit_is_the_least_squares_solution,
 ]
 
 
