@@ -51,7 +51,7 @@ def workload_planes():
     return [img] * len(TOLS)
 
 
-UNEVEN_WORKLOAD = ("64 synthetic RGB images (gradient scenes, a seed per channel), width U{256..2048} x "
+UNEVEN_WORKLOAD = ("64 synthetic RGB images (piecewise scenes of the 512x512 workload, a seed per channel), width U{256..2048} x "
                    "height U{256..1536} in multiples of 64, encoded per channel as 192 planes in one call, "
                    "RMSE tol 2, quadtree 64->4, k=b^2/4, DCT-II+Haar")
 
@@ -127,6 +127,13 @@ def kernel_breakdown(aqmp, encode, flush):
     return {k: (v[0] / KERNEL_PASSES, v[1] / KERNEL_PASSES) for k, v in prof.items()}, top, per_call
 
 
+def autotune_choices(aqmp):
+    """The autotuner's settled choices, by kernel and side."""
+    return {f'{e["kind"]}_b{e["side"]}': (("tcgen05", "simt") if e["kind"] == "corr"
+                                          else ("default", "alternate"))[e["chosen"]]
+            for e in aqmp.aqmp_autotune_read() if e["chosen"] >= 0}
+
+
 def settle_autotuner(aqmp, encode, most=8):
     """Set-up, untimed: the library's autotuner measures its kernel
     candidates on the first calls of a configuration (the pursuit's over four
@@ -188,6 +195,7 @@ def run_uneven(args):
                                       for k, v in sorted(breakdown.items(), key=lambda kv: -kv[1][1])},
                           "timed_kernel": {top: {"launches": prof[top][0], "ms": round(prof[top][1], 3)}}
                           if top in prof else None,
+                          "autotune": autotune_choices(aqmp),
                           "gpu_launches": int(round(launches_per_step * args.steps)),
                           "clocks": clocks.summary()}))
     return 0
@@ -582,9 +590,7 @@ def run_ours(args):
                 "leaves_per_step": stats_sum["n_leaves"] / args.steps,
                 "near_tie_leaves": stats_sum["near_tie_leaves"],
                 "window_step_fraction": sum(stats_sum["window_steps_per_level"]) / max(1, stats_sum["atom_iterations"]),
-                "autotune": {f'{e["kind"]}_b{e["side"]}': (("tcgen05", "simt") if e["kind"] == "corr"
-                                                          else ("default", "alternate"))[e["chosen"]]
-                             for e in aqmp.aqmp_autotune_read() if e["chosen"] >= 0},
+                "autotune": autotune_choices(aqmp),
                 "forms": {"exact (bf16-limb tensor GEMM + f32x2 certified pursuit)": value,
                           "fp32 (same GEMM rounded to fp32 + fp32 pursuit, not certified)": fp32_value},
                 "roofline": roof, "kernels": kernels, "gpu_launches": launches,

@@ -228,12 +228,13 @@ __device__ __forceinline__ void zero_slot(float (&ch)[E], float (&cl)[E], int s2
 // 1 = a single orthonormal family); DF: double-float state with certified
 // decisions (true) or the plain FP32 form (false: FP32 correlations, energy
 // and stop test, one FMA per Gram entry, no certification).
-#ifndef AQMP_MP_MINB64
-#define AQMP_MP_MINB64 1            // resident CTAs per SM asked of the side-64 kernel
-#endif
 
-template <int B, int T, int NF, bool DF>
-__global__ void __launch_bounds__(T > 32 ? T : 256, T > 32 ? (B == 64 ? AQMP_MP_MINB64 : 1) : 2)
+// MINB: resident CTAs per SM the compiler is asked to fit (registers per
+// thread follow): 1 keeps the side-64 state in registers for the fastest
+// single pursuit, 2 halves the registers so two leaves share an SM, which
+// wins when leaves outnumber SMs.
+template <int B, int T, int NF, bool DF, int MINB = (T > 32 ? 1 : 2)>
+__global__ void __launch_bounds__(T > 32 ? T : 256, MINB)
 mp_kernel(MPArgs a) {
     constexpr int n = B * B;
     constexpr int M = NF * n;
@@ -655,12 +656,12 @@ static size_t mp_smem_bytes(int k, int groups) {
     return bytes;
 }
 
-template <int B, int T, int NF, bool DF>
+template <int B, int T, int NF, bool DF, int MINB = (T > 32 ? 1 : 2)>
 static cudaError_t launch_mp_t(const MPArgs &a, int num_sms, cudaStream_t st) {
     const int block = (T == 32) ? 256 : T;
     const int groups = (T == 32) ? block / 32 : 1;
     const size_t smem = mp_smem_bytes<B, T, NF>(a.lv.k, groups);
-    auto kern = mp_kernel<B, T, NF, DF>;
+    auto kern = mp_kernel<B, T, NF, DF, MINB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -684,15 +685,13 @@ static cudaError_t launch_mp_t(const MPArgs &a, int num_sms, cudaStream_t st) {
 #define AQMP_MP_T64 256
 #endif
 
-// Alternate threads per leaf, chosen between by the host's autotuner.
+// Alternate launch shapes, chosen between by the host's autotuner: other
+// threads per leaf at sides 16 and 32; two resident CTAs per SM at side 64.
 #ifndef AQMP_MP_T16_ALT
 #define AQMP_MP_T16_ALT 64
 #endif
 #ifndef AQMP_MP_T32_ALT
 #define AQMP_MP_T32_ALT 64
-#endif
-#ifndef AQMP_MP_T64_ALT
-#define AQMP_MP_T64_ALT 512
 #endif
 
 template <bool DF>
@@ -709,7 +708,7 @@ static cudaError_t launch_mp_prec(const MPArgs &a, int nf, int variant, int num_
                 return variant ? launch_mp_t<32, AQMP_MP_T32_ALT, 2, DF>(a, num_sms, st)
                                : launch_mp_t<32, AQMP_MP_T32, 2, DF>(a, num_sms, st);
             case 64:
-                return variant ? launch_mp_t<64, AQMP_MP_T64_ALT, 2, DF>(a, num_sms, st)
+                return variant ? launch_mp_t<64, AQMP_MP_T64, 2, DF, 2>(a, num_sms, st)
                                : launch_mp_t<64, AQMP_MP_T64, 2, DF>(a, num_sms, st);
         }
     } else {

@@ -90,14 +90,16 @@ def noise_plane(h: int, w: int, seed: int = 0, mean: float = 128.0, sigma: float
 
 
 def uneven_rgb_batch(n_images: int = 64, seed: int = 0, wmin: int = 256, wmax: int = 2048,
-                     hmin: int = 256, hmax: int = 1536, step: int = 64):
+                     hmin: int = 256, hmax: int = 1536, step: int = 64, scene=None):
     """`n_images` RGB images of uneven sizes, width and height drawn uniformly
-    from multiples of `step`; channel c of image i is the gradient scene of
-    seed `seed + 3 i + c`.  Returns a list of (h, w, [R, G, B]) tuples."""
+    from multiples of `step`; channel c of image i is the piecewise scene (the
+    512x512 workload's generator) of seed `seed + 3 i + c`, or `scene(h, w,
+    seed=...)` when given.  Returns a list of (h, w, [R, G, B]) tuples."""
+    make = scene or piecewise_scene
     rng = np.random.default_rng(seed)
     out = []
     for i in range(n_images):
         w = int(rng.integers(wmin // step, wmax // step + 1)) * step
         h = int(rng.integers(hmin // step, hmax // step + 1)) * step
-        out.append((h, w, [gradient_scene(h, w, seed=seed + 3 * i + c) for c in range(3)]))
+        out.append((h, w, [make(h, w, seed=seed + 3 * i + c) for c in range(3)]))
     return out
