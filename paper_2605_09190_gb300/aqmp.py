@@ -252,12 +252,28 @@ def aqmp_code_stats(code: Code) -> dict:
             "window_steps_per_level": list(s.window_steps_per_level)}
 
 
+def _pinned(n: int, dtype) -> np.ndarray:
+    """Host array of n elements in page-locked memory from torch's caching
+    host allocator (blocks are reused, so a copy into them is plain DMA with
+    no page faults); the array keeps its block alive."""
+    dt = np.dtype(dtype)
+    if n == 0:
+        return np.zeros(0, dt)
+    try:
+        import torch
+        buf = torch.empty(n * dt.itemsize, dtype=torch.uint8, pin_memory=True)
+    except (ImportError, RuntimeError):          # no driver to pin with: ordinary memory
+        return np.empty(n, dt)
+    return buf.numpy().view(dt)
+
+
 def aqmp_code_copy(code: Code):
-    """Host copies (leaves, atoms, alpha_lo) in canonical depth-first order."""
+    """Host copies (leaves, atoms, alpha_lo) in canonical depth-first order,
+    in page-locked memory."""
     st = aqmp_code_stats(code)
-    leaves = np.zeros(st["n_leaves"], LEAF_DTYPE)
-    atoms = np.zeros(st["n_atoms"], ATOM_DTYPE)
-    lo = np.zeros(st["n_atoms"], np.float32)
+    leaves = _pinned(st["n_leaves"], LEAF_DTYPE)
+    atoms = _pinned(st["n_atoms"], ATOM_DTYPE)
+    lo = _pinned(st["n_atoms"], np.float32)
     _check(load_library().aqmp_code_copy(code.handle, leaves.ctypes.data, atoms.ctypes.data, lo.ctypes.data))
     return leaves, atoms, lo
 

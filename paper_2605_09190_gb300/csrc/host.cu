@@ -915,12 +915,18 @@ int aqmp_code_stats(const aqmp_code *code, aqmp_stats *stats) {
 
 int aqmp_code_copy(const aqmp_code *code, aqmp_leaf *leaves, aqmp_atom *atoms, float *alpha_lo) {
     if (!code || (!leaves && code->n_leaves) || (!atoms && code->n_atoms)) return fail(AQMP_E_ARG, "NULL argument");
-    // the device arrays are already in canonical order (written so by the encode)
-    if (code->n_leaves) CK(cudaMemcpy(leaves, code->leaves, sizeof(LeafRec) * code->n_leaves, cudaMemcpyDeviceToHost));
+    // the device arrays are already in canonical order (written so by the
+    // encode); the three transfers are queued together and waited for once
+    // (into page-locked buffers they overlap; pageable ones are staged)
+    cudaStream_t st = cudaStreamLegacy;
+    if (code->n_leaves)
+        CK(cudaMemcpyAsync(leaves, code->leaves, sizeof(LeafRec) * code->n_leaves, cudaMemcpyDeviceToHost, st));
     if (code->n_atoms) {
-        CK(cudaMemcpy(atoms, code->atoms, sizeof(AtomRec) * code->n_atoms, cudaMemcpyDeviceToHost));
-        if (alpha_lo) CK(cudaMemcpy(alpha_lo, code->alpha_lo, sizeof(float) * code->n_atoms, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpyAsync(atoms, code->atoms, sizeof(AtomRec) * code->n_atoms, cudaMemcpyDeviceToHost, st));
+        if (alpha_lo)
+            CK(cudaMemcpyAsync(alpha_lo, code->alpha_lo, sizeof(float) * code->n_atoms, cudaMemcpyDeviceToHost, st));
     }
+    CK(cudaStreamSynchronize(st));
     return AQMP_OK;
 }
 
