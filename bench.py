@@ -260,6 +260,92 @@ def run_omp(args):
     return 0
 
 
+PRECISION_WORKLOAD = ("one 4096x4096 RGB synthetic image (piecewise scene per channel, seeds 0..2), RMSE tol 2, "
+                      "quadtree 64->4, k=b^2/4, DCT-II+Haar: exact form vs plain FP32 form")
+
+
+def run_precision(args):
+    """The large-image precision comparison: the exact (certified) form and
+    the plain FP32 form on one 4096x4096 RGB image; throughput of each, the
+    share of leaves and of atom choices they share, and the quality of each
+    (PSNR, and SSIM from the library's FP64-window kernel)."""
+    import torch
+    from paper_2605_09190_gb300 import aqmp, build_lib, synthetic
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local if world > 1 else 0)
+    dist_init("nccl")
+    build_lib.build()
+    n = 4096
+    planes = [torch.from_numpy(synthetic.piecewise_scene(n, n, seed=rank * 3 + c)).cuda() for c in range(3)]
+    npix = 3 * n * n
+    stream = torch.cuda.current_stream()
+    forms = {"exact": aqmp.AQMP_PREC_EXACT, "fp32": aqmp.AQMP_PREC_FP32}
+    out = {}
+    with ClockSampler(local) as clocks:
+        for name, prec in forms.items():
+            encode = lambda: aqmp.aqmp_encode_planes(planes, 2.0, min_block=MIN_BLOCK, max_block=MAX_BLOCK,  # noqa: E731
+                                                     precision=prec)
+            settle_autotuner(aqmp, encode)
+            for _ in range(args.warmup):
+                encode().free()
+            ms = []
+            for _ in range(args.steps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                code = encode()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+                if len(ms) < args.steps:
+                    code.free()
+            out[name] = {"s": max_over_ranks(sum(ms) / 1e3, device="cuda"), "code": code}
+    le, ae, _ = out["exact"]["code"].copy()
+    lf, af, _ = out["fp32"]["code"].copy()
+    key = lambda L: (int(L["plane"]), int(L["y"]), int(L["x"]), int(L["b"]))  # noqa: E731
+    fmap = {key(L): L for L in lf}
+    same_leaves = same_atoms = 0
+    for L in le:
+        F = fmap.get(key(L))
+        if F is None:
+            continue
+        a = ae["j"][int(L["atom_off"]):int(L["atom_off"]) + int(L["n_atoms"])]
+        b = af["j"][int(F["atom_off"]):int(F["atom_off"]) + int(F["n_atoms"])]
+        m = min(len(a), len(b))
+        pref = int(np.argmax(a[:m] != b[:m])) if m and np.any(a[:m] != b[:m]) else m
+        same_atoms += pref
+        same_leaves += int(len(a) == len(b) and pref == m)
+    quality = {}
+    rec = torch.empty((n, n), dtype=torch.float32, device="cuda")
+    s_out = torch.zeros((), dtype=torch.float64, device="cuda")
+    for name in forms:
+        ps, ss = [], []
+        for c in range(3):
+            out[name]["code"].decode(c, rec)
+            ref = planes[c].float()
+            clip = rec.clamp(0.0, 255.0)
+            mse = float(((clip.double() - ref.double()) ** 2).mean())
+            ps.append(10.0 * np.log10(255.0 ** 2 / max(mse, 1e-30)))
+            aqmp.aqmp_ssim(ref, clip.contiguous(), s_out)
+            ss.append(float(s_out))
+        quality[name] = {"psnr": float(np.mean(ps)), "ssim": float(np.mean(ss))}
+    if rank == 0:
+        print(json.dumps({"metric": METRIC, "value": weak_scaling_value(npix, args.steps, out["exact"]["s"], world),
+                          "unit": "MP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": 1e3 * out["exact"]["s"] / args.steps, "higher_is_better": True,
+                          "scaling": "weak", "vs_baseline": None, "dtype": "bf16-limb tensor GEMM + f32x2 pursuit",
+                          "data": "synthetic",
+                          "config": {"workload": PRECISION_WORKLOAD, "pixels_per_step": npix, "input": "device-resident",
+                                     "l2": "inputs (50 M px) and working set exceed L2"},
+                          "fp32_form": {"value": weak_scaling_value(npix, args.steps, out["fp32"]["s"], world),
+                                        "unit": "MP/s"},
+                          "leaves": {"exact": len(le), "fp32": len(lf)},
+                          "same_leaves_share": same_leaves / max(1, len(le)),
+                          "same_atom_choices_share": same_atoms / max(1, len(ae)),
+                          "quality": quality, "autotune": autotune_choices(aqmp),
+                          "clocks": clocks.summary()}))
+    return 0
+
+
 def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
         int(os.environ.get("LOCAL_RANK", "0"))
@@ -608,10 +694,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["sweep512", "uneven64", "refine16", "omp512"], default="sweep512",
+    ap.add_argument("--workload", choices=["sweep512", "uneven64", "refine16", "omp512", "precision4096"],
+                    default="sweep512",
                     help="sweep512: the 512x512 tolerance sweep (default); uneven64: 64 uneven RGB images; "
                          "refine16: coefficient refinement on 16 images (steps = Adam steps); "
-                         "omp512: the sweep's planes with 16x16 roots, Orthogonal Matching Pursuit")
+                         "omp512: the sweep's planes with 16x16 roots, Orthogonal Matching Pursuit; "
+                         "precision4096: one 4096x4096 RGB image, exact vs plain FP32 form")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -621,6 +709,8 @@ def main():
         return run_refine(args)
     if args.workload == "omp512":
         return run_omp(args)
+    if args.workload == "precision4096":
+        return run_precision(args)
     return run_ours(args)
 
 
