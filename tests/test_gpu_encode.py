@@ -237,3 +237,23 @@ def test_device_arrays_are_in_canonical_order(lib, min_block, max_block):
         sel = leaves[leaves["plane"] == i]
         assert int(np.sum(sel["b"].astype(np.int64) ** 2)) == p.size
     code.free()
+
+
+def test_one_large_plane_sampled_roots(lib):
+    """One 16384 x 8192 plane (134 M px, 32 768 roots): sampled roots at the
+    corners and in the middle match the oracle, the leaves tile the plane and
+    the leaf order is depth-first (the 64-bit index arithmetic at size)."""
+    h, w = 16384, 8192
+    img = synthetic.gradient_scene(h, w, seed=13)
+    code = lib.aqmp_encode_planes([torch.from_numpy(img).cuda()], 3.0)
+    leaves, atoms, lo = code.copy()
+    code.free()
+    assert int(np.sum(leaves["b"].astype(np.int64) ** 2)) == h * w
+    keys = _dfs_keys(leaves, [img.shape], 64, 4)
+    assert all(a < b for a, b in zip(keys, keys[1:]))
+    nroots = (h // 64) * (w // 64)
+    roots = sorted({0, w // 64 - 1, nroots // 2 + 17, nroots - w // 64, nroots - 1})
+    enc = oracle.encode([img], [3.0], roots=[roots])
+    gl, ga, glo = parity.restrict_to_roots(leaves, atoms, lo, 0, roots, 64, w)
+    gl["atom_off"] = np.concatenate([[0], np.cumsum(gl["n_atoms"].astype(np.int64))[:-1]]).astype(np.uint32)
+    parity.compare(enc, gl, ga, glo, [img])
