@@ -13,41 +13,79 @@
 
 namespace aqmp {
 
-// One warp per leaf, grid-stride over the level's entries.
-__global__ void gather_kernel(GatherArgs a) {
-    const int lane = threadIdx.x & 31;
-    const unsigned warps = (gridDim.x * blockDim.x) >> 5;
+// TPL threads per leaf (a warp below side 32, the whole 256-thread CTA at
+// sides 32 and 64), grid-stride over the level's entries.  The block's rows
+// are read coalesced into the group's shared-memory tile (row stride B + 4
+// bytes), then written in unravel order v = m B + i as BF16 pairs, so both
+// the pixel reads and the BF16 writes are contiguous.
+template <int B, int TPL>
+__global__ void __launch_bounds__(256) gather_kernel(GatherArgs a) {
+    constexpr int n = B * B, stride = B + 4, GROUPS = 256 / TPL, NW = TPL / 32;
+    extern __shared__ uint8_t gather_tile[];
+    __shared__ uint32_t s_ss[8];
+    const int t = threadIdx.x % TPL, g = threadIdx.x / TPL, lane = threadIdx.x & 31;
+    uint8_t *tile = gather_tile + (size_t)g * B * stride;
     const unsigned count = *a.count;
-    for (unsigned leaf = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; leaf < count; leaf += warps) {
+    for (unsigned leaf = blockIdx.x * GROUPS + g; leaf < count; leaf += gridDim.x * GROUPS) {
         const QueueEntry q = a.queue[leaf];
         const PlaneDesc pd = a.planes[q.plane];
         const uint8_t *base = pd.pix + (long long)q.y * pd.pitch + q.x;
-        __nv_bfloat16 *dst = a.Y + (size_t)leaf * a.Kpad;
         uint32_t ss = 0;
-        for (int v = lane; v < a.Kpad; v += 32) {
-            float val = 0.0f;
-            if (v < a.n) {
-                const int m = v / a.b, i = v - m * a.b;
-                const uint32_t p = base[(long long)i * pd.pitch + m];
-                ss += p * p;
-                val = (float)((int)p - 128);
-            }
-            dst[v] = __float2bfloat16_rn(val);
+#pragma unroll 4
+        for (int idx = t; idx < n; idx += TPL) {               // rows, coalesced
+            const int i = idx / B, m = idx % B;
+            const uint32_t p = base[(long long)i * pd.pitch + m];
+            ss += p * p;
+            tile[i * stride + m] = (uint8_t)p;
+        }
+        if (TPL == 32) __syncwarp(); else __syncthreads();
+        __nv_bfloat162 *dst = reinterpret_cast<__nv_bfloat162 *>(a.Y + (size_t)leaf * a.Kpad);
+        for (int v = 2 * t; v < a.Kpad; v += 2 * TPL) {          // unravel order, BF16 pairs
+            float v0 = 0.0f, v1 = 0.0f;
+            if (v < n) v0 = (float)((int)tile[(v % B) * stride + v / B] - 128);
+            if (v + 1 < n) v1 = (float)((int)tile[((v + 1) % B) * stride + (v + 1) / B] - 128);
+            dst[v >> 1] = __floats2bfloat162_rn(v0, v1);
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, off);
-        if (lane == 0) a.e0[leaf] = ss;
+        if (NW == 1) {
+            if (lane == 0) a.e0[leaf] = ss;
+            __syncwarp();
+        } else {
+            if (lane == 0) s_ss[threadIdx.x >> 5] = ss;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                uint32_t tot = 0;
+                for (int w = 0; w < NW; ++w) tot += s_ss[w];
+                a.e0[leaf] = tot;
+            }
+            __syncthreads();
+        }
     }
 }
 
-cudaError_t launch_gather(const GatherArgs &a, int num_sms, cudaStream_t st) {
-    long long warps_needed = a.capacity;
-    long long blocks = (warps_needed + 7) / 8;
-    long long cap = (long long)num_sms * 8;
+template <int B>
+static cudaError_t launch_gather_t(const GatherArgs &a, int num_sms, cudaStream_t st) {
+    constexpr int TPL = B >= 32 ? 256 : 32;
+    constexpr int GROUPS = 256 / TPL;
+    long long blocks = ((long long)a.capacity + GROUPS - 1) / GROUPS;
+    const long long cap = (long long)num_sms * 8;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    gather_kernel<<<(unsigned)blocks, 256, 0, st>>>(a);
+    const size_t smem = (size_t)GROUPS * B * (B + 4);
+    gather_kernel<B, TPL><<<(unsigned)blocks, 256, smem, st>>>(a);
     return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const GatherArgs &a, int num_sms, cudaStream_t st) {
+    switch (a.b) {
+        case 4: return launch_gather_t<4>(a, num_sms, st);
+        case 8: return launch_gather_t<8>(a, num_sms, st);
+        case 16: return launch_gather_t<16>(a, num_sms, st);
+        case 32: return launch_gather_t<32>(a, num_sms, st);
+        case 64: return launch_gather_t<64>(a, num_sms, st);
+    }
+    return cudaErrorInvalidValue;
 }
 
 // L contiguous row-major b x b blocks.
