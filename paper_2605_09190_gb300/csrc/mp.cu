@@ -284,6 +284,7 @@ mp_kernel(MPArgs a) {
     const unsigned count = *lv.count;
     const int k = lv.k;
     unsigned *work = &a.ctr->work_next[lv.level];
+    unsigned long long n_attempts = 0, n_steps = 0, n_windows = 0;
 
     for (;;) {
         // dynamic assignment: the next unclaimed leaf of this level
@@ -572,11 +573,10 @@ mp_kernel(MPArgs a) {
         } else {
             tie_any = __any_sync(0xffffffffu, tie) != 0;
         }
-        if (lane == 0) {
-            atomicAdd(&a.ctr->attempts[lv.level], 1ull);
-            atomicAdd(&a.ctr->iterations[lv.level], (unsigned long long)t);
-            if (windows) atomicAdd(&a.ctr->window_steps[lv.level], (unsigned long long)windows);
-        }
+        // work counters: kept by the group's lane 0, added once at exit
+        n_attempts += 1;
+        n_steps += (unsigned long long)t;
+        n_windows += (unsigned long long)windows;
         const bool emit = conv || lv.is_last;
         uint32_t off = 0, eslot = 0;
         if (emit) {
@@ -643,6 +643,11 @@ mp_kernel(MPArgs a) {
             }
         }
         if (T > 32) __syncthreads(); else __syncwarp();
+    }
+    if (lane == 0 && n_attempts) {
+        atomicAdd(&a.ctr->attempts[lv.level], n_attempts);
+        atomicAdd(&a.ctr->iterations[lv.level], n_steps);
+        if (n_windows) atomicAdd(&a.ctr->window_steps[lv.level], n_windows);
     }
 }
 
