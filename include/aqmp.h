@@ -63,9 +63,11 @@ extern "C" {
                                       (bit-identical result; for validation) */
 #define AQMP_FLAG_NO_AUTOTUNE   4u /* use the default kernel at every side instead
                                       of the autotuned choice */
-#define AQMP_FLAG_ALT_THREADS   8u /* run the pursuit with the alternate number of
-                                      threads per leaf at sides 16, 32 and 64
-                                      (bit-identical result; for validation) */
+#define AQMP_FLAG_ALT_THREADS   8u /* run the pursuit with its alternate launch
+                                      shape: the other threads per leaf at
+                                      sides 16 and 32, two resident CTAs per SM
+                                      at side 64 (bit-identical result; for
+                                      validation) */
 #define AQMP_FLAG_OMP          16u /* Orthogonal Matching Pursuit (the solver the
                                       paper's authors ran, Section 2.2) instead
                                       of MP: after each selection the support's
@@ -80,8 +82,9 @@ extern "C" {
  * is kept for the life of the process: the initial correlation on the
  * tensor cores or on the integer SIMT path (both are timed, twice each, on
  * the first encode that meets a side, dictionary, precision and capacity),
- * and the pursuit's threads per leaf at sides 16, 32 and 64 (the two
- * candidates alternate over the first four such encodes). */
+ * and the pursuit's launch shape at sides 16, 32 and 64 (threads per leaf,
+ * or resident CTAs per SM at side 64; the two candidates alternate over the
+ * first four such encodes). */
 
 typedef struct {
     float   rmse_tol;     /* per-block RMSE tolerance on the 0-255 scale:

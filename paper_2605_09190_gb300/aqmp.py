@@ -343,8 +343,8 @@ def aqmp_profile_filter(prefix: str | None = None) -> None:
 
 def aqmp_autotune_read() -> list:
     """The autotuner's choice points on the current device: dicts with kind
-    ("corr": 0 tcgen05 / 1 SIMT, "mp": 0 default / 1 alternate threads per
-    leaf), side, dict_id, precision, capacity_log2, chosen (-1 while
+    ("corr": 0 tcgen05 / 1 SIMT, "mp": 0 default / 1 alternate launch
+    shape), side, dict_id, precision, capacity_log2, chosen (-1 while
     measuring), samples and best_ms per candidate."""
     arr = (aqmp_tune_entry * 64)()
     n = ctypes.c_int(0)

@@ -226,7 +226,8 @@ std::string kname(const char *k, int b) { return std::string(k) + "_b" + std::to
 //
 // Choice points whose candidates give the same result bit for bit: the
 // initial correlation on the tensor cores or the integer SIMT path (K1), and
-// the pursuit's threads per leaf (K2).  Each is keyed by (kind, side,
+// the pursuit's launch shape (K2: threads per leaf, or resident CTAs per SM
+// at side 64).  Each is keyed by (kind, side,
 // dictionary, precision, log2 capacity); its candidates are timed with CUDA
 // events on the first calls (K1: both, twice each, within one encode, since
 // recomputing the correlation is harmless; K2: alternately over encodes),

@@ -26,9 +26,10 @@ struct MPArgs {
     CellMap cells;               // emitted leaves are marked here
     Counters *ctr;
 };
-// variant 0: the default threads per leaf; 1: the alternate one (sides 16,
-// 32, 64 with two families; the same as 0 elsewhere).  Both give the same
-// result bit for bit.
+// variant 0: the default launch shape; 1: the alternate one (other threads
+// per leaf at sides 16 and 32, two resident CTAs per SM at side 64; two
+// families only, the same as 0 elsewhere).  Both give the same result bit
+// for bit.
 cudaError_t launch_mp(const MPArgs &a, int nf, bool double_float, int variant, int num_sms, cudaStream_t st);
 bool mp_has_variant(int b, int nf);
 
