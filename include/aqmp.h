@@ -168,6 +168,14 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
 int aqmp_encode(const aqmp_params *params, const uint8_t *pixels, int channels, int h, int w,
                 size_t pitch, void *stream, aqmp_code **out);
 
+/* Batch form (Algorithm 1 over several images): image i has channels[i]
+ * planes of h[i] x w[i] stacked one after another at images[i] (plane c at
+ * images[i] + c h[i] pitch[i]); all planes of all images go through one
+ * encode, planes numbered image by image, and use params->rmse_tol. */
+int aqmp_encode_batch(const aqmp_params *params, int n_images, const uint8_t *const *images,
+                      const int *channels, const int *h, const int *w, const size_t *pitch,
+                      void *stream, aqmp_code **out);
+
 /* Counters of a finished encode (host struct, filled in place). */
 int aqmp_code_stats(const aqmp_code *code, aqmp_stats *stats);
 

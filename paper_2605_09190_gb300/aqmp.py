@@ -70,7 +70,7 @@ EXPORTS = ["aqmp_params_default", "aqmp_encode_planes", "aqmp_encode", "aqmp_cod
            "aqmp_correlate_noalloc", "aqmp_selftest_wait", "aqmp_code_device", "aqmp_synth_forward",
            "aqmp_synth_backward", "aqmp_ssim", "aqmp_image_to_planes", "aqmp_planes_to_image",
            "aqmp_bitstream_size", "aqmp_bitstream_write", "aqmp_bitstream_parse", "aqmp_code_from_bitstream",
-           "aqmp_autotune_read", "aqmp_autotune_reset", "aqmp_profile_filter"]
+           "aqmp_autotune_read", "aqmp_autotune_reset", "aqmp_profile_filter", "aqmp_encode_batch"]
 
 
 class aqmp_tune_entry(ctypes.Structure):
@@ -112,6 +112,7 @@ def load_library(path: str | None = None):
         lib.aqmp_encode_planes.argtypes = [ctypes.POINTER(aqmp_params), ctypes.POINTER(aqmp_plane), I, V,
                                            ctypes.POINTER(V)]
         lib.aqmp_encode.argtypes = [ctypes.POINTER(aqmp_params), V, I, I, I, ctypes.c_size_t, V, ctypes.POINTER(V)]
+        lib.aqmp_encode_batch.argtypes = [ctypes.POINTER(aqmp_params), I, V, V, V, V, V, V, ctypes.POINTER(V)]
         lib.aqmp_code_stats.argtypes = [V, ctypes.POINTER(aqmp_stats)]
         lib.aqmp_code_copy.argtypes = [V, V, V, V]
         lib.aqmp_decode.argtypes = [V, I, V, I64, I, V]
@@ -240,6 +241,30 @@ def aqmp_encode_planes(planes, tols=None, params: aqmp_params | None = None, str
 def aqmp_encode(pixels, params: aqmp_params | None = None, stream=None, **param_kw) -> Code:
     """Encode a (channels, h, w) uint8 stack with the parameters' tolerance."""
     return aqmp_encode_planes([pixels[c] for c in range(pixels.shape[0])], None, params, stream, **param_kw)
+
+
+def aqmp_encode_batch(images, params: aqmp_params | None = None, stream=None, **param_kw) -> Code:
+    """Encode several images at once (Algorithm 1 over a batch): each image a
+    (channels, h, w) uint8 CUDA tensor, contiguous; planes are numbered image
+    by image and all use the parameters' tolerance."""
+    if params is None:
+        params = default_params(**param_kw)
+    n = len(images)
+    ptrs = (ctypes.c_void_p * n)(*[im.data_ptr() for im in images])
+    ch = (ctypes.c_int * n)(*[int(im.shape[0]) for im in images])
+    hh = (ctypes.c_int * n)(*[int(im.shape[1]) for im in images])
+    ww = (ctypes.c_int * n)(*[int(im.shape[2]) for im in images])
+    pp = (ctypes.c_size_t * n)(*[int(im.stride(1)) for im in images])
+    for im in images:
+        if (im.dtype.itemsize != 1 or not im.is_cuda or im.stride(2) != 1
+                or (im.shape[0] > 1 and im.stride(0) != im.shape[1] * im.stride(1))):
+            raise ValueError("images must be (channels, h, w) uint8 CUDA tensors with stacked rows")
+    p = aqmp_params.from_buffer_copy(params)
+    p.flags = p.flags | AQMP_FLAG_INPUT_DEVICE
+    out = ctypes.c_void_p()
+    _check(load_library().aqmp_encode_batch(ctypes.byref(p), n, ptrs, ch, hh, ww, pp, _stream_handle(stream),
+                                            ctypes.byref(out)))
+    return Code(out.value)
 
 
 def aqmp_code_stats(code: Code) -> dict:

@@ -908,6 +908,25 @@ int aqmp_encode(const aqmp_params *params, const uint8_t *pixels, int channels, 
     return aqmp_encode_planes(params, pl.data(), channels, stream, out);
 }
 
+int aqmp_encode_batch(const aqmp_params *params, int n_images, const uint8_t *const *images, const int *channels,
+                      const int *h, const int *w, const size_t *pitch, void *stream, aqmp_code **out) {
+    if (n_images <= 0 || !images || !channels || !h || !w || !pitch) return fail(AQMP_E_ARG, "bad batch arguments");
+    std::vector<aqmp_plane> pl;
+    for (int i = 0; i < n_images; ++i) {
+        if (!images[i] || channels[i] <= 0) return fail(AQMP_E_ARG, "image %d: no pixels", i);
+        for (int c = 0; c < channels[i]; ++c) {
+            aqmp_plane p{};
+            p.pixels = images[i] + (size_t)c * h[i] * pitch[i];
+            p.height = h[i];
+            p.width = w[i];
+            p.pitch = (int64_t)pitch[i];
+            p.rmse_tol = -1.0f;
+            pl.push_back(p);
+        }
+    }
+    return aqmp_encode_planes(params, pl.data(), (int)pl.size(), stream, out);
+}
+
 int aqmp_code_stats(const aqmp_code *code, aqmp_stats *stats) {
     if (!code || !stats) return fail(AQMP_E_ARG, "NULL argument");
     *stats = code->stats;

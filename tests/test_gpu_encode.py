@@ -257,3 +257,17 @@ def test_one_large_plane_sampled_roots(lib):
     gl, ga, glo = parity.restrict_to_roots(leaves, atoms, lo, 0, roots, 64, w)
     gl["atom_off"] = np.concatenate([[0], np.cumsum(gl["n_atoms"].astype(np.int64))[:-1]]).astype(np.uint32)
     parity.compare(enc, gl, ga, glo, [img])
+
+
+def test_batch_entry_point_equals_the_plane_list(lib):
+    """aqmp_encode_batch (images of several sizes and channel counts) gives the
+    plane-list encode's result bit for bit."""
+    imgs = [np.stack([synthetic.gradient_scene(128, 192, seed=30 + c) for c in range(3)]),
+            synthetic.piecewise_scene(64, 128, seed=33)[None]]
+    dev = [torch.from_numpy(np.ascontiguousarray(im)).cuda() for im in imgs]
+    a = lib.aqmp_encode_batch(dev, rmse_tol=2.0)
+    planes = [p for im in dev for p in im]
+    b = lib.aqmp_encode_planes(planes, 2.0)
+    for x, y in zip(a.copy(), b.copy()):
+        np.testing.assert_array_equal(x.view(np.uint8), y.view(np.uint8))
+    assert a.stats()["n_leaves"] == b.stats()["n_leaves"] > 0
