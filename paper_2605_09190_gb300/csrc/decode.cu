@@ -9,27 +9,93 @@
 
 namespace aqmp {
 
-__global__ void __launch_bounds__(128) decode_kernel(DecodeArgs a) {
-    for (unsigned long long li = blockIdx.x; li < a.n_leaves; li += gridDim.x) {
-        const LeafRec L = a.leaves[li];
-        if (L.plane != a.plane) continue;
-        const int b = L.b, n = b * b;
-        int lg = 0;
-        while ((1 << lg) < b) ++lg;
-        const float *basis = a.basis[lg];
-        for (int v = threadIdx.x; v < n; v += blockDim.x) {
-            const int m = v / b, i = v - m * b;
-            float s = 0.0f;
-            for (int t = 0; t < L.n_atoms; ++t) {
-                const AtomRec at = a.atoms[L.atom_off + t];
-                int fam = (int)(at.j >= (uint32_t)n);
-                const int f = (int)at.j - fam * n;
-                if (a.nf == 1) fam = a.single_family;
-                const float *B = basis + fam * b * b;
-                const int p = f % b, q = f / b;
-                s = __fmaf_rn(at.alpha, __fmul_rn(B[p * b + i], B[q * b + m]), s);
+// Leaves of `plane` in canonical order form one range (planes ascending).
+__device__ __forceinline__ void plane_range(const LeafRec *leaves, unsigned long long n, uint32_t plane,
+                                            unsigned long long &lo, unsigned long long &hi) {
+    unsigned long long a = 0, b = n;
+    while (a < b) {                                    // first leaf with plane >= `plane`
+        const unsigned long long m = (a + b) >> 1;
+        if (leaves[m].plane < plane) a = m + 1; else b = m;
+    }
+    lo = a;
+    b = n;
+    while (a < b) {                                    // first leaf with plane > `plane`
+        const unsigned long long m = (a + b) >> 1;
+        if (leaves[m].plane <= plane) a = m + 1; else b = m;
+    }
+    hi = a;
+}
+
+constexpr int kDecodeThreads = 128;
+constexpr int kDecodeChunk = 256;                      // atoms staged per pass
+
+struct DecodeStage {
+    float al[kDecodeChunk];
+    int p[kDecodeChunk], q[kDecodeChunk];
+};
+
+// One leaf of side B on the whole CTA: its atoms staged in shared memory as
+// (alpha, offset of row p, offset of row q) into the FP32 basis of their
+// family, so the per-pixel loop is two loads and two multiply-adds.
+template <int B>
+__device__ __forceinline__ void decode_leaf(const DecodeArgs &a, const float *alpha, const LeafRec &L,
+                                            DecodeStage &st) {
+    constexpr int n = B * B;
+    constexpr int PER = (n + kDecodeThreads - 1) / kDecodeThreads;
+    constexpr int LG = B == 4 ? 2 : B == 8 ? 3 : B == 16 ? 4 : B == 32 ? 5 : 6;
+    const float *basis = a.basis[LG];
+    float acc[PER];
+#pragma unroll
+    for (int r = 0; r < PER; ++r) acc[r] = 0.0f;
+    for (int t0 = 0; t0 < L.n_atoms; t0 += kDecodeChunk) {
+        const int cnt = min(kDecodeChunk, (int)L.n_atoms - t0);
+        __syncthreads();
+        for (int t = threadIdx.x; t < cnt; t += kDecodeThreads) {
+            const AtomRec at = a.atoms[L.atom_off + t0 + t];
+            int fam = (int)(at.j >= (uint32_t)n);
+            const int f = (int)at.j - fam * n;
+            if (a.nf == 1) fam = a.single_family;
+            st.al[t] = alpha ? alpha[L.atom_off + t0 + t] : at.alpha;
+            st.p[t] = fam * n + (f % B) * B;
+            st.q[t] = fam * n + (f / B) * B;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < PER; ++r) {
+            const int v = threadIdx.x + r * kDecodeThreads;
+            if (v < n) {
+                const int m = v / B, i = v % B;
+                float s = acc[r];
+                for (int t = 0; t < cnt; ++t) s = __fmaf_rn(st.al[t], __fmul_rn(basis[st.p[t] + i], basis[st.q[t] + m]), s);
+                acc[r] = s;
             }
-            a.out[(long long)(L.y + i) * a.out_pitch + L.x + m] = s;
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+        const int v = threadIdx.x + r * kDecodeThreads;
+        if (v < n) a.out[(long long)(L.y + v % B) * a.out_pitch + L.x + v / B] = acc[r];
+    }
+    __syncthreads();
+}
+
+// One CTA per leaf of the plane.  `alpha` overrides the code's coefficients
+// when not NULL (synthesis with caller coefficients).
+__global__ void __launch_bounds__(kDecodeThreads) decode_kernel(DecodeArgs a, const float *alpha) {
+    __shared__ DecodeStage st;
+    __shared__ unsigned long long s_range[2];
+    if (threadIdx.x == 0) plane_range(a.leaves, a.n_leaves, a.plane, s_range[0], s_range[1]);
+    __syncthreads();
+    const unsigned long long lo = s_range[0], hi = s_range[1];
+    for (unsigned long long li = lo + blockIdx.x; li < hi; li += gridDim.x) {
+        const LeafRec L = a.leaves[li];
+        switch (L.b) {
+            case 4: decode_leaf<4>(a, alpha, L, st); break;
+            case 8: decode_leaf<8>(a, alpha, L, st); break;
+            case 16: decode_leaf<16>(a, alpha, L, st); break;
+            case 32: decode_leaf<32>(a, alpha, L, st); break;
+            case 64: decode_leaf<64>(a, alpha, L, st); break;
+            default: break;
         }
     }
 }
@@ -39,7 +105,16 @@ cudaError_t launch_decode(const DecodeArgs &a, int num_sms, cudaStream_t st) {
     long long blocks = (long long)a.n_leaves;
     long long cap = (long long)num_sms * 16;
     if (blocks > cap) blocks = cap;
-    decode_kernel<<<(unsigned)blocks, 128, 0, st>>>(a);
+    decode_kernel<<<(unsigned)blocks, kDecodeThreads, 0, st>>>(a, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_decode_alpha(const DecodeArgs &a, const float *alpha, int num_sms, cudaStream_t st) {
+    if (a.n_leaves == 0) return cudaSuccess;
+    long long blocks = (long long)a.n_leaves;
+    long long cap = (long long)num_sms * 16;
+    if (blocks > cap) blocks = cap;
+    decode_kernel<<<(unsigned)blocks, kDecodeThreads, 0, st>>>(a, alpha);
     return cudaGetLastError();
 }
 

@@ -33,31 +33,6 @@ __constant__ double c_gauss[11];
 
 __device__ __forceinline__ int ilog2_dev(int v) { int l = 0; while ((1 << l) < v) ++l; return l; }
 
-// One CTA per leaf of `plane`: out block = sum_t alpha_t phi_{j_t}.
-__global__ void synth_forward_kernel(const LeafRec *leaves, unsigned long long n_leaves, const AtomRec *atoms,
-                                     const float *alpha, uint32_t plane, float *out, long long pitch,
-                                     DecodeArgs bases) {
-    for (unsigned long long li = blockIdx.x; li < n_leaves; li += gridDim.x) {
-        const LeafRec L = leaves[li];
-        if (L.plane != plane) continue;
-        const int b = L.b, n = b * b;
-        const float *basis = bases.basis[ilog2_dev(b)];
-        for (int v = threadIdx.x; v < n; v += blockDim.x) {
-            const int m = v / b, i = v - m * b;
-            float s = 0.0f;
-            for (int t = 0; t < L.n_atoms; ++t) {
-                const uint32_t j = atoms[L.atom_off + t].j;
-                int fam = (int)(j >= (uint32_t)n);
-                const int f = (int)j - fam * n;
-                if (bases.nf == 1) fam = bases.single_family;
-                const float *B = basis + fam * b * b;
-                s = __fmaf_rn(alpha[L.atom_off + t], __fmul_rn(B[(f % b) * b + i], B[(f / b) * b + m]), s);
-            }
-            out[(long long)(L.y + i) * pitch + L.x + m] = s;
-        }
-    }
-}
-
 // One CTA per leaf: T_fam = B G B^T for the families present, then gather.
 __global__ void synth_backward_kernel(const LeafRec *leaves, unsigned long long n_leaves, const AtomRec *atoms,
                                       uint32_t plane, const float *grad, long long pitch, float *grad_alpha,
@@ -234,11 +209,15 @@ cudaError_t upload_gauss11(cudaStream_t st) {
 cudaError_t launch_synth_forward(const LeafRec *leaves, unsigned long long n_leaves, const AtomRec *atoms,
                                  const float *alpha, uint32_t plane, float *out, long long pitch,
                                  const DecodeArgs &bases, int num_sms, cudaStream_t st) {
-    if (n_leaves == 0) return cudaSuccess;
-    long long blocks = (long long)n_leaves;
-    if (blocks > (long long)num_sms * 16) blocks = (long long)num_sms * 16;
-    synth_forward_kernel<<<(unsigned)blocks, 128, 0, st>>>(leaves, n_leaves, atoms, alpha, plane, out, pitch, bases);
-    return cudaGetLastError();
+    // the decoder with caller coefficients (decode.cu)
+    DecodeArgs a = bases;
+    a.leaves = leaves;
+    a.n_leaves = n_leaves;
+    a.atoms = atoms;
+    a.plane = plane;
+    a.out = out;
+    a.out_pitch = pitch;
+    return launch_decode_alpha(a, alpha, num_sms, st);
 }
 
 cudaError_t launch_synth_backward(const LeafRec *leaves, unsigned long long n_leaves, const AtomRec *atoms,

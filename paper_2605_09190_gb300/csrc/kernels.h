@@ -96,6 +96,8 @@ struct DecodeArgs {
     int single_family;           // 0: DCT, 1: Haar (when nf == 1)
 };
 cudaError_t launch_decode(const DecodeArgs &a, int num_sms, cudaStream_t st);
+// The same with caller coefficients alpha[atom] in place of the code's.
+cudaError_t launch_decode_alpha(const DecodeArgs &a, const float *alpha, int num_sms, cudaStream_t st);
 
 // Refinement on a fixed support (diff.cu).
 cudaError_t upload_gauss11(cudaStream_t st);
