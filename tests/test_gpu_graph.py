@@ -63,3 +63,18 @@ def test_replays_on_a_side_stream(lib):
         lib.aqmp_profile_enable(False)
     prof = lib.aqmp_profile_read()
     assert prof["mp_b64"][0] == 4 and prof["order_copy"][0] == 4
+
+
+def test_replays_with_host_input(lib):
+    """Host planes are staged into the library's buffer before the replayed
+    graph runs; each replay must see its own pixels."""
+    A = [synthetic.piecewise_scene(128, 192, seed=31), synthetic.gradient_scene(64, 192, seed=32)]
+    B = [synthetic.piecewise_scene(128, 192, seed=33), synthetic.gradient_scene(64, 192, seed=34)]
+    ref = {"A": _run(lib, A, [1.5, 2.0], autotune=False), "B": _run(lib, B, [1.5, 2.0], autotune=False)}
+    for name in "ABABAB":
+        planes = A if name == "A" else B
+        host = [torch.from_numpy(p).pin_memory() for p in planes]
+        code = lib.aqmp_encode_planes(host, [1.5, 2.0], autotune=False)
+        got = code.copy(), code.stats()
+        code.free()
+        _same(got, ref[name])
