@@ -93,7 +93,10 @@ typedef struct {
     int32_t cap_num;      /* atom budget k(b) = max(1, b^2 cap_num / cap_den) */
     int32_t cap_den;      /*   (min_sparsity of Algorithm 2), cap <= 1 */
     int32_t min_block;    /* N_min, N_max: powers of two, 4 <= N_min <= N_max */
-    int32_t max_block;    /*   <= 64 (Section 2.3, set S) */
+    int32_t max_block;    /*   <= 128 (Section 2.3, set S); a side-128
+                             leaf runs on a cluster of four CTAs (two for a
+                             single-family dictionary), its correlation on
+                             the tensor cores in four exact K chunks */
     int32_t dict_id;      /* AQMP_DICT_* */
     int32_t precision;    /* AQMP_PREC_* */
     uint32_t flags;       /* AQMP_FLAG_* */

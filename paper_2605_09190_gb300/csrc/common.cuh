@@ -18,7 +18,7 @@ constexpr int kLimbs = 8;
 constexpr int kDigitBits = 6;
 constexpr int kMaxLevels = 8;          // block sides 4 .. 512 at most
 constexpr int kKBlock = 64;            // K padding unit (one 128-byte BF16 row)
-constexpr int kMaxSide = 64;           // largest block side this build serves
+constexpr int kMaxSide = 128;          // largest block side this build serves
 
 // One quadtree node waiting for its pursuit.
 struct QueueEntry {

@@ -12,11 +12,20 @@
 // exact integers and rounds once to a double-float (fixed_to_df), which
 // matches the SIMT kernel bit for bit.
 //
-// Tile: 128 atoms (TMEM lanes) x 64 leaves x all K, eight accumulators of 64
-// columns each (the full 512-column TMEM).  One thread issues TMA loads, one
+// Above K = 4096 (side 128) the contraction runs as consecutive launches
+// over K chunks of at most 4096: each chunk's eight accumulators are exact,
+// the chunk's exact integer T_c = sum_s 64^(7-s) P_s (|T_c| < 2^62 for a
+// unit-norm atom) is added into the output slot held as an int64, and the
+// last chunk converts the total once -- the same value, rounded the same
+// way, as a single pass.
+//
+// Tile: 128 atoms (TMEM lanes) x 64 leaves x the K range, eight accumulators
+// of 64 columns each (the full 512-column TMEM).  One thread issues TMA loads, one
 // issues MMAs, all four warps run the epilogue.  Every wait is bounded by a
 // timer; on expiry the kernel records AQMP_E_TIMEOUT, releases its TMEM and
 // returns.
+#include <algorithm>
+
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
@@ -25,6 +34,12 @@
 #include "kernels.h"
 
 namespace aqmp {
+
+// Largest K whose digit-plane sums stay exact in an FP32 accumulator
+// (|P_s| <= 4096 * 2^5 * 2^7 = 2^24), and the roles of a launch over one K
+// chunk.
+constexpr int kCorrExactK = 4096;
+enum { kCorrSingle = 0, kCorrFirst = 1, kCorrMiddle = 2, kCorrLast = 3 };
 
 namespace tc {
 
@@ -143,8 +158,9 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
 
 __global__ void __launch_bounds__(tc::kThreads, 1)
 corr_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M,
-               int Mpad, int Kpad, const long long *__restrict__ Sh, const long long *__restrict__ Sl,
-               const unsigned *count_dev, long long fixed_count, float2 *__restrict__ c0, Counters *ctr) {
+               int Mpad, int kb0, int KB, int mode, const long long *__restrict__ Sh,
+               const long long *__restrict__ Sl, const unsigned *count_dev, long long fixed_count,
+               float2 *__restrict__ c0, Counters *ctr) {
     using namespace tc;
     const long long count = count_dev ? (long long)*count_dev : fixed_count;
     const long long leaf0 = (long long)blockIdx.x * kN;
@@ -181,7 +197,6 @@ corr_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_holder;
-    const int KB = Kpad / kK;
 
     if (warp == 0 && lane == 0) {
         // TMA producer
@@ -190,12 +205,12 @@ corr_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         for (int kb = 0; kb < KB && !*abort_flag; ++kb) {
             if (!mbar_wait(emptyB(sb), pb ^ 1u, abort_flag)) break;
             mbar_expect_tx(fullB(sb), kTileB);
-            tma_load_2d(sB + sb * kTileB, &tmB, fullB(sb), kb * kK, (int)leaf0);
+            tma_load_2d(sB + sb * kTileB, &tmB, fullB(sb), (kb0 + kb) * kK, (int)leaf0);
             if (++sb == kStagesB) { sb = 0; pb ^= 1u; }
             for (int s = 0; s < kLimbs; ++s) {
                 if (!mbar_wait(emptyA(sa), pa ^ 1u, abort_flag)) break;
                 mbar_expect_tx(fullA(sa), kTileA);
-                tma_load_2d(sA + sa * kTileA, &tmA, fullA(sa), kb * kK, s * Mpad + m0);
+                tma_load_2d(sA + sa * kTileA, &tmA, fullA(sa), (kb0 + kb) * kK, s * Mpad + m0);
                 if (++sa == kStagesA) { sa = 0; pa ^= 1u; }
             }
         }
@@ -248,8 +263,21 @@ corr_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                         for (int s = 0; s < 4; ++s) top = top * 64 + (long long)__float2int_rn(P[s][i]);
 #pragma unroll
                         for (int s = 4; s < 8; ++s) bot = bot * 64 + (long long)__float2int_rn(P[s][i]);
-                        const df v = fixed_to_df(top + sh, bot + sl);
-                        c0[leaf * M + m] = make_float2(v.hi, v.lo);
+                        long long *slot = reinterpret_cast<long long *>(c0 + leaf * M + m);
+                        if (mode == kCorrSingle) {
+                            const df v = fixed_to_df(top + sh, bot + sl);
+                            c0[leaf * M + m] = make_float2(v.hi, v.lo);
+                        } else {
+                            long long T = top * (1ll << 24) + bot;      // this chunk, exact
+                            if (mode != kCorrFirst) T += *slot;
+                            if (mode == kCorrLast) {
+                                const long long hi = T >> 24;           // floor; T = hi 2^24 + (T - hi 2^24)
+                                const df v = fixed_to_df(hi + sh, (T - hi * (1ll << 24)) + sl);
+                                c0[leaf * M + m] = make_float2(v.hi, v.lo);
+                            } else {
+                                *slot = T;
+                            }
+                        }
                     }
                 }
             }
@@ -287,7 +315,6 @@ cudaError_t launch_wait_selftest(Counters *ctr, unsigned long long limit_ns, cud
 
 cudaError_t launch_corr_tc(const CorrArgs &a, cudaStream_t st) {
     const DictDev &d = *a.d;
-    if (d.Kpad > 4096) return cudaErrorInvalidValue;   // exactness bound of the FP32 accumulator
     const long long rows = a.count ? (long long)a.capacity : a.fixed_count;
     dim3 grid((unsigned)((rows + tc::kN - 1) / tc::kN), (unsigned)(d.Mpad / tc::kM));
     if (grid.x == 0) return cudaSuccess;
@@ -295,9 +322,17 @@ cudaError_t launch_corr_tc(const CorrArgs &a, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     const CUtensorMap *ma = reinterpret_cast<const CUtensorMap *>(d.tmap_limbs);
     const CUtensorMap *mb = reinterpret_cast<const CUtensorMap *>(a.tmap_Y);
-    corr_tc_kernel<<<grid, tc::kThreads, tc::kSmemBytes, st>>>(*ma, *mb, d.M, d.Mpad, d.Kpad, d.Sh, d.Sl, a.count,
-                                                               a.fixed_count, a.c0, a.ctr);
-    return cudaGetLastError();
+    // K chunks within the exactness bound of the FP32 accumulator
+    const int kblocks = d.Kpad / tc::kK, chunk = kCorrExactK / tc::kK;
+    const int chunks = (kblocks + chunk - 1) / chunk;
+    for (int c = 0; c < chunks; ++c) {
+        const int kb0 = c * chunk, kbs = std::min(chunk, kblocks - kb0);
+        const int mode = chunks == 1 ? kCorrSingle : c == 0 ? kCorrFirst : c == chunks - 1 ? kCorrLast : kCorrMiddle;
+        corr_tc_kernel<<<grid, tc::kThreads, tc::kSmemBytes, st>>>(*ma, *mb, d.M, d.Mpad, kb0, kbs, mode, d.Sh,
+                                                                   d.Sl, a.count, a.fixed_count, a.c0, a.ctr);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace aqmp

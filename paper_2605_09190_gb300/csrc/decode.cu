@@ -36,51 +36,63 @@ struct DecodeStage {
 
 // One leaf of side B on the whole CTA: its atoms staged in shared memory as
 // (alpha, offset of row p, offset of row q) into the FP32 basis of their
-// family, so the per-pixel loop is two loads and two multiply-adds.
+// family, so the per-pixel loop is two loads and two multiply-adds.  Side
+// 128 runs over its pixels in four passes (32 accumulators per thread, as
+// at side 64), re-staging the atoms for each.
 template <int B>
 __device__ __forceinline__ void decode_leaf(const DecodeArgs &a, const float *alpha, const LeafRec &L,
                                             DecodeStage &st) {
     constexpr int n = B * B;
-    constexpr int PER = (n + kDecodeThreads - 1) / kDecodeThreads;
-    constexpr int LG = B == 4 ? 2 : B == 8 ? 3 : B == 16 ? 4 : B == 32 ? 5 : 6;
+    constexpr int PASSES = B > 64 ? (B / 64) * (B / 64) : 1;
+    constexpr int NP = n / PASSES;                     // pixels per pass
+    constexpr int PER = (NP + kDecodeThreads - 1) / kDecodeThreads;
+    constexpr int LG = B == 4 ? 2 : B == 8 ? 3 : B == 16 ? 4 : B == 32 ? 5 : B == 64 ? 6 : 7;
     const float *basis = a.basis[LG];
-    float acc[PER];
+#pragma unroll 1
+    for (int pass = 0; pass < PASSES; ++pass) {
+        float acc[PER];
 #pragma unroll
-    for (int r = 0; r < PER; ++r) acc[r] = 0.0f;
-    for (int t0 = 0; t0 < L.n_atoms; t0 += kDecodeChunk) {
-        const int cnt = min(kDecodeChunk, (int)L.n_atoms - t0);
-        __syncthreads();
-        for (int t = threadIdx.x; t < cnt; t += kDecodeThreads) {
-            const AtomRec at = a.atoms[L.atom_off + t0 + t];
-            int fam = (int)(at.j >= (uint32_t)n);
-            const int f = (int)at.j - fam * n;
-            if (a.nf == 1) fam = a.single_family;
-            st.al[t] = alpha ? alpha[L.atom_off + t0 + t] : at.alpha;
-            st.p[t] = fam * n + (f % B) * B;
-            st.q[t] = fam * n + (f / B) * B;
-        }
-        __syncthreads();
+        for (int r = 0; r < PER; ++r) acc[r] = 0.0f;
+        for (int t0 = 0; t0 < L.n_atoms; t0 += kDecodeChunk) {
+            const int cnt = min(kDecodeChunk, (int)L.n_atoms - t0);
+            __syncthreads();
+            for (int t = threadIdx.x; t < cnt; t += kDecodeThreads) {
+                const AtomRec at = a.atoms[L.atom_off + t0 + t];
+                int fam = (int)(at.j >= (uint32_t)n);
+                const int f = (int)at.j - fam * n;
+                if (a.nf == 1) fam = a.single_family;
+                st.al[t] = alpha ? alpha[L.atom_off + t0 + t] : at.alpha;
+                st.p[t] = fam * n + (f % B) * B;
+                st.q[t] = fam * n + (f / B) * B;
+            }
+            __syncthreads();
 #pragma unroll
-        for (int r = 0; r < PER; ++r) {
-            const int v = threadIdx.x + r * kDecodeThreads;
-            if (v < n) {
-                const int m = v / B, i = v % B;
-                float s = acc[r];
-                for (int t = 0; t < cnt; ++t) s = __fmaf_rn(st.al[t], __fmul_rn(basis[st.p[t] + i], basis[st.q[t] + m]), s);
-                acc[r] = s;
+            for (int r = 0; r < PER; ++r) {
+                const int v = pass * NP + threadIdx.x + r * kDecodeThreads;
+                if (threadIdx.x + r * kDecodeThreads < NP) {
+                    const int m = v / B, i = v % B;
+                    float s = acc[r];
+                    for (int t = 0; t < cnt; ++t)
+                        s = __fmaf_rn(st.al[t], __fmul_rn(basis[st.p[t] + i], basis[st.q[t] + m]), s);
+                    acc[r] = s;
+                }
             }
         }
-    }
 #pragma unroll
-    for (int r = 0; r < PER; ++r) {
-        const int v = threadIdx.x + r * kDecodeThreads;
-        if (v < n) a.out[(long long)(L.y + v % B) * a.out_pitch + L.x + v / B] = acc[r];
+        for (int r = 0; r < PER; ++r) {
+            const int v = pass * NP + threadIdx.x + r * kDecodeThreads;
+            if (threadIdx.x + r * kDecodeThreads < NP)
+                a.out[(long long)(L.y + v % B) * a.out_pitch + L.x + v / B] = acc[r];
+        }
     }
     __syncthreads();
 }
 
 // One CTA per leaf of the plane.  `alpha` overrides the code's coefficients
-// when not NULL (synthesis with caller coefficients).
+// when not NULL (synthesis with caller coefficients).  BIG = false serves
+// sides up to 64; BIG = true only side 128, in a launch of its own so that
+// its register needs do not lower the occupancy of the common sizes.
+template <bool BIG>
 __global__ void __launch_bounds__(kDecodeThreads) decode_kernel(DecodeArgs a, const float *alpha) {
     __shared__ DecodeStage st;
     __shared__ unsigned long long s_range[2];
@@ -89,6 +101,10 @@ __global__ void __launch_bounds__(kDecodeThreads) decode_kernel(DecodeArgs a, co
     const unsigned long long lo = s_range[0], hi = s_range[1];
     for (unsigned long long li = lo + blockIdx.x; li < hi; li += gridDim.x) {
         const LeafRec L = a.leaves[li];
+        if (BIG) {
+            if (L.b == 128) decode_leaf<128>(a, alpha, L, st);
+            continue;
+        }
         switch (L.b) {
             case 4: decode_leaf<4>(a, alpha, L, st); break;
             case 8: decode_leaf<8>(a, alpha, L, st); break;
@@ -100,22 +116,20 @@ __global__ void __launch_bounds__(kDecodeThreads) decode_kernel(DecodeArgs a, co
     }
 }
 
-cudaError_t launch_decode(const DecodeArgs &a, int num_sms, cudaStream_t st) {
-    if (a.n_leaves == 0) return cudaSuccess;
-    long long blocks = (long long)a.n_leaves;
-    long long cap = (long long)num_sms * 16;
-    if (blocks > cap) blocks = cap;
-    decode_kernel<<<(unsigned)blocks, kDecodeThreads, 0, st>>>(a, nullptr);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_decode_alpha(const DecodeArgs &a, const float *alpha, int num_sms, cudaStream_t st) {
     if (a.n_leaves == 0) return cudaSuccess;
     long long blocks = (long long)a.n_leaves;
     long long cap = (long long)num_sms * 16;
     if (blocks > cap) blocks = cap;
-    decode_kernel<<<(unsigned)blocks, kDecodeThreads, 0, st>>>(a, alpha);
+    decode_kernel<false><<<(unsigned)blocks, kDecodeThreads, 0, st>>>(a, alpha);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || a.basis[7] == nullptr) return e;      // no side-128 table: no side-128 leaves
+    decode_kernel<true><<<(unsigned)blocks, kDecodeThreads, 0, st>>>(a, alpha);
     return cudaGetLastError();
+}
+
+cudaError_t launch_decode(const DecodeArgs &a, int num_sms, cudaStream_t st) {
+    return launch_decode_alpha(a, nullptr, num_sms, st);
 }
 
 }  // namespace aqmp

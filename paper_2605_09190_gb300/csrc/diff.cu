@@ -46,7 +46,7 @@ __global__ void synth_backward_kernel(const LeafRec *leaves, unsigned long long 
         const int nfam = bases.nf;
         float *G = sm;               // b x b gradient block, G[i][m]
         float *U = G + n;            // B G (per family), U[p][m]
-        float *Tc = U + n;           // coefficients per family: Tc[fam][p][q]
+        float *Tc = U + n;           // one family's coefficients Tc[p][q]
         __syncthreads();
         for (int v = threadIdx.x; v < n; v += blockDim.x) {
             const int i = v / b, m = v - i * b;
@@ -66,17 +66,18 @@ __global__ void synth_backward_kernel(const LeafRec *leaves, unsigned long long 
                 const int p = v / b, q = v - p * b;
                 float s = 0.0f;
                 for (int m = 0; m < b; ++m) s = __fmaf_rn(U[p * b + m], B[q * b + m], s);
-                Tc[fam * n + v] = s;
+                Tc[v] = s;
+            }
+            __syncthreads();
+            for (int t = threadIdx.x; t < L.n_atoms; t += blockDim.x) {    // this family's atoms
+                const uint32_t j = atoms[L.atom_off + t].j;
+                const int fa = nfam == 2 ? (int)(j >= (uint32_t)n) : 0;
+                if (fa != fam) continue;
+                const int f = (int)j - (nfam == 2 ? fa * n : 0);
+                grad_alpha[L.atom_off + t] = Tc[(f % b) * b + (f / b)];
             }
             __syncthreads();
         }
-        for (int t = threadIdx.x; t < L.n_atoms; t += blockDim.x) {
-            const uint32_t j = atoms[L.atom_off + t].j;
-            const int fam = nfam == 2 ? (int)(j >= (uint32_t)n) : 0;
-            const int f = (int)j - (nfam == 2 ? fam * n : 0);
-            grad_alpha[L.atom_off + t] = Tc[fam * n + (f % b) * b + (f / b)];
-        }
-        __syncthreads();
     }
 }
 
@@ -224,7 +225,7 @@ cudaError_t launch_synth_backward(const LeafRec *leaves, unsigned long long n_le
                                   uint32_t plane, const float *grad, long long pitch, float *grad_alpha,
                                   const DecodeArgs &bases, int max_side, int num_sms, cudaStream_t st) {
     if (n_leaves == 0) return cudaSuccess;
-    const size_t smem = sizeof(float) * (size_t)max_side * max_side * 4;
+    const size_t smem = sizeof(float) * (size_t)max_side * max_side * 3;   // G, U, Tc
     cudaError_t e = cudaFuncSetAttribute(synth_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     long long blocks = (long long)n_leaves;

@@ -14,7 +14,7 @@
 namespace aqmp {
 
 // TPL threads per leaf (a warp below side 32, the whole 256-thread CTA at
-// sides 32 and 64), grid-stride over the level's entries.  The block's rows
+// sides 32 to 128), grid-stride over the level's entries.  The block's rows
 // are read coalesced into the group's shared-memory tile (row stride B + 4
 // bytes), then written in unravel order v = m B + i as BF16 pairs, so both
 // the pixel reads and the BF16 writes are contiguous.
@@ -84,6 +84,7 @@ cudaError_t launch_gather(const GatherArgs &a, int num_sms, cudaStream_t st) {
         case 16: return launch_gather_t<16>(a, num_sms, st);
         case 32: return launch_gather_t<32>(a, num_sms, st);
         case 64: return launch_gather_t<64>(a, num_sms, st);
+        case 128: return launch_gather_t<128>(a, num_sms, st);
     }
     return cudaErrorInvalidValue;
 }

@@ -288,6 +288,7 @@ struct Dict {
     DictDev d{};
     DeviceBuf limbs, dh, dl, sh, sl, w, basis, basis64;
     CUtensorMap tmap;
+    bool tables = false;         // fixed-point correlation tables built (16 M n B + 8 M n B)
 };
 
 struct Ctx {
@@ -358,69 +359,85 @@ int get_ctx(Ctx **out) {
 
 int num_families(int dict_id) { return dict_id == AQMP_DICT_DCT_HAAR ? 2 : 1; }
 
-// Tables of one (side, dictionary), built once per device.
-int get_dict(Ctx *c, int b, int dict_id, cudaStream_t st, Dict **out) {
+// Tables of one (side, dictionary), built once per device: the FP32/FP64
+// bases and W always; the fixed-point correlation tables (digit planes and
+// (Dh, Dl): 24 M n bytes, 12.9 GB at side 128) only when `tables` is set,
+// so that decoding and synthesis never build them.
+int get_dict(Ctx *c, int b, int dict_id, cudaStream_t st, Dict **out, bool tables = true) {
     const int key = b * 16 + dict_id;
     auto it = c->dicts.find(key);
-    if (it != c->dicts.end()) { *out = it->second.get(); return AQMP_OK; }
-    auto D = std::make_unique<Dict>();
-    DictDev &d = D->d;
-    d.b = b;
-    d.n = b * b;
-    d.nf = num_families(dict_id);
-    d.M = d.nf * d.n;
-    d.Mpad = std::max(128, (d.M + 127) / 128 * 128);
-    d.Kpad = std::max(kKBlock, (d.n + kKBlock - 1) / kKBlock * kKBlock);
-    int rc;
-    if ((rc = D->limbs.reserve(sizeof(__nv_bfloat16) * (size_t)kLimbs * d.Mpad * d.Kpad))) return rc;
-    if ((rc = D->dh.reserve(sizeof(int32_t) * (size_t)d.M * d.n))) return rc;
-    if ((rc = D->dl.reserve(sizeof(int32_t) * (size_t)d.M * d.n))) return rc;
-    if ((rc = D->sh.reserve(sizeof(long long) * d.M))) return rc;
-    if ((rc = D->sl.reserve(sizeof(long long) * d.M))) return rc;
-    if ((rc = D->w.reserve(sizeof(float) * 4 * (size_t)b * b))) return rc;
-    if ((rc = D->basis.reserve(sizeof(float) * 2 * (size_t)b * b))) return rc;
-    if ((rc = D->basis64.reserve(sizeof(double) * 2 * (size_t)b * b))) return rc;
-    d.limbs = (__nv_bfloat16 *)D->limbs.p;
-    d.Dh = (int32_t *)D->dh.p;
-    d.Dl = (int32_t *)D->dl.p;
-    d.Sh = (long long *)D->sh.p;
-    d.Sl = (long long *)D->sl.p;
-    d.W = (float2 *)D->w.p;
-    d.WT = d.W + b * b;
-    d.basis = (float *)D->basis.p;
+    Dict *D = nullptr;
+    if (it != c->dicts.end()) {
+        D = it->second.get();
+    } else {
+        auto Dn = std::make_unique<Dict>();
+        DictDev &d = Dn->d;
+        d.b = b;
+        d.n = b * b;
+        d.nf = num_families(dict_id);
+        d.M = d.nf * d.n;
+        d.Mpad = std::max(128, (d.M + 127) / 128 * 128);
+        d.Kpad = std::max(kKBlock, (d.n + kKBlock - 1) / kKBlock * kKBlock);
+        int rc;
+        if ((rc = Dn->w.reserve(sizeof(float) * 4 * (size_t)b * b))) return rc;
+        if ((rc = Dn->basis.reserve(sizeof(float) * 2 * (size_t)b * b))) return rc;
+        if ((rc = Dn->basis64.reserve(sizeof(double) * 2 * (size_t)b * b))) return rc;
+        d.W = (float2 *)Dn->w.p;
+        d.WT = d.W + b * b;
+        d.basis = (float *)Dn->basis.p;
 
-    std::vector<double> basis;
-    make_bases(b, basis);
-    // W = C H^T with exact structural zeros: entries below 2^-40 are the
-    // rounding of an exact zero (e.g. W[p][0] = <C_p, H_0> = 0 for p > 0)
-    std::vector<float> w(4 * (size_t)b * b);      // W then W^T, (hi, lo) interleaved
-    const double *C = basis.data(), *H = basis.data() + (size_t)b * b;
-    for (int p = 0; p < b; ++p)
-        for (int q = 0; q < b; ++q) {
-            double x = dot2(C + (size_t)p * b, H + (size_t)q * b, b);
-            if (std::fabs(x) < 0x1p-40) x = 0.0;
-            else if (std::fabs(x) < 1e-7)
-                return fail(AQMP_E_DICT, "cross-Gram entry W[%d][%d] = %g is neither zero nor well separated", p, q, x);
-            const float hi = (float)x, lo = (float)(x - (double)hi);
-            w[2 * ((size_t)p * b + q)] = hi;                         // W[p][q]
-            w[2 * ((size_t)p * b + q) + 1] = lo;
-            w[2 * ((size_t)b * b + (size_t)q * b + p)] = hi;         // W^T[q][p]
-            w[2 * ((size_t)b * b + (size_t)q * b + p) + 1] = lo;
+        std::vector<double> basis;
+        make_bases(b, basis);
+        // W = C H^T with exact structural zeros: entries below 2^-40 are the
+        // rounding of an exact zero (e.g. W[p][0] = <C_p, H_0> = 0 for p > 0)
+        std::vector<float> w(4 * (size_t)b * b);      // W then W^T, (hi, lo) interleaved
+        const double *C = basis.data(), *H = basis.data() + (size_t)b * b;
+        for (int p = 0; p < b; ++p)
+            for (int q = 0; q < b; ++q) {
+                double x = dot2(C + (size_t)p * b, H + (size_t)q * b, b);
+                if (std::fabs(x) < 0x1p-40) x = 0.0;
+                else if (std::fabs(x) < 1e-7)
+                    return fail(AQMP_E_DICT, "cross-Gram entry W[%d][%d] = %g is neither zero nor well separated", p,
+                                q, x);
+                const float hi = (float)x, lo = (float)(x - (double)hi);
+                w[2 * ((size_t)p * b + q)] = hi;                         // W[p][q]
+                w[2 * ((size_t)p * b + q) + 1] = lo;
+                w[2 * ((size_t)b * b + (size_t)q * b + p)] = hi;         // W^T[q][p]
+                w[2 * ((size_t)b * b + (size_t)q * b + p) + 1] = lo;
+            }
+        CK(cudaMemcpyAsync(Dn->w.p, w.data(), sizeof(float) * w.size(), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(Dn->basis64.p, basis.data(), sizeof(double) * basis.size(), cudaMemcpyHostToDevice, st));
+        CK(launch_basis_to_float((const double *)Dn->basis64.p, d.basis, 2 * b * b, st));
+        if (dict_id == AQMP_DICT_HAAR) {
+            // single Haar family: decoder table slot 0 must hold the Haar basis
+            CK(cudaMemcpyAsync(d.basis, (const float *)Dn->basis.p + b * b, sizeof(float) * b * b,
+                               cudaMemcpyDeviceToDevice, st));
         }
-    CK(cudaMemcpyAsync(D->w.p, w.data(), sizeof(float) * w.size(), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(D->basis64.p, basis.data(), sizeof(double) * basis.size(), cudaMemcpyHostToDevice, st));
-    const int fam0 = dict_id == AQMP_DICT_HAAR ? 1 : 0;
-    CK(build_fixed_tables_fam(d, (const double *)D->basis64.p, fam0, st));
-    if (dict_id == AQMP_DICT_HAAR) {
-        // single Haar family: decoder table slot 0 must hold the Haar basis
-        CK(cudaMemcpyAsync(d.basis, (const float *)D->basis.p + b * b, sizeof(float) * b * b,
-                           cudaMemcpyDeviceToDevice, st));
+        CK(cudaStreamSynchronize(st));
+        D = Dn.get();
+        c->dicts[key] = std::move(Dn);
     }
-    if ((rc = encode_bf16_map(&D->tmap, d.limbs, (unsigned long long)kLimbs * d.Mpad, d.Kpad, 128))) return rc;
-    d.tmap_limbs = &D->tmap;
-    CK(cudaStreamSynchronize(st));
-    *out = D.get();
-    c->dicts[key] = std::move(D);
+    if (tables && !D->tables) {
+        DictDev &d = D->d;
+        int rc;
+        if ((rc = D->limbs.reserve(sizeof(__nv_bfloat16) * (size_t)kLimbs * d.Mpad * d.Kpad))) return rc;
+        if ((rc = D->dh.reserve(sizeof(int32_t) * (size_t)d.M * d.n))) return rc;
+        if ((rc = D->dl.reserve(sizeof(int32_t) * (size_t)d.M * d.n))) return rc;
+        if ((rc = D->sh.reserve(sizeof(long long) * d.M))) return rc;
+        if ((rc = D->sl.reserve(sizeof(long long) * d.M))) return rc;
+        d.limbs = (__nv_bfloat16 *)D->limbs.p;
+        d.Dh = (int32_t *)D->dh.p;
+        d.Dl = (int32_t *)D->dl.p;
+        d.Sh = (long long *)D->sh.p;
+        d.Sl = (long long *)D->sl.p;
+        const int fam0 = dict_id == AQMP_DICT_HAAR ? 1 : 0;
+        CK(build_fixed_tables_fam(d, (const double *)D->basis64.p, fam0, st));
+        if ((rc = encode_bf16_map(&D->tmap, d.limbs, (unsigned long long)kLimbs * d.Mpad, d.Kpad, 128))) return rc;
+        d.tmap_limbs = &D->tmap;
+        CK(cudaStreamSynchronize(st));
+        D->tables = true;
+    }
+    *out = D;
     return AQMP_OK;
 }
 
@@ -969,7 +986,7 @@ int aqmp_decode(const aqmp_code *code, int plane, float *out, int64_t out_pitch,
     a.single_family = 0;
     for (int b = code->min_block; b <= code->max_block; b *= 2) {
         Dict *d;
-        if ((rc = get_dict(c, b, code->dict_id, st, &d))) return rc;
+        if ((rc = get_dict(c, b, code->dict_id, st, &d, false))) return rc;
         a.basis[ilog2(b)] = d->d.basis;
     }
     float *dst = out;
@@ -1015,7 +1032,7 @@ static int code_bases(Ctx *c, const aqmp_code *code, cudaStream_t st, DecodeArgs
     a->single_family = 0;
     for (int b = code->min_block; b <= code->max_block; b *= 2) {
         Dict *d;
-        int rc = get_dict(c, b, code->dict_id, st, &d);
+        int rc = get_dict(c, b, code->dict_id, st, &d, false);
         if (rc) return rc;
         a->basis[ilog2(b)] = d->d.basis;
     }

@@ -32,6 +32,9 @@ struct MPArgs {
 // for bit.
 cudaError_t launch_mp(const MPArgs &a, int nf, bool double_float, int variant, int num_sms, cudaStream_t st);
 bool mp_has_variant(int b, int nf);
+// Side 128 (mp_cluster.cu): one leaf per cluster of 2 nf CTAs, same
+// arguments and outputs as launch_mp.
+cudaError_t launch_mp_cluster(const MPArgs &a, int nf, bool double_float, int num_sms, cudaStream_t st);
 
 // Orthogonal Matching Pursuit of one level (omp.cu): sides 4, 8, 16, budget
 // k <= omp_max_budget(); same arguments and outputs as the MP kernel (the
@@ -164,6 +167,8 @@ cudaError_t launch_color(const ColorArgs &a, bool to_planes, int num_sms, cudaSt
 // basis_dev = [2][b][b] (DCT, Haar); fam0 selects the family of a
 // single-family dictionary (0 = DCT, 1 = Haar).
 cudaError_t build_fixed_tables_fam(DictDev &d, const double *basis_dev, int fam0, cudaStream_t st);
+// FP32 copy of the FP64 bases (decoder tables).
+cudaError_t launch_basis_to_float(const double *basis_dev, float *out, int count, cudaStream_t st);
 
 // Host helpers defined in host.cu for the library's other entry points.
 int set_error(int code, const char *msg);

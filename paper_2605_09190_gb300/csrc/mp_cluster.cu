@@ -1,0 +1,497 @@
+// mp_cluster.cu -- the pursuit of side-128 leaves (Section 2.2 steps (b)-(d),
+// stop rule Eq. (3), split / emit of Algorithm 2) on a thread-block cluster.
+//
+// A side-128 leaf has M = 2 b^2 = 32 768 correlations, 256 KB as double-float
+// pairs: more than one SM holds next to its working registers.  A cluster of
+// 2 NF CTAs owns the leaf.  CTA rank r holds half h = r mod 2 of family
+// f = r div 2: thread `lane` keeps the 32 elements of in-family index
+// f' = h T + lane + 2 T s (s = 0..31) in registers.  Every element of a CTA
+// belongs to one family, so the CTA needs only the one cross-Gram table its
+// updates read -- W^T for DCT elements, W for Haar elements, b x b
+// double-float pairs, 128 KB of shared memory -- where a CTA holding both
+// families would need both (256 KB, more than fits).
+//
+// Each step every CTA reduces its own top-2 summary (the same summaries,
+// window rule and certification as the single-CTA kernel), the summaries
+// are exchanged through distributed shared memory -- a 16-byte slot per CTA
+// in every peer, written remotely, with an mbarrier per slot that each peer
+// arrives on remotely -- and every CTA merges the same values into the same
+// choice.  The energy, the stop test and the choice then run identically on
+// every CTA, so the cluster stays in lock step with no further exchange.  A
+// step chosen from the other family updates all of a CTA's elements through
+// W (the rank-1 Gram column); a step of its own family zeroes one element of
+// one CTA.  Rank 0 records the steps and emits or splits the leaf.
+//
+// Every exchange wait is bounded: on expiry the CTA records AQMP_E_TIMEOUT,
+// stays resident for a grace period (so that peers, which poll the error
+// word while they wait, stop writing into its shared memory) and returns.
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "mp_step.cuh"
+
+namespace aqmp {
+
+namespace {
+
+constexpr int kCB = 128;                                  // block side
+constexpr int kCT = 256;                                  // threads per CTA
+constexpr unsigned long long kExchangeWaitNs = 2000000000ull;
+constexpr unsigned long long kGraceNs = 50000000ull;
+
+__device__ __forceinline__ uint32_t sh_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t peer_addr(uint32_t addr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ unsigned long long now_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void st_peer(uint32_t addr, uint4 v) {
+    asm volatile("st.shared::cluster.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z),
+                 "r"(v.w)
+                 : "memory");
+}
+
+__device__ __forceinline__ void arrive_peer(uint32_t bar) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool try_wait_cluster(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint4 pack_top2(const Top2 &t) {
+    return make_uint4((uint32_t)t.P, (uint32_t)(t.P >> 32), t.k2, __float_as_uint(t.lo1));
+}
+
+__device__ __forceinline__ Top2 unpack_top2(const uint4 &v) {
+    return Top2{((unsigned long long)v.y << 32) | v.x, v.z, __uint_as_float(v.w)};
+}
+
+// Move a summary's index from in-family f' to global f' + off (the index
+// field is (0xffff - j) << 1 below the sign bit; no borrow since j + off <=
+// 0xffff).  An empty summary stays empty.
+__device__ __forceinline__ Top2 top2_shift(Top2 t, uint32_t off) {
+    if (t.P != 0ull) t.P -= (unsigned long long)(off << 1);
+    return t;
+}
+
+// One exchange among the C CTAs of the cluster: thread 0 of every CTA puts
+// `v` into slot [seq & 1][rank] of every CTA and arrives on that slot's
+// mbarrier there; then thread 0 waits (bounded) for the C arrivals on its
+// own.  All threads call it; the leading barrier keeps a slot from being
+// rewritten (two exchanges later, by a peer that needs this CTA's next
+// arrival first) while a thread still reads it.  Returns false on timeout
+// or when another CTA has recorded an error; the verdict is CTA-uniform.
+template <int C>
+__device__ __forceinline__ bool cluster_exchange(uint4 *xs, unsigned long long *xbar, volatile uint32_t *verdict,
+                                                 int &seq, uint32_t rank, const uint4 &v,
+                                                 volatile unsigned *err, const uint4 *&out) {
+    const int slot = seq & 1;
+    const uint32_t parity = (uint32_t)(seq >> 1) & 1u;
+    ++seq;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        bool ok = *err == 0u;
+        if (ok) {
+            const uint32_t dst = sh_addr(xs + slot * C + rank);
+            const uint32_t bar = sh_addr(xbar + slot);
+#pragma unroll
+            for (int r = 0; r < C; ++r) {
+                st_peer(peer_addr(dst, (uint32_t)r), v);
+                arrive_peer(peer_addr(bar, (uint32_t)r));
+            }
+            if (!try_wait_cluster(bar, parity)) {
+                const unsigned long long t0 = now_ns();
+                for (;;) {
+                    if (try_wait_cluster(bar, parity)) break;
+                    if (*err != 0u || now_ns() - t0 > kExchangeWaitNs) { ok = false; break; }
+                }
+            }
+        }
+        *verdict = ok ? 1u : 0u;
+    }
+    __syncthreads();
+    out = xs + slot * C;
+    return *verdict != 0u;
+}
+
+}  // namespace
+
+// NF: atom families (2: DCT + Haar on four CTAs; 1: one orthonormal family
+// on two); DF as in the single-CTA kernel (double-float state and certified
+// decisions, or the plain FP32 form).
+template <int NF, bool DF>
+__global__ void __launch_bounds__(kCT, 1) mp_cluster_kernel(MPArgs a) {
+    constexpr int B = kCB, T = kCT, n = B * B, M = NF * n, C = 2 * NF, VT = 2 * T;
+    constexpr int E = n / VT;                  // 32 elements per thread
+    constexpr int NW = T / 32;
+    static_assert(n % VT == 0 && VT % B == 0, "layout");
+
+    extern __shared__ __align__(16) unsigned char smem[];
+    float2 *sV = reinterpret_cast<float2 *>(smem);                      // NF == 2: W^T or W
+    unsigned char *p = smem + (NF == 2 ? B * B * sizeof(float2) : 0);
+    uint4 *sPart = reinterpret_cast<uint4 *>(p);                        // [2][NW]
+    uint4 *sX = sPart + 2 * NW;                                         // [2][C] exchange slots
+    unsigned long long *sXbar = reinterpret_cast<unsigned long long *>(sX + 2 * C);   // [2]
+    uint32_t *sMisc = reinterpret_cast<uint32_t *>(sXbar + 2);          // [16]
+    unsigned long long *sRk = reinterpret_cast<unsigned long long *>(sMisc + 16);     // [NW]
+    uint32_t *sRj = reinterpret_cast<uint32_t *>(sRk + NW);             // [NW]
+    StepRec *steps = reinterpret_cast<StepRec *>(sRj + NW);             // [k], rank 0
+
+    const uint32_t rank = cluster_ctarank();
+    const int fam = NF == 2 ? (int)(rank >> 1) : 0;
+    const int half = (int)(rank & 1u);
+    const int lane = threadIdx.x;
+    const int vl = half * T + lane;            // lane within the family's 2T virtual threads
+    const int p_own = lane % B;                // row p' of every element of this thread
+    const uint32_t joff = NF == 2 ? (uint32_t)(fam * n) : 0u;
+    const LevelArgs &lv = a.lv;
+    volatile unsigned *err = &a.ctr->error;
+    volatile uint32_t *verdict = sMisc + 12;
+
+    if (NF == 2) {
+        const float2 *src = fam == 0 ? a.WT : a.W;   // the table of the other family's steps
+        for (int i = threadIdx.x; i < B * B; i += T) sV[i] = src[i];
+    }
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < 2; ++s)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sh_addr(sXbar + s)), "r"(C) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // every peer's barriers are initialised before the first remote arrive
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+
+    const unsigned count = *lv.count;
+    const int k = lv.k;
+    unsigned *work = &a.ctr->work_next[lv.level];
+    unsigned long long n_attempts = 0, n_steps = 0, n_windows = 0;
+    int seq = 0;
+    bool aborted = false;
+    const uint4 *xr;
+
+    for (;;) {
+        uint4 claim = make_uint4(0u, 0u, 0u, 0u);
+        if (rank == 0 && threadIdx.x == 0) claim.x = atomicAdd(work, 1u);
+        if (!cluster_exchange<C>(sX, sXbar, verdict, seq, rank, claim, err, xr)) { aborted = true; break; }
+        const unsigned leaf = xr[0].x;
+        if (leaf >= count) break;
+
+        const QueueEntry qe = lv.queue[leaf];
+        const float tol = a.planes[qe.plane].tol;
+        const df eps2 = df_scale(df_two_prod(tol, tol), (float)n);
+        const uint32_t e0 = a.e0[leaf];
+        df En = df_from_i64((long long)e0);
+        const df thrE = df_sub(eps2, df_scale(df_from_i64((long long)e0), 0x1p-32f));
+        const float bandE_f = ldexpf((float)e0, -37);
+        const float eps2_f = __fmul_rn(__fmul_rn(tol, tol), (float)n);
+        const float S_f = sqrtf((float)e0);
+        const float pre = ldexpf(S_f, -32) * 1.05f + ldexpf(S_f, -37) * 1.05f;
+
+        float ch[E], cl[E];
+        const float2 *cp = a.c0 + (size_t)leaf * M + joff;
+        Run2 acc = run2_empty();
+#pragma unroll
+        for (int s = 0; s < E; ++s) {
+            const float2 v = cp[vl + VT * s];
+            ch[s] = v.x;
+            cl[s] = DF ? v.y : 0.0f;
+            run2_fold(acc, ch[s], cl[s], (uint32_t)s);
+        }
+        Top2 top = top2_shift(run2_top2<VT>(acc, vl), joff);
+
+        int t = 0, windows = 0;
+        bool conv = false, tie = false;
+        const bool energy_warp = lane < 32;
+        for (;;) {
+            // (a6) accuracy test before every step, strict (identical on every CTA)
+            bool below = false;
+            if (energy_warp) {
+                below = DF ? df_lt(En, thrE) : (En.hi < eps2_f);
+                if (DF && fabsf(En.hi - thrE.hi) <= bandE_f * 1.01f + 0x1p-20f * fabsf(thrE.hi)) {
+                    if (fabs(df_to_double(En) - df_to_double(thrE)) < ldexp((double)e0, -37)) tie = true;
+                }
+            }
+            if (t == k) {
+                if (lane == 0) sMisc[10] = below ? 1u : 0u;
+                __syncthreads();
+                conv = sMisc[10] != 0u;
+                break;
+            }
+
+            // (a3) argmax: this CTA's summary, then the cluster's
+            const int buf = t & 1;
+            Top2 best = warp_top2(top);
+            if ((lane & 31) == 0) sPart[buf * NW + (lane >> 5)] = pack_top2(best);
+            if (lane == 0) sMisc[8 + buf] = below ? 1u : 0u;
+            __syncthreads();
+            if (sMisc[8 + buf] != 0u) { conv = true; break; }
+            best = (lane & 31) < NW ? unpack_top2(sPart[buf * NW + (lane & 31)]) : top2_empty();
+            best = warp_top2(best);
+            if (!cluster_exchange<C>(sX, sXbar, verdict, seq, rank, pack_top2(best), err, xr)) {
+                aborted = true;
+                break;
+            }
+            best = (lane & 31) < C ? unpack_top2(xr[lane & 31]) : top2_empty();
+            best = warp_top2(best);
+            if ((best.P >> 32) == 0ull) break;   // every correlation is exactly zero
+            uint32_t j1 = top2_index(best);
+            const float amax = top2_amax(best);
+            df alpha = df{top2_negative(best) ? -amax : amax, best.lo1};
+            const float window = amax * 0x1p-20f + pre;
+            if (DF && __uint_as_float(best.k2) >= amax - window) {
+                // Another atom is within the window: decide in full precision
+                // over the cluster's candidates (largest magnitude, then the
+                // lowest index within 2^-32 ||y|| of it; candidates within
+                // 2^-37 ||y|| of that edge are not certified).
+                ++windows;
+                const double tieC = ldexp((double)S_f, -32);
+                const double bandC = ldexp((double)S_f, -37);
+                unsigned long long mk = 0ull;
+                uint32_t mj = kNone;
+#pragma unroll
+                for (int s = 0; s < E; ++s) {
+                    if (fabsf(ch[s]) >= amax - window) {
+                        const double m = fabs((double)ch[s] + (double)cl[s]);
+                        const unsigned long long key = (unsigned long long)__double_as_longlong(m);
+                        if (key > mk) { mk = key; mj = joff + (uint32_t)(vl + VT * s); }
+                    }
+                }
+                warp_argmax64(mk, mj);
+                if ((lane & 31) == 0) {
+                    sRk[lane >> 5] = mk;
+                    sRj[lane >> 5] = mj;
+                }
+                __syncthreads();
+                mk = (lane & 31) < NW ? sRk[lane & 31] : 0ull;
+                mj = (lane & 31) < NW ? sRj[lane & 31] : kNone;
+                warp_argmax64(mk, mj);
+                if (!cluster_exchange<C>(sX, sXbar, verdict, seq, rank,
+                                         make_uint4((uint32_t)mk, (uint32_t)(mk >> 32), mj, 0u), err, xr)) {
+                    aborted = true;
+                    break;
+                }
+                {
+                    const uint4 e = (lane & 31) < C ? xr[lane & 31] : make_uint4(0u, 0u, kNone, 0u);
+                    mk = ((unsigned long long)e.y << 32) | e.x;
+                    mj = e.z;
+                    warp_argmax64(mk, mj);
+                }
+                const double edge = __longlong_as_double((long long)mk) - tieC;
+                uint32_t lower = kNone;
+#pragma unroll
+                for (int s = 0; s < E; ++s) {
+                    if (fabsf(ch[s]) >= amax - window) {
+                        const double m = fabs((double)ch[s] + (double)cl[s]);
+                        const uint32_t j = joff + (uint32_t)(vl + VT * s);
+                        if (fabs(m - edge) < bandC) tie = true;
+                        if (m >= edge && j < lower) lower = j;
+                    }
+                }
+                if (lane == 0) sMisc[6] = kNone;
+                __syncthreads();
+                if (lower != kNone) atomicMin(&sMisc[6], lower);
+                __syncthreads();
+                if (!cluster_exchange<C>(sX, sXbar, verdict, seq, rank, make_uint4(sMisc[6], 0u, 0u, 0u), err,
+                                         xr)) {
+                    aborted = true;
+                    break;
+                }
+                lower = kNone;
+#pragma unroll
+                for (int r = 0; r < C; ++r) lower = min(lower, xr[r].x);
+                // the owner of `lower` publishes its value
+                if (lane == 0) sMisc[3] = 0u;
+                __syncthreads();
+#pragma unroll
+                for (int s = 0; s < E; ++s)
+                    if (joff + (uint32_t)(vl + VT * s) == lower) {
+                        sMisc[3] = 1u;
+                        sMisc[4] = __float_as_uint(ch[s]);
+                        sMisc[5] = __float_as_uint(cl[s]);
+                    }
+                __syncthreads();
+                if (!cluster_exchange<C>(sX, sXbar, verdict, seq, rank, make_uint4(sMisc[3], sMisc[4], sMisc[5], 0u),
+                                         err, xr)) {
+                    aborted = true;
+                    break;
+                }
+                float wh = 0.0f, wl = 0.0f;
+#pragma unroll
+                for (int r = 0; r < C; ++r)
+                    if (xr[r].x != 0u) {
+                        wh = __uint_as_float(xr[r].y);
+                        wl = __uint_as_float(xr[r].z);
+                    }
+                j1 = lower;
+                alpha = df{wh, wl};
+            }
+            if (rank == 0 && lane == 0) steps[t] = StepRec{j1, alpha.hi, alpha.lo};
+
+            // (a5) energy
+            if (energy_warp) {
+                if (DF) En = df_sub(En, df_mul(alpha, alpha));
+                else En = df{__fmaf_rn(-alpha.hi, alpha.hi, En.hi), 0.0f};
+            }
+
+            // (a4) correlation update through the Gram matrix
+            const int fam1 = NF == 2 ? (int)(j1 >= (uint32_t)n) : 0;
+            const uint32_t f1 = j1 - (uint32_t)(fam1 * n);
+            if (NF == 2 && fam1 != fam) {
+                const int p1 = (int)(f1 % (uint32_t)B), q1 = (int)(f1 / (uint32_t)B);
+                const float2 vp = sV[p1 * B + p_own];
+                const df u = DF ? df_mul(alpha, df{vp.x, vp.y}) : df{__fmul_rn(alpha.hi, vp.x), 0.0f};
+                top = top2_shift(update_family<B, VT, E, E, 0, 0, DF>(ch, cl, vl, u, sV + q1 * B), joff);
+            } else if (fam1 == fam && f1 % (uint32_t)VT == (uint32_t)vl) {
+                top = top2_shift(zero_and_rescan<VT, E, E, 0>(ch, cl, vl, f1), joff);
+            }
+            ++t;
+        }
+        if (aborted) break;
+
+        // cluster-wide outcome of the certification
+        const bool tie_cta = __syncthreads_or(tie) != 0;
+        if (!cluster_exchange<C>(sX, sXbar, verdict, seq, rank, make_uint4(tie_cta ? 1u : 0u, 0u, 0u, 0u), err,
+                                 xr)) {
+            aborted = true;
+            break;
+        }
+        bool tie_any = false;
+#pragma unroll
+        for (int r = 0; r < C; ++r) tie_any = tie_any || xr[r].x != 0u;
+
+        if (rank == 0) {
+            n_attempts += 1;
+            n_steps += (unsigned long long)t;
+            n_windows += (unsigned long long)windows;
+            const bool emit = conv || lv.is_last;
+            if (emit) {
+                if (lane == 0) {
+                    uint32_t off = kNone, eslot = 0;
+                    const unsigned long long slot = atomicAdd(&a.ctr->n_leaves, 1ull);
+                    const unsigned long long o = atomicAdd(&a.ctr->n_atoms, (unsigned long long)t);
+                    const uint8_t flags = (uint8_t)((tie_any ? 1u : 0u) | (qe.flags & 2u));
+                    if (slot >= a.leaf_cap || o + t > a.atom_cap) {
+                        raise_error(a.ctr, kDevErrQueueOverflow, 1u);
+                    } else {
+                        LeafRec rec;
+                        rec.plane = qe.plane;
+                        rec.y = qe.y;
+                        rec.x = qe.x;
+                        rec.atom_off = (uint32_t)o;
+                        rec.b = (uint16_t)B;
+                        rec.n_atoms = (uint16_t)t;
+                        rec.converged = conv ? 1 : 0;
+                        rec.flags = flags;
+                        rec.reserved = 0;
+                        a.leaves[slot] = rec;
+                        off = (uint32_t)o;
+                        eslot = (uint32_t)slot;
+                        const unsigned long long cell = cell_of(a.cells, a.planes[qe.plane], qe.y, qe.x);
+                        if (cell != ~0ull) a.cells.cell[cell] = (uint32_t)slot + 1u;
+                        if (flags) atomicAdd(&a.ctr->near_tie_leaves, 1ull);
+                    }
+                    sMisc[0] = off;
+                    sMisc[1] = eslot;
+                }
+                __syncthreads();
+                const uint32_t off = sMisc[0], eslot = sMisc[1];
+                if (off != kNone) {
+                    for (int i = lane; i < t; i += T) {
+                        const StepRec st = steps[i];
+                        a.atoms[off + i] = AtomRec{st.j, st.hi};
+                        a.alpha_lo[off + i] = st.lo;
+                        a.atom_leaf[off + i] = eslot;
+                    }
+                }
+            } else if (lane == 0) {
+                const unsigned slot = atomicAdd(lv.next_count, 4u);
+                if (slot + 4u > lv.next_capacity) {
+                    raise_error(a.ctr, kDevErrQueueOverflow, 2u);
+                } else {
+                    const uint32_t h = B / 2;
+                    const uint32_t fl = (qe.flags & 2u) | (tie_any ? 2u : 0u);
+                    lv.next_queue[slot + 0] = QueueEntry{qe.plane, qe.y, qe.x, fl};
+                    lv.next_queue[slot + 1] = QueueEntry{qe.plane, qe.y, qe.x + h, fl};
+                    lv.next_queue[slot + 2] = QueueEntry{qe.plane, qe.y + h, qe.x, fl};
+                    lv.next_queue[slot + 3] = QueueEntry{qe.plane, qe.y + h, qe.x + h, fl};
+                }
+            }
+        }
+    }
+    if (rank == 0 && lane == 0 && n_attempts) {
+        atomicAdd(&a.ctr->attempts[lv.level], n_attempts);
+        atomicAdd(&a.ctr->iterations[lv.level], n_steps);
+        if (n_windows) atomicAdd(&a.ctr->window_steps[lv.level], n_windows);
+    }
+    if (aborted && threadIdx.x == 0) {
+        raise_error(a.ctr, kDevErrTimeout, 11u);
+        const unsigned long long t0 = now_ns();
+        while (now_ns() - t0 < kGraceNs) {
+        }
+    }
+}
+
+template <int NF, bool DF>
+static cudaError_t launch_cluster_t(const MPArgs &a, int num_sms, cudaStream_t st) {
+    constexpr int C = 2 * NF, NW = kCT / 32;
+    (void)num_sms;
+    const size_t smem = (NF == 2 ? (size_t)kCB * kCB * sizeof(float2) : 0) + 2 * NW * sizeof(uint4) +
+                        2 * C * sizeof(uint4) + 2 * sizeof(unsigned long long) + 16 * sizeof(uint32_t) +
+                        NW * (sizeof(unsigned long long) + sizeof(uint32_t)) + (size_t)a.lv.k * sizeof(StepRec);
+    auto kern = mp_cluster_kernel<NF, DF>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(kCT, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3((unsigned)C, 1, 1);
+    int clusters = 0;
+    e = cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg);
+    if (e != cudaSuccess) return e;
+    if (clusters < 1) return cudaErrorInvalidConfiguration;
+    long long need = (long long)a.lv.capacity;
+    if (need > clusters) need = clusters;
+    if (need < 1) need = 1;
+    cfg.gridDim = dim3((unsigned)(need * C), 1, 1);
+    return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+cudaError_t launch_mp_cluster(const MPArgs &a, int nf, bool double_float, int num_sms, cudaStream_t st) {
+    if (a.lv.b != kCB) return cudaErrorInvalidValue;
+    if (nf == 2) return double_float ? launch_cluster_t<2, true>(a, num_sms, st) : launch_cluster_t<2, false>(a, num_sms, st);
+    return double_float ? launch_cluster_t<1, true>(a, num_sms, st) : launch_cluster_t<1, false>(a, num_sms, st);
+}
+
+}  // namespace aqmp

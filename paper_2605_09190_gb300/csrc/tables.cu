@@ -86,8 +86,11 @@ cudaError_t build_fixed_tables_fam(DictDev &d, const double *basis_dev, int fam0
     int sblocks = (d.M + 7) / 8;
     if (sblocks > 4096) sblocks = 4096;
     fixed_sums_kernel<<<sblocks, 256, 0, st>>>(d.b, d.n, d.M, d.nf, fam0, basis_dev, d.Sh, d.Sl);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    basis_to_float_kernel<<<(2 * d.b * d.b + 255) / 256, 256, 0, st>>>(basis_dev, d.basis, 2 * d.b * d.b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_basis_to_float(const double *basis_dev, float *out, int count, cudaStream_t st) {
+    basis_to_float_kernel<<<(count + 255) / 256, 256, 0, st>>>(basis_dev, out, count);
     return cudaGetLastError();
 }
 

@@ -59,7 +59,7 @@ def _encode_rc(lib, params, planes):
 @pytest.mark.parametrize("field,value,code", [
     ("min_block", 3, -1), ("max_block", 48, -1), ("min_block", 128, -1),
     ("cap_den", 0, -1), ("cap_num", 5, -1), ("rmse_tol", -1.0, -1),
-    ("dict_id", 7, -3), ("max_block", 128, -8), ("precision", 9, -8)])
+    ("dict_id", 7, -3), ("max_block", 256, -8), ("precision", 9, -8)])
 def test_bad_parameters_are_rejected_before_any_device_work(lib, field, value, code):
     img = np.zeros((64, 64), np.uint8)
     p = aqmp.default_params()

@@ -35,7 +35,7 @@ def fast_haar_2d(Y: np.ndarray) -> np.ndarray:
 
 # --------------------------------------------------------------- tables
 
-@pytest.mark.parametrize("b", SIDES + [64])
+@pytest.mark.parametrize("b", SIDES + [64, 128])
 def test_dct_rows_match_scipy(b):
     ref = scipy.fft.dct(np.eye(b), type=2, norm="ortho", axis=0)
     # the argument pi/N (m + 1/2) k reaches ~1e4 at b = 64, so cos carries ~1e-13 of
@@ -43,7 +43,7 @@ def test_dct_rows_match_scipy(b):
     np.testing.assert_allclose(oracle.dct_1d(b), ref, atol=2e-13, rtol=0)
 
 
-@pytest.mark.parametrize("b", SIDES + [64])
+@pytest.mark.parametrize("b", SIDES + [64, 128])
 def test_haar_rows_match_filter_bank(b):
     ref = np.stack([fast_haar_1d(e) for e in np.eye(b)], axis=1)   # column m = transform of e_m
     np.testing.assert_allclose(oracle.haar_1d(b), ref, atol=2e-15, rtol=0)
@@ -128,6 +128,29 @@ def test_mp_on_haar_basis_is_sorted_fast_haar(b):
     np.testing.assert_array_equal(res["j"], j_ref)
     np.testing.assert_allclose(res["alpha"], a_ref, rtol=1e-12, atol=1e-10)
     assert res["energy"][-1] < 1e-18 * res["energy"][0]
+
+
+def test_side128_correlations_and_first_steps():
+    """Side 128, the largest root: D^T y is dctn and the separable fast Haar
+    of the block (the atom index and unravel conventions at that size), and
+    the first MP steps take the largest |correlation| and drop the energy by
+    alpha^2 each."""
+    b, n = 128, 128 * 128
+    rng = np.random.default_rng(128)
+    Y = rng.integers(0, 256, size=(b, b)).astype(np.float64)
+    D = oracle.dictionary(b, 0)
+    y = oracle.unravel(Y)
+    c = D @ y
+    np.testing.assert_allclose(c[:n].reshape(b, b).T, scipy.fft.dctn(Y, type=2, norm="ortho"), atol=1e-9)
+    np.testing.assert_allclose(c[n:].reshape(b, b).T, fast_haar_2d(Y), atol=1e-9)
+    res = oracle.mp(D, y, 0.0, 3)
+    assert res["j"][0] == int(np.argmax(np.abs(c))) == 0     # DC, before the identical Haar scaling atom
+    E = res["energy"]
+    np.testing.assert_allclose(E[:-1] - E[1:], res["alpha"] ** 2, rtol=0, atol=1e-12 * E[0])
+    r1 = y - res["alpha"][0] * D[0]
+    c1 = D @ r1
+    c1[[0, n]] = 0.0                                          # the chosen atom and its twin
+    assert res["j"][1] == int(np.argmax(np.abs(c1)))
 
 
 @pytest.mark.parametrize("b,seed", [(8, 1), (16, 2), (32, 3)])
