@@ -260,8 +260,9 @@ def run_omp(args):
     return 0
 
 
+PRECISION_ROOT = 128
 PRECISION_WORKLOAD = ("one 4096x4096 RGB synthetic image (piecewise scene per channel, seeds 0..2), RMSE tol 2, "
-                      "quadtree 64->4, k=b^2/4, DCT-II+Haar: exact form vs plain FP32 form")
+                      "quadtree 128->4, k=b^2/4, DCT-II+Haar: exact form vs plain FP32 form")
 
 
 def run_precision(args):
@@ -283,8 +284,8 @@ def run_precision(args):
     out = {}
     with ClockSampler(local) as clocks:
         for name, prec in forms.items():
-            encode = lambda: aqmp.aqmp_encode_planes(planes, 2.0, min_block=MIN_BLOCK, max_block=MAX_BLOCK,  # noqa: E731
-                                                     precision=prec)
+            encode = lambda: aqmp.aqmp_encode_planes(planes, 2.0, min_block=MIN_BLOCK,  # noqa: E731
+                                                     max_block=args.root or PRECISION_ROOT, precision=prec)
             settle_autotuner(aqmp, encode)
             for _ in range(args.warmup):
                 encode().free()
@@ -298,7 +299,10 @@ def run_precision(args):
                 ms.append(e0.elapsed_time(e1))
                 if len(ms) < args.steps:
                     code.free()
-            out[name] = {"s": max_over_ranks(sum(ms) / 1e3, device="cuda"), "code": code}
+            out[name] = {"s": max_over_ranks(sum(ms) / 1e3, device="cuda"), "code": code,
+                         "stats": code.stats()}
+            if name == "exact":
+                kernels, _, launches = kernel_breakdown(aqmp, encode, lambda: None)
     le, ae, _ = out["exact"]["code"].copy()
     lf, af, _ = out["fp32"]["code"].copy()
     key = lambda L: (int(L["plane"]), int(L["y"]), int(L["x"]), int(L["b"]))  # noqa: E731
@@ -339,6 +343,14 @@ def run_precision(args):
                           "fp32_form": {"value": weak_scaling_value(npix, args.steps, out["fp32"]["s"], world),
                                         "unit": "MP/s"},
                           "leaves": {"exact": len(le), "fp32": len(lf)},
+                          "per_level": {f"b{(args.root or PRECISION_ROOT) >> i}": {
+                              "attempts": out["exact"]["stats"]["attempts_per_level"][i],
+                              "atom_iterations": out["exact"]["stats"]["iterations_per_level"][i],
+                              "leaves": int(np.sum(le["b"] == ((args.root or PRECISION_ROOT) >> i)))}
+                              for i in range(int(np.log2((args.root or PRECISION_ROOT) // MIN_BLOCK)) + 1)},
+                          "kernels_ms": {k: round(v[1], 3) for k, v in sorted(kernels.items(),
+                                                                              key=lambda kv: -kv[1][1])},
+                          "gpu_launches_per_encode": launches,
                           "same_leaves_share": same_leaves / max(1, len(le)),
                           "same_atom_choices_share": same_atoms / max(1, len(ae)),
                           "quality": quality, "autotune": autotune_choices(aqmp),
@@ -700,6 +712,8 @@ def main():
                          "refine16: coefficient refinement on 16 images (steps = Adam steps); "
                          "omp512: the sweep's planes with 16x16 roots, Orthogonal Matching Pursuit; "
                          "precision4096: one 4096x4096 RGB image, exact vs plain FP32 form")
+    ap.add_argument("--root", type=int, default=0,
+                    help="precision4096 only: root block side (default 128; 64 for comparison)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -3,13 +3,20 @@
 //
 // A side-128 leaf has M = 2 b^2 = 32 768 correlations, 256 KB as double-float
 // pairs: more than one SM holds next to its working registers.  A cluster of
-// 2 NF CTAs owns the leaf.  CTA rank r holds half h = r mod 2 of family
-// f = r div 2: thread `lane` keeps the 32 elements of in-family index
-// f' = h T + lane + 2 T s (s = 0..31) in registers.  Every element of a CTA
-// belongs to one family, so the CTA needs only the one cross-Gram table its
-// updates read -- W^T for DCT elements, W for Haar elements, b x b
-// double-float pairs, 128 KB of shared memory -- where a CTA holding both
-// families would need both (256 KB, more than fits).
+// C CTAs owns the leaf (C = 4 for the DCT + Haar union, 2 for one family):
+// with the virtual lane v = rank T + lane, thread `lane` of CTA `rank` keeps
+// the 32 elements j = v + C T s in registers -- the single-CTA kernel's
+// layout over C T threads, so every CTA holds a quarter (a half) of each
+// family and each step's update is spread evenly over the cluster.
+//
+// A step chosen from one family updates the other through the rank-1 Gram
+// column W[p*, p'] W[q*, q'] (W = C H^T, or its transpose).  An element's row
+// p' is lane mod b, its column q' = 2 rank + lane div b + 8 s'; so a CTA reads
+// only 32 of the b columns of each table -- kept as a local slice -- and one
+// row entry W[p*, p'] per thread.  The full tables (2 x 128 KB) do not fit
+// one CTA; their rows are sharded over the cluster (rows 32 r .. 32 r + 31 on
+// rank r), and each thread loads its row entry from the owning peer through
+// distributed shared memory.
 //
 // Each step every CTA reduces its own top-2 summary (the same summaries,
 // window rule and certification as the single-CTA kernel), the summaries
@@ -60,14 +67,17 @@ __device__ __forceinline__ unsigned long long now_ns() {
     return t;
 }
 
-__device__ __forceinline__ void st_peer(uint32_t addr, uint4 v) {
-    asm volatile("st.shared::cluster.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z),
-                 "r"(v.w)
+// Asynchronous 16-byte store into a peer's shared memory that completes 16
+// transaction bytes on the peer's mbarrier (no release fence is needed: the
+// barrier's phase completes only once the bytes have landed).
+__device__ __forceinline__ void st_async_peer(uint32_t addr, uint4 v, uint32_t bar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];"
+                 ::"r"(addr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w), "r"(bar)
                  : "memory");
 }
 
-__device__ __forceinline__ void arrive_peer(uint32_t bar) {
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar) : "memory");
+__device__ __forceinline__ void arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
 __device__ __forceinline__ bool try_wait_cluster(uint32_t bar, uint32_t parity) {
@@ -90,45 +100,67 @@ __device__ __forceinline__ Top2 unpack_top2(const uint4 &v) {
     return Top2{((unsigned long long)v.y << 32) | v.x, v.z, __uint_as_float(v.w)};
 }
 
-// Move a summary's index from in-family f' to global f' + off (the index
-// field is (0xffff - j) << 1 below the sign bit; no borrow since j + off <=
-// 0xffff).  An empty summary stays empty.
-__device__ __forceinline__ Top2 top2_shift(Top2 t, uint32_t off) {
-    if (t.P != 0ull) t.P -= (unsigned long long)(off << 1);
-    return t;
+__device__ __forceinline__ float2 ld_peer_f2(uint32_t addr) {
+    float2 v;
+    asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr) : "memory");
+    return v;
 }
 
-// One exchange among the C CTAs of the cluster: thread 0 of every CTA puts
-// `v` into slot [seq & 1][rank] of every CTA and arrives on that slot's
-// mbarrier there; then thread 0 waits (bounded) for the C arrivals on its
-// own.  All threads call it; the leading barrier keeps a slot from being
-// rewritten (two exchanges later, by a peer that needs this CTA's next
-// arrival first) while a thread still reads it.  Returns false on timeout
-// or when another CTA has recorded an error; the verdict is CTA-uniform.
-template <int C>
+// Rank-1 update of the G elements in slots [S0, S0 + G) of one family and
+// their new top-2: element (v, S0 + s2) takes u W[q*, q'] with q' the slot's
+// column, read from the CTA's column slice at wcol[2 s2].
+template <int VT, int E, int G, int S0, bool DF>
+__device__ __forceinline__ Top2 update_cols(float (&ch)[E], float (&cl)[E], int v, const df &u,
+                                            const float2 *wcol) {
+    Run2 acc = run2_empty();
+#pragma unroll
+    for (int s2 = 0; s2 < G; ++s2) {
+        const int s = S0 + s2;
+        const float2 w = wcol[2 * s2];
+        if (DF) {
+            const df r = df_sub_mul(df{ch[s], cl[s]}, u, df{w.x, w.y});
+            ch[s] = r.hi;
+            cl[s] = r.lo;
+        } else {
+            ch[s] = __fmaf_rn(-u.hi, w.x, ch[s]);
+        }
+        run2_fold(acc, ch[s], cl[s], (uint32_t)s);
+    }
+    return run2_top2<VT>(acc, v);
+}
+
+// One exchange among the C CTAs of the cluster: lane r < C of warp 0 puts
+// `v` (equal on those lanes) into slot [seq & 1][rank] of CTA r with an
+// asynchronous store that completes 16 bytes on that slot's mbarrier there;
+// thread 0 arms its own barrier for the C * 16 bytes of the phase and waits
+// (bounded) for them.  All threads call it; the leading barrier keeps a slot
+// from being rewritten (two exchanges later, by a peer that needs this
+// CTA's next store first) while a thread still reads it.  Returns false on
+// timeout or when another CTA has recorded an error (checked only while
+// waiting); the verdict is CTA-uniform.
+// LEAD = false skips that barrier where the caller has one between its last
+// read of the previous exchange and this call.
+template <int C, bool LEAD = true>
 __device__ __forceinline__ bool cluster_exchange(uint4 *xs, unsigned long long *xbar, volatile uint32_t *verdict,
                                                  int &seq, uint32_t rank, const uint4 &v,
                                                  volatile unsigned *err, const uint4 *&out) {
     const int slot = seq & 1;
     const uint32_t parity = (uint32_t)(seq >> 1) & 1u;
     ++seq;
-    __syncthreads();
+    if (LEAD) __syncthreads();
+    const uint32_t bar = sh_addr(xbar + slot);
+    if (threadIdx.x < C) {
+        if (threadIdx.x == 0) arrive_expect_tx(bar, (uint32_t)(C * sizeof(uint4)));
+        const uint32_t r = threadIdx.x;
+        st_async_peer(peer_addr(sh_addr(xs + slot * C + rank), r), v, peer_addr(bar, r));
+    }
     if (threadIdx.x == 0) {
-        bool ok = *err == 0u;
-        if (ok) {
-            const uint32_t dst = sh_addr(xs + slot * C + rank);
-            const uint32_t bar = sh_addr(xbar + slot);
-#pragma unroll
-            for (int r = 0; r < C; ++r) {
-                st_peer(peer_addr(dst, (uint32_t)r), v);
-                arrive_peer(peer_addr(bar, (uint32_t)r));
-            }
-            if (!try_wait_cluster(bar, parity)) {
-                const unsigned long long t0 = now_ns();
-                for (;;) {
-                    if (try_wait_cluster(bar, parity)) break;
-                    if (*err != 0u || now_ns() - t0 > kExchangeWaitNs) { ok = false; break; }
-                }
+        bool ok = true;
+        if (!try_wait_cluster(bar, parity)) {
+            const unsigned long long t0 = now_ns();
+            for (unsigned it = 1;; ++it) {
+                if (try_wait_cluster(bar, parity)) break;
+                if ((it & 255u) == 0u && (*err != 0u || now_ns() - t0 > kExchangeWaitNs)) { ok = false; break; }
             }
         }
         *verdict = ok ? 1u : 0u;
@@ -145,14 +177,20 @@ __device__ __forceinline__ bool cluster_exchange(uint4 *xs, unsigned long long *
 // decisions, or the plain FP32 form).
 template <int NF, bool DF>
 __global__ void __launch_bounds__(kCT, 1) mp_cluster_kernel(MPArgs a) {
-    constexpr int B = kCB, T = kCT, n = B * B, M = NF * n, C = 2 * NF, VT = 2 * T;
-    constexpr int E = n / VT;                  // 32 elements per thread
+    constexpr int B = kCB, T = kCT, n = B * B, M = NF * n, C = 2 * NF, VT = C * T;
+    constexpr int E = M / VT;                  // 32 elements per thread
+    constexpr int NG = NF, G = E / NG;         // one top-2 per family
     constexpr int NW = T / 32;
-    static_assert(n % VT == 0 && VT % B == 0, "layout");
+    constexpr int RS = B / C;                  // table rows held per CTA (NF == 2)
+    constexpr int CS = B * T / VT;             // columns of a CTA's slice (NF == 2: 32)
+    static_assert(M % VT == 0 && T % B == 0 && G * VT == n, "layout");
+    static_assert(NF == 1 || (CS == 32 && RS == 32), "slices");
 
     extern __shared__ __align__(16) unsigned char smem[];
-    float2 *sV = reinterpret_cast<float2 *>(smem);                      // NF == 2: W^T or W
-    unsigned char *p = smem + (NF == 2 ? B * B * sizeof(float2) : 0);
+    // NF == 2: column slices colV[fam table][q1][32] and row shards rowV[fam table][32][b]
+    float2 *sCol = reinterpret_cast<float2 *>(smem);                    // [2][B][CS]: W, W^T
+    float2 *sRow = sCol + (NF == 2 ? 2 * B * CS : 0);                   // [2][RS][B]: W, W^T
+    unsigned char *p = reinterpret_cast<unsigned char *>(sRow + (NF == 2 ? 2 * RS * B : 0));
     uint4 *sPart = reinterpret_cast<uint4 *>(p);                        // [2][NW]
     uint4 *sX = sPart + 2 * NW;                                         // [2][C] exchange slots
     unsigned long long *sXbar = reinterpret_cast<unsigned long long *>(sX + 2 * C);   // [2]
@@ -162,27 +200,32 @@ __global__ void __launch_bounds__(kCT, 1) mp_cluster_kernel(MPArgs a) {
     StepRec *steps = reinterpret_cast<StepRec *>(sRj + NW);             // [k], rank 0
 
     const uint32_t rank = cluster_ctarank();
-    const int fam = NF == 2 ? (int)(rank >> 1) : 0;
-    const int half = (int)(rank & 1u);
     const int lane = threadIdx.x;
-    const int vl = half * T + lane;            // lane within the family's 2T virtual threads
+    const int vl = (int)rank * T + lane;       // virtual lane: element s is atom vl + VT s
     const int p_own = lane % B;                // row p' of every element of this thread
-    const uint32_t joff = NF == 2 ? (uint32_t)(fam * n) : 0u;
+    const int hb = lane / B;                   // column q' = 2 rank + hb + 8 s'
     const LevelArgs &lv = a.lv;
     volatile unsigned *err = &a.ctr->error;
     volatile uint32_t *verdict = sMisc + 12;
 
     if (NF == 2) {
-        const float2 *src = fam == 0 ? a.WT : a.W;   // the table of the other family's steps
-        for (int i = threadIdx.x; i < B * B; i += T) sV[i] = src[i];
+        for (int i = threadIdx.x; i < 2 * B * CS; i += T) {
+            const int tab = i / (B * CS), r = (i / CS) % B, lc = i % CS;
+            const int q = 8 * (lc >> 1) + 2 * (int)rank + (lc & 1);
+            sCol[i] = (tab ? a.WT : a.W)[r * B + q];
+        }
+        for (int i = threadIdx.x; i < 2 * RS * B; i += T) {
+            const int tab = i / (RS * B), r = (i / B) % RS, c = i % B;
+            sRow[i] = (tab ? a.WT : a.W)[((int)rank * RS + r) * B + c];
+        }
     }
     if (threadIdx.x == 0) {
         for (int s = 0; s < 2; ++s)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sh_addr(sXbar + s)), "r"(C) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sh_addr(sXbar + s)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    // every peer's barriers are initialised before the first remote arrive
+    // every peer's tables and barriers are in place before the first remote access
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 
     const unsigned count = *lv.count;
@@ -196,6 +239,7 @@ __global__ void __launch_bounds__(kCT, 1) mp_cluster_kernel(MPArgs a) {
     for (;;) {
         uint4 claim = make_uint4(0u, 0u, 0u, 0u);
         if (rank == 0 && threadIdx.x == 0) claim.x = atomicAdd(work, 1u);
+        if (threadIdx.x < 32) claim.x = __shfl_sync(0xffffffffu, claim.x, 0);   // the sending lanes
         if (!cluster_exchange<C>(sX, sXbar, verdict, seq, rank, claim, err, xr)) { aborted = true; break; }
         const unsigned leaf = xr[0].x;
         if (leaf >= count) break;
@@ -212,16 +256,21 @@ __global__ void __launch_bounds__(kCT, 1) mp_cluster_kernel(MPArgs a) {
         const float pre = ldexpf(S_f, -32) * 1.05f + ldexpf(S_f, -37) * 1.05f;
 
         float ch[E], cl[E];
-        const float2 *cp = a.c0 + (size_t)leaf * M + joff;
-        Run2 acc = run2_empty();
+        Top2 top[NG];
+        const float2 *cp = a.c0 + (size_t)leaf * M;
 #pragma unroll
-        for (int s = 0; s < E; ++s) {
-            const float2 v = cp[vl + VT * s];
-            ch[s] = v.x;
-            cl[s] = DF ? v.y : 0.0f;
-            run2_fold(acc, ch[s], cl[s], (uint32_t)s);
+        for (int g = 0; g < NG; ++g) {
+            Run2 acc = run2_empty();
+#pragma unroll
+            for (int s2 = 0; s2 < G; ++s2) {
+                const int s = g * G + s2;
+                const float2 v = cp[vl + VT * s];
+                ch[s] = v.x;
+                cl[s] = DF ? v.y : 0.0f;
+                run2_fold(acc, ch[s], cl[s], (uint32_t)s);
+            }
+            top[g] = run2_top2<VT>(acc, vl);
         }
-        Top2 top = top2_shift(run2_top2<VT>(acc, vl), joff);
 
         int t = 0, windows = 0;
         bool conv = false, tie = false;
@@ -244,14 +293,18 @@ __global__ void __launch_bounds__(kCT, 1) mp_cluster_kernel(MPArgs a) {
 
             // (a3) argmax: this CTA's summary, then the cluster's
             const int buf = t & 1;
-            Top2 best = warp_top2(top);
+            Top2 best = top[0];
+#pragma unroll
+            for (int g = 1; g < NG; ++g) best = top2_merge(best, top[g]);
+            best = warp_top2(best);
             if ((lane & 31) == 0) sPart[buf * NW + (lane >> 5)] = pack_top2(best);
             if (lane == 0) sMisc[8 + buf] = below ? 1u : 0u;
             __syncthreads();
             if (sMisc[8 + buf] != 0u) { conv = true; break; }
             best = (lane & 31) < NW ? unpack_top2(sPart[buf * NW + (lane & 31)]) : top2_empty();
             best = warp_top2(best);
-            if (!cluster_exchange<C>(sX, sXbar, verdict, seq, rank, pack_top2(best), err, xr)) {
+            // the barrier above follows every read of the previous exchange
+            if (!cluster_exchange<C, false>(sX, sXbar, verdict, seq, rank, pack_top2(best), err, xr)) {
                 aborted = true;
                 break;
             }
@@ -277,7 +330,7 @@ __global__ void __launch_bounds__(kCT, 1) mp_cluster_kernel(MPArgs a) {
                     if (fabsf(ch[s]) >= amax - window) {
                         const double m = fabs((double)ch[s] + (double)cl[s]);
                         const unsigned long long key = (unsigned long long)__double_as_longlong(m);
-                        if (key > mk) { mk = key; mj = joff + (uint32_t)(vl + VT * s); }
+                        if (key > mk) { mk = key; mj = (uint32_t)(vl + VT * s); }
                     }
                 }
                 warp_argmax64(mk, mj);
@@ -306,7 +359,7 @@ __global__ void __launch_bounds__(kCT, 1) mp_cluster_kernel(MPArgs a) {
                 for (int s = 0; s < E; ++s) {
                     if (fabsf(ch[s]) >= amax - window) {
                         const double m = fabs((double)ch[s] + (double)cl[s]);
-                        const uint32_t j = joff + (uint32_t)(vl + VT * s);
+                        const uint32_t j = (uint32_t)(vl + VT * s);
                         if (fabs(m - edge) < bandC) tie = true;
                         if (m >= edge && j < lower) lower = j;
                     }
@@ -328,7 +381,7 @@ __global__ void __launch_bounds__(kCT, 1) mp_cluster_kernel(MPArgs a) {
                 __syncthreads();
 #pragma unroll
                 for (int s = 0; s < E; ++s)
-                    if (joff + (uint32_t)(vl + VT * s) == lower) {
+                    if ((uint32_t)(vl + VT * s) == lower) {
                         sMisc[3] = 1u;
                         sMisc[4] = __float_as_uint(ch[s]);
                         sMisc[5] = __float_as_uint(cl[s]);
@@ -357,16 +410,28 @@ __global__ void __launch_bounds__(kCT, 1) mp_cluster_kernel(MPArgs a) {
                 else En = df{__fmaf_rn(-alpha.hi, alpha.hi, En.hi), 0.0f};
             }
 
-            // (a4) correlation update through the Gram matrix
-            const int fam1 = NF == 2 ? (int)(j1 >= (uint32_t)n) : 0;
-            const uint32_t f1 = j1 - (uint32_t)(fam1 * n);
-            if (NF == 2 && fam1 != fam) {
-                const int p1 = (int)(f1 % (uint32_t)B), q1 = (int)(f1 / (uint32_t)B);
-                const float2 vp = sV[p1 * B + p_own];
+            // (a4) correlation update through the Gram matrix: the other
+            // family on every CTA, the chosen element on its owner
+            const bool owner = j1 % (uint32_t)VT == (uint32_t)vl;
+            if (NF == 2) {
+                const int fam1 = (int)(j1 >= (uint32_t)n);
+                const int f1 = (int)j1 - fam1 * n;
+                const int p1 = f1 % B, q1 = f1 / B;
+                // the table of the chosen family's steps: W for a DCT atom, W^T for a Haar atom
+                const int tab = fam1;
+                const uint32_t raddr = sh_addr(sRow + (size_t)tab * RS * B + (p1 % RS) * B + p_own);
+                const float2 vp = ld_peer_f2(peer_addr(raddr, (uint32_t)(p1 / RS)));
                 const df u = DF ? df_mul(alpha, df{vp.x, vp.y}) : df{__fmul_rn(alpha.hi, vp.x), 0.0f};
-                top = top2_shift(update_family<B, VT, E, E, 0, 0, DF>(ch, cl, vl, u, sV + q1 * B), joff);
-            } else if (fam1 == fam && f1 % (uint32_t)VT == (uint32_t)vl) {
-                top = top2_shift(zero_and_rescan<VT, E, E, 0>(ch, cl, vl, f1), joff);
+                const float2 *wcol = sCol + (size_t)tab * B * CS + q1 * CS + hb;
+                if (fam1) {
+                    top[0] = update_cols<VT, E, G, 0, DF>(ch, cl, vl, u, wcol);
+                    if (owner) top[1] = zero_and_rescan<VT, E, G, G>(ch, cl, vl, j1);
+                } else {
+                    top[1] = update_cols<VT, E, G, G, DF>(ch, cl, vl, u, wcol);
+                    if (owner) top[0] = zero_and_rescan<VT, E, G, 0>(ch, cl, vl, j1);
+                }
+            } else if (owner) {
+                top[0] = zero_and_rescan<VT, E, G, 0>(ch, cl, vl, j1);
             }
             ++t;
         }
@@ -459,7 +524,8 @@ template <int NF, bool DF>
 static cudaError_t launch_cluster_t(const MPArgs &a, int num_sms, cudaStream_t st) {
     constexpr int C = 2 * NF, NW = kCT / 32;
     (void)num_sms;
-    const size_t smem = (NF == 2 ? (size_t)kCB * kCB * sizeof(float2) : 0) + 2 * NW * sizeof(uint4) +
+    // NF == 2: column slices 2 x b x 32 and row shards 2 x 32 x b double-float pairs (128 KB)
+    const size_t smem = (NF == 2 ? (size_t)4 * kCB * 32 * sizeof(float2) : 0) + 2 * NW * sizeof(uint4) +
                         2 * C * sizeof(uint4) + 2 * sizeof(unsigned long long) + 16 * sizeof(uint32_t) +
                         NW * (sizeof(unsigned long long) + sizeof(uint32_t)) + (size_t)a.lv.k * sizeof(StepRec);
     auto kern = mp_cluster_kernel<NF, DF>;
