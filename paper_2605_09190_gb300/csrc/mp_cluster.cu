@@ -129,6 +129,21 @@ __device__ __forceinline__ Top2 update_cols(float (&ch)[E], float (&cl)[E], int 
     return run2_top2<VT>(acc, v);
 }
 
+// A low word that no summary carries (a NaN pattern): marks the stop
+// verdict in warp 0's step summary.
+constexpr uint32_t kStopWord = 0x7fffffffu;
+
+// Bounded wait for phase `parity` of a local mbarrier fed by peers; false on
+// timeout or when another CTA has recorded an error (checked while waiting).
+__device__ __forceinline__ bool wait_phase(uint32_t bar, uint32_t parity, volatile unsigned *err) {
+    if (try_wait_cluster(bar, parity)) return true;
+    const unsigned long long t0 = now_ns();
+    for (unsigned it = 1;; ++it) {
+        if (try_wait_cluster(bar, parity)) return true;
+        if ((it & 255u) == 0u && (*err != 0u || now_ns() - t0 > kExchangeWaitNs)) return false;
+    }
+}
+
 // One exchange among the C CTAs of the cluster: lane r < C of warp 0 puts
 // `v` (equal on those lanes) into slot [seq & 1][rank] of CTA r with an
 // asynchronous store that completes 16 bytes on that slot's mbarrier there;
@@ -154,17 +169,7 @@ __device__ __forceinline__ bool cluster_exchange(uint4 *xs, unsigned long long *
         const uint32_t r = threadIdx.x;
         st_async_peer(peer_addr(sh_addr(xs + slot * C + rank), r), v, peer_addr(bar, r));
     }
-    if (threadIdx.x == 0) {
-        bool ok = true;
-        if (!try_wait_cluster(bar, parity)) {
-            const unsigned long long t0 = now_ns();
-            for (unsigned it = 1;; ++it) {
-                if (try_wait_cluster(bar, parity)) break;
-                if ((it & 255u) == 0u && (*err != 0u || now_ns() - t0 > kExchangeWaitNs)) { ok = false; break; }
-            }
-        }
-        *verdict = ok ? 1u : 0u;
-    }
+    if (threadIdx.x == 0) *verdict = wait_phase(bar, parity, err) ? 1u : 0u;
     __syncthreads();
     out = xs + slot * C;
     return *verdict != 0u;
@@ -191,10 +196,11 @@ __global__ void __launch_bounds__(kCT, 1) mp_cluster_kernel(MPArgs a) {
     float2 *sCol = reinterpret_cast<float2 *>(smem);                    // [2][B][CS]: W, W^T
     float2 *sRow = sCol + (NF == 2 ? 2 * B * CS : 0);                   // [2][RS][B]: W, W^T
     unsigned char *p = reinterpret_cast<unsigned char *>(sRow + (NF == 2 ? 2 * RS * B : 0));
-    uint4 *sPart = reinterpret_cast<uint4 *>(p);                        // [2][NW]
-    uint4 *sX = sPart + 2 * NW;                                         // [2][C] exchange slots
-    unsigned long long *sXbar = reinterpret_cast<unsigned long long *>(sX + 2 * C);   // [2]
-    uint32_t *sMisc = reinterpret_cast<uint32_t *>(sXbar + 2);          // [16]
+    uint4 *sXs = reinterpret_cast<uint4 *>(p);                          // [2][C][NW] step exchange
+    uint4 *sX = sXs + 2 * C * NW;                                       // [2][C] other exchanges
+    unsigned long long *sXbar = reinterpret_cast<unsigned long long *>(sX + 2 * C);   // [2], then [2] step
+    unsigned long long *sXsbar = sXbar + 2;
+    uint32_t *sMisc = reinterpret_cast<uint32_t *>(sXbar + 4);          // [16]
     unsigned long long *sRk = reinterpret_cast<unsigned long long *>(sMisc + 16);     // [NW]
     uint32_t *sRj = reinterpret_cast<uint32_t *>(sRk + NW);             // [NW]
     StepRec *steps = reinterpret_cast<StepRec *>(sRj + NW);             // [k], rank 0
@@ -220,7 +226,7 @@ __global__ void __launch_bounds__(kCT, 1) mp_cluster_kernel(MPArgs a) {
         }
     }
     if (threadIdx.x == 0) {
-        for (int s = 0; s < 2; ++s)
+        for (int s = 0; s < 4; ++s)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sh_addr(sXbar + s)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -232,8 +238,9 @@ __global__ void __launch_bounds__(kCT, 1) mp_cluster_kernel(MPArgs a) {
     const int k = lv.k;
     unsigned *work = &a.ctr->work_next[lv.level];
     unsigned long long n_attempts = 0, n_steps = 0, n_windows = 0;
-    int seq = 0;
+    int seq = 0, sseq = 0;
     bool aborted = false;
+    const int warp = lane >> 5;
     const uint4 *xr;
 
     for (;;) {
@@ -291,25 +298,36 @@ __global__ void __launch_bounds__(kCT, 1) mp_cluster_kernel(MPArgs a) {
                 break;
             }
 
-            // (a3) argmax: this CTA's summary, then the cluster's
-            const int buf = t & 1;
-            Top2 best = top[0];
+            // (a3) argmax: every warp's top-2 goes to every CTA of the
+            // cluster (lane r < C of each warp stores it into CTA r), so
+            // after one wait each CTA holds all C NW summaries and every warp
+            // reduces them alike; warp 0's entry carries the stop verdict.
+            Top2 best;
+            {
+                Top2 wb = top[0];
 #pragma unroll
-            for (int g = 1; g < NG; ++g) best = top2_merge(best, top[g]);
-            best = warp_top2(best);
-            if ((lane & 31) == 0) sPart[buf * NW + (lane >> 5)] = pack_top2(best);
-            if (lane == 0) sMisc[8 + buf] = below ? 1u : 0u;
-            __syncthreads();
-            if (sMisc[8 + buf] != 0u) { conv = true; break; }
-            best = (lane & 31) < NW ? unpack_top2(sPart[buf * NW + (lane & 31)]) : top2_empty();
-            best = warp_top2(best);
-            // the barrier above follows every read of the previous exchange
-            if (!cluster_exchange<C, false>(sX, sXbar, verdict, seq, rank, pack_top2(best), err, xr)) {
-                aborted = true;
-                break;
+                for (int g = 1; g < NG; ++g) wb = top2_merge(wb, top[g]);
+                wb = warp_top2(wb);
+                uint4 v = pack_top2(wb);
+                if (warp == 0 && below) v.w = kStopWord;
+                const int ss = sseq & 1;
+                const uint32_t spar = (uint32_t)(sseq >> 1) & 1u;
+                ++sseq;
+                const uint32_t sbar = sh_addr(sXsbar + ss);
+                if (lane == 0) arrive_expect_tx(sbar, (uint32_t)(C * NW * sizeof(uint4)));
+                if ((lane & 31) < C) {
+                    const uint32_t r = (uint32_t)(lane & 31);
+                    st_async_peer(peer_addr(sh_addr(sXs + (ss * C + (int)rank) * NW + warp), r), v,
+                                  peer_addr(sbar, r));
+                }
+                if (lane == 0) sMisc[13 + ss] = wait_phase(sbar, spar, err) ? 1u : 0u;
+                __syncthreads();
+                if (sMisc[13 + ss] == 0u) { aborted = true; break; }
+                const uint4 *xe = sXs + ss * C * NW;
+                if (xe[rank * NW].w == kStopWord) { conv = true; break; }
+                best = (lane & 31) < C * NW ? unpack_top2(xe[lane & 31]) : top2_empty();
+                best = warp_top2(best);
             }
-            best = (lane & 31) < C ? unpack_top2(xr[lane & 31]) : top2_empty();
-            best = warp_top2(best);
             if ((best.P >> 32) == 0ull) break;   // every correlation is exactly zero
             uint32_t j1 = top2_index(best);
             const float amax = top2_amax(best);
@@ -525,8 +543,8 @@ static cudaError_t launch_cluster_t(const MPArgs &a, int num_sms, cudaStream_t s
     constexpr int C = 2 * NF, NW = kCT / 32;
     (void)num_sms;
     // NF == 2: column slices 2 x b x 32 and row shards 2 x 32 x b double-float pairs (128 KB)
-    const size_t smem = (NF == 2 ? (size_t)4 * kCB * 32 * sizeof(float2) : 0) + 2 * NW * sizeof(uint4) +
-                        2 * C * sizeof(uint4) + 2 * sizeof(unsigned long long) + 16 * sizeof(uint32_t) +
+    const size_t smem = (NF == 2 ? (size_t)4 * kCB * 32 * sizeof(float2) : 0) + 2 * C * NW * sizeof(uint4) +
+                        2 * C * sizeof(uint4) + 4 * sizeof(unsigned long long) + 16 * sizeof(uint32_t) +
                         NW * (sizeof(unsigned long long) + sizeof(uint32_t)) + (size_t)a.lv.k * sizeof(StepRec);
     auto kern = mp_cluster_kernel<NF, DF>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
