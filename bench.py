@@ -262,7 +262,7 @@ def run_omp(args):
 
 PRECISION_ROOT = 128
 PRECISION_WORKLOAD = ("one 4096x4096 RGB synthetic image (piecewise scene per channel, seeds 0..2), RMSE tol 2, "
-                      "quadtree 128->4, k=b^2/4, DCT-II+Haar: exact form vs plain FP32 form")
+                      "quadtree 128->4, k=b^2/4, DCT-II+Haar: exact form vs plain FP32 form vs BF16 form")
 
 
 def run_precision(args):
@@ -280,7 +280,7 @@ def run_precision(args):
     planes = [torch.from_numpy(synthetic.piecewise_scene(n, n, seed=rank * 3 + c)).cuda() for c in range(3)]
     npix = 3 * n * n
     stream = torch.cuda.current_stream()
-    forms = {"exact": aqmp.AQMP_PREC_EXACT, "fp32": aqmp.AQMP_PREC_FP32}
+    forms = {"exact": aqmp.AQMP_PREC_EXACT, "fp32": aqmp.AQMP_PREC_FP32, "bf16": aqmp.AQMP_PREC_BF16}
     out = {}
     with ClockSampler(local) as clocks:
         for name, prec in forms.items():
@@ -304,20 +304,27 @@ def run_precision(args):
             if name == "exact":
                 kernels, _, launches = kernel_breakdown(aqmp, encode, lambda: None)
     le, ae, _ = out["exact"]["code"].copy()
-    lf, af, _ = out["fp32"]["code"].copy()
     key = lambda L: (int(L["plane"]), int(L["y"]), int(L["x"]), int(L["b"]))  # noqa: E731
-    fmap = {key(L): L for L in lf}
-    same_leaves = same_atoms = 0
-    for L in le:
-        F = fmap.get(key(L))
-        if F is None:
-            continue
-        a = ae["j"][int(L["atom_off"]):int(L["atom_off"]) + int(L["n_atoms"])]
-        b = af["j"][int(F["atom_off"]):int(F["atom_off"]) + int(F["n_atoms"])]
-        m = min(len(a), len(b))
-        pref = int(np.argmax(a[:m] != b[:m])) if m and np.any(a[:m] != b[:m]) else m
-        same_atoms += pref
-        same_leaves += int(len(a) == len(b) and pref == m)
+
+    def agreement(name):
+        """Share of the exact form's leaves reproduced with the same atoms,
+        and of its atom choices (common prefixes at shared leaf positions)."""
+        lf, af, _ = out[name]["code"].copy()
+        fmap = {key(L): L for L in lf}
+        same_leaves = same_atoms = 0
+        for L in le:
+            F = fmap.get(key(L))
+            if F is None:
+                continue
+            a = ae["j"][int(L["atom_off"]):int(L["atom_off"]) + int(L["n_atoms"])]
+            b = af["j"][int(F["atom_off"]):int(F["atom_off"]) + int(F["n_atoms"])]
+            m = min(len(a), len(b))
+            pref = int(np.argmax(a[:m] != b[:m])) if m and np.any(a[:m] != b[:m]) else m
+            same_atoms += pref
+            same_leaves += int(len(a) == len(b) and pref == m)
+        return len(lf), same_leaves / max(1, len(le)), same_atoms / max(1, len(ae))
+
+    agree = {name: agreement(name) for name in forms if name != "exact"}
     quality = {}
     rec = torch.empty((n, n), dtype=torch.float32, device="cuda")
     s_out = torch.zeros((), dtype=torch.float64, device="cuda")
@@ -342,7 +349,11 @@ def run_precision(args):
                                      "l2": "inputs (50 M px) and working set exceed L2"},
                           "fp32_form": {"value": weak_scaling_value(npix, args.steps, out["fp32"]["s"], world),
                                         "unit": "MP/s"},
-                          "leaves": {"exact": len(le), "fp32": len(lf)},
+                          "bf16_form": {"value": weak_scaling_value(npix, args.steps, out["bf16"]["s"], world),
+                                        "unit": "MP/s", "leaves": agree["bf16"][0],
+                                        "same_leaves_share": agree["bf16"][1],
+                                        "same_atom_choices_share": agree["bf16"][2]},
+                          "leaves": {"exact": len(le), "fp32": agree["fp32"][0]},
                           "per_level": {f"b{(args.root or PRECISION_ROOT) >> i}": {
                               "attempts": out["exact"]["stats"]["attempts_per_level"][i],
                               "atom_iterations": out["exact"]["stats"]["iterations_per_level"][i],
@@ -351,8 +362,8 @@ def run_precision(args):
                           "kernels_ms": {k: round(v[1], 3) for k, v in sorted(kernels.items(),
                                                                               key=lambda kv: -kv[1][1])},
                           "gpu_launches_per_encode": launches,
-                          "same_leaves_share": same_leaves / max(1, len(le)),
-                          "same_atom_choices_share": same_atoms / max(1, len(ae)),
+                          "same_leaves_share": agree["fp32"][1],
+                          "same_atom_choices_share": agree["fp32"][2],
                           "quality": quality, "autotune": autotune_choices(aqmp),
                           "clocks": clocks.summary()}))
     return 0

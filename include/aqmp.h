@@ -55,6 +55,11 @@ extern "C" {
                                       rounded to FP32, FP32 pursuit state (one
                                       FMA per Gram entry), FP32 energy and stop
                                       test; faster, decisions not certified */
+#define AQMP_PREC_BF16      2      /* the reduced-precision form: the correlation
+                                      from one BF16 tensor-core pass of bf16(D)
+                                      (FP32 accumulation, no exact digits), then
+                                      the FP32 form's pursuit; decisions not
+                                      certified */
 
 /* aqmp_params.flags */
 #define AQMP_FLAG_INPUT_DEVICE  1u /* plane pointers are device addresses */
@@ -236,7 +241,9 @@ int aqmp_ssim(const float *x, const float *y, int h, int w, int64_t pitch, doubl
  * holding L blocks of b x b bytes, each row-major and contiguous; `corr` is
  * device memory for L x M float pairs (hi, lo) whose sum is the correlation
  * of the 2^-48 fixed-point dictionary with the block, rounded once.
- * gemm: 0 = tcgen05 tensor-core kernel, 1 = integer SIMT kernel. */
+ * gemm: 0 = tcgen05 tensor-core kernel, 1 = integer SIMT kernel (both exact,
+ * identical bits), 2 = the reduced-precision BF16 form (one tcgen05 pass of
+ * bf16(D), FP32 accumulation; low words 0). */
 int aqmp_correlate(int b, int dict_id, const uint8_t *blocks, int64_t L, float *corr,
                    int gemm, void *stream);
 

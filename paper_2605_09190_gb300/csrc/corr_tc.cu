@@ -156,11 +156,15 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
 
 }  // namespace tc
 
+// L = kLimbs: the exact form above.  L = 1: the reduced-precision form --
+// one BF16 matrix bf16(D) against the centred pixels, FP32 accumulation,
+// c0 = acc + 128 Sbf[j] (Sbf the row sums of bf16(D)), low word 0.
+template <int L>
 __global__ void __launch_bounds__(tc::kThreads, 1)
 corr_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M,
                int Mpad, int kb0, int KB, int mode, const long long *__restrict__ Sh,
-               const long long *__restrict__ Sl, const unsigned *count_dev, long long fixed_count,
-               float2 *__restrict__ c0, Counters *ctr) {
+               const long long *__restrict__ Sl, const float *__restrict__ Sbf, const unsigned *count_dev,
+               long long fixed_count, float2 *__restrict__ c0, Counters *ctr) {
     using namespace tc;
     const long long count = count_dev ? (long long)*count_dev : fixed_count;
     const long long leaf0 = (long long)blockIdx.x * kN;
@@ -207,7 +211,7 @@ corr_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             mbar_expect_tx(fullB(sb), kTileB);
             tma_load_2d(sB + sb * kTileB, &tmB, fullB(sb), (kb0 + kb) * kK, (int)leaf0);
             if (++sb == kStagesB) { sb = 0; pb ^= 1u; }
-            for (int s = 0; s < kLimbs; ++s) {
+            for (int s = 0; s < L; ++s) {
                 if (!mbar_wait(emptyA(sa), pa ^ 1u, abort_flag)) break;
                 mbar_expect_tx(fullA(sa), kTileA);
                 tma_load_2d(sA + sa * kTileA, &tmA, fullA(sa), (kb0 + kb) * kK, s * Mpad + m0);
@@ -221,7 +225,7 @@ corr_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         bool ok = true;
         for (int kb = 0; kb < KB && ok; ++kb) {
             if (!(ok = mbar_wait(fullB(sb), pb, abort_flag))) break;
-            for (int s = 0; s < kLimbs; ++s) {
+            for (int s = 0; s < L; ++s) {
                 if (!(ok = mbar_wait(fullA(sa), pa, abort_flag))) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const unsigned long long ad = smem_desc(sA + sa * kTileA);
@@ -244,7 +248,23 @@ corr_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     // Epilogue: warp w reads TMEM lanes 32w..32w+31 (atoms m0 + 32w + lane).
     const bool acc_ok = mbar_wait(accBar, 0u, abort_flag) && !*abort_flag;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (acc_ok) {
+    if (acc_ok && L == 1) {
+        const int m = m0 + warp * 32 + lane;
+        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+        const float centre = m < M ? 128.0f * Sbf[m] : 0.0f;
+        for (int nb = 0; nb < kN; nb += 8) {
+            float P[8];
+            tmem_ld8(lane_addr + (uint32_t)nb, P);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (m < M) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const long long leaf = leaf0 + nb + i;
+                    if (leaf < count) c0[leaf * M + m] = make_float2(P[i] + centre, 0.0f);
+                }
+            }
+        }
+    } else if (acc_ok) {
         const int m = m0 + warp * 32 + lane;
         const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
         const long long sh = m < M ? 128ll * Sh[m] : 0, sl = m < M ? 128ll * Sl[m] : 0;
@@ -294,6 +314,23 @@ corr_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 
 bool corr_tc_available() { return true; }
 
+cudaError_t launch_corr_tc_bf16(const CorrArgs &a, cudaStream_t st) {
+    const DictDev &d = *a.d;
+    if (!d.tmap_bf16 || !d.Sbf) return cudaErrorInvalidValue;
+    const long long rows = a.count ? (long long)a.capacity : a.fixed_count;
+    dim3 grid((unsigned)((rows + tc::kN - 1) / tc::kN), (unsigned)(d.Mpad / tc::kM));
+    if (grid.x == 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(corr_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         tc::kSmemBytes);
+    if (e != cudaSuccess) return e;
+    const CUtensorMap *ma = reinterpret_cast<const CUtensorMap *>(d.tmap_bf16);
+    const CUtensorMap *mb = reinterpret_cast<const CUtensorMap *>(a.tmap_Y);
+    corr_tc_kernel<1><<<grid, tc::kThreads, tc::kSmemBytes, st>>>(*ma, *mb, d.M, d.Mpad, 0, d.Kpad / tc::kK,
+                                                                  kCorrSingle, nullptr, nullptr, d.Sbf, a.count,
+                                                                  a.fixed_count, a.c0, a.ctr);
+    return cudaGetLastError();
+}
+
 // Failure-path check: one thread waits, through the same bounded wait as the
 // correlation kernel, on an mbarrier that nothing ever arrives on, and must
 // give up after `limit_ns` and record AQMP_E_TIMEOUT in the error word.
@@ -318,7 +355,8 @@ cudaError_t launch_corr_tc(const CorrArgs &a, cudaStream_t st) {
     const long long rows = a.count ? (long long)a.capacity : a.fixed_count;
     dim3 grid((unsigned)((rows + tc::kN - 1) / tc::kN), (unsigned)(d.Mpad / tc::kM));
     if (grid.x == 0) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(corr_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes);
+    cudaError_t e = cudaFuncSetAttribute(corr_tc_kernel<kLimbs>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         tc::kSmemBytes);
     if (e != cudaSuccess) return e;
     const CUtensorMap *ma = reinterpret_cast<const CUtensorMap *>(d.tmap_limbs);
     const CUtensorMap *mb = reinterpret_cast<const CUtensorMap *>(a.tmap_Y);
@@ -328,8 +366,8 @@ cudaError_t launch_corr_tc(const CorrArgs &a, cudaStream_t st) {
     for (int c = 0; c < chunks; ++c) {
         const int kb0 = c * chunk, kbs = std::min(chunk, kblocks - kb0);
         const int mode = chunks == 1 ? kCorrSingle : c == 0 ? kCorrFirst : c == chunks - 1 ? kCorrLast : kCorrMiddle;
-        corr_tc_kernel<<<grid, tc::kThreads, tc::kSmemBytes, st>>>(*ma, *mb, d.M, d.Mpad, kb0, kbs, mode, d.Sh,
-                                                                   d.Sl, a.count, a.fixed_count, a.c0, a.ctr);
+        corr_tc_kernel<kLimbs><<<grid, tc::kThreads, tc::kSmemBytes, st>>>(
+            *ma, *mb, d.M, d.Mpad, kb0, kbs, mode, d.Sh, d.Sl, nullptr, a.count, a.fixed_count, a.c0, a.ctr);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;

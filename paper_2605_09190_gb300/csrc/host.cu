@@ -289,6 +289,9 @@ struct Dict {
     DeviceBuf limbs, dh, dl, sh, sl, w, basis, basis64;
     CUtensorMap tmap;
     bool tables = false;         // fixed-point correlation tables built (16 M n B + 8 M n B)
+    DeviceBuf dbf, sbf;          // reduced-precision form: bf16(D) and its row sums
+    CUtensorMap tmap_bf;
+    bool bf16 = false;
 };
 
 struct Ctx {
@@ -362,8 +365,9 @@ int num_families(int dict_id) { return dict_id == AQMP_DICT_DCT_HAAR ? 2 : 1; }
 // Tables of one (side, dictionary), built once per device: the FP32/FP64
 // bases and W always; the fixed-point correlation tables (digit planes and
 // (Dh, Dl): 24 M n bytes, 12.9 GB at side 128) only when `tables` is set,
-// so that decoding and synthesis never build them.
-int get_dict(Ctx *c, int b, int dict_id, cudaStream_t st, Dict **out, bool tables = true) {
+// so that decoding and synthesis never build them; bf16(D) (2 M Kpad bytes)
+// only when `bf16` is set (the reduced-precision form).
+int get_dict(Ctx *c, int b, int dict_id, cudaStream_t st, Dict **out, bool tables = true, bool bf16 = false) {
     const int key = b * 16 + dict_id;
     auto it = c->dicts.find(key);
     Dict *D = nullptr;
@@ -437,6 +441,20 @@ int get_dict(Ctx *c, int b, int dict_id, cudaStream_t st, Dict **out, bool table
         CK(cudaStreamSynchronize(st));
         D->tables = true;
     }
+    if (bf16 && !D->bf16) {
+        DictDev &d = D->d;
+        int rc;
+        if ((rc = D->dbf.reserve(sizeof(__nv_bfloat16) * (size_t)d.Mpad * d.Kpad))) return rc;
+        if ((rc = D->sbf.reserve(sizeof(float) * (size_t)d.M))) return rc;
+        d.Dbf = (__nv_bfloat16 *)D->dbf.p;
+        d.Sbf = (float *)D->sbf.p;
+        const int fam0 = dict_id == AQMP_DICT_HAAR ? 1 : 0;
+        CK(build_bf16_tables(d, (const double *)D->basis64.p, fam0, st));
+        if ((rc = encode_bf16_map(&D->tmap_bf, d.Dbf, (unsigned long long)d.Mpad, d.Kpad, 128))) return rc;
+        d.tmap_bf16 = &D->tmap_bf;
+        CK(cudaStreamSynchronize(st));
+        D->bf16 = true;
+    }
     *out = D;
     return AQMP_OK;
 }
@@ -450,7 +468,7 @@ int check_params(const aqmp_params *p) {
         return fail(AQMP_E_ARG, "block sizes must be powers of two with 4 <= min_block <= max_block");
     if (p->max_block > kMaxSide) return fail(AQMP_E_UNSUPPORTED, "max_block above %d is not built", kMaxSide);
     if (p->dict_id < 0 || p->dict_id > 2) return fail(AQMP_E_DICT, "unknown dictionary id %d", p->dict_id);
-    if (p->precision != AQMP_PREC_EXACT && p->precision != AQMP_PREC_FP32)
+    if (p->precision != AQMP_PREC_EXACT && p->precision != AQMP_PREC_FP32 && p->precision != AQMP_PREC_BF16)
         return fail(AQMP_E_UNSUPPORTED, "unknown precision %d", p->precision);
     return AQMP_OK;
 }
@@ -549,6 +567,7 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
     const bool tune = (P.flags & AQMP_FLAG_NO_AUTOTUNE) == 0;
     const bool alt_threads = (P.flags & AQMP_FLAG_ALT_THREADS) != 0;
     const bool omp = (P.flags & AQMP_FLAG_OMP) != 0;
+    const bool bf16 = P.precision == AQMP_PREC_BF16;
     if (omp) {
         if (P.max_block > 16 || P.precision != AQMP_PREC_EXACT)
             return fail(AQMP_E_UNSUPPORTED, "OMP needs max_block <= 16 and the exact precision");
@@ -580,7 +599,7 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
     const int nlev = ilog2(P.max_block) - ilog2(P.min_block) + 1;
     std::vector<Dict *> dicts(nlev);
     for (int l = 0; l < nlev; ++l)
-        if ((rc = get_dict(c, P.max_block >> l, P.dict_id, st, &dicts[l]))) return rc;
+        if ((rc = get_dict(c, P.max_block >> l, P.dict_id, st, &dicts[l], !bf16, bf16))) return rc;
 
     // capacities
     std::vector<unsigned long long> cap(nlev), qoff(nlev + 1, 0);
@@ -673,7 +692,8 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
         if (!tune) return true;
         for (int l = 0; l < nlev; ++l) {
             const int b = P.max_block >> l;
-            if (!simt && c->tuner.slot(Tuner::CORR, b, P.dict_id, P.precision, cap[l]).chosen < 0) return false;
+            if (!simt && !bf16 && c->tuner.slot(Tuner::CORR, b, P.dict_id, P.precision, cap[l]).chosen < 0)
+                return false;
             if (!alt_threads && !omp && mp_has_variant(b, dicts[l]->d.nf) &&
                 c->tuner.slot(Tuner::MP, b, P.dict_id, P.precision, cap[l]).chosen < 0)
                 return false;
@@ -740,7 +760,9 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
         auto corr_simt = [&] {
             return g_prof.run(kname("corr_simt", b), st, [&] { return launch_corr_simt(ca, st); });
         };
-        if (simt) {
+        if (bf16) {
+            CK(g_prof.run(kname("corr_bf16", b), st, [&] { return launch_corr_tc_bf16(ca, st); }));
+        } else if (simt) {
             CK(corr_simt());
         } else if (!tune) {
             CK(corr_tc());
@@ -1166,8 +1188,9 @@ int aqmp_correlate(int b, int dict_id, const uint8_t *blocks, int64_t L, float *
     if ((rc = get_ctx(&c))) return rc;
     std::lock_guard<std::mutex> lock(c->mu);
     cudaStream_t st = (cudaStream_t)stream;
+    if (gemm < 0 || gemm > 2) return fail(AQMP_E_ARG, "gemm must be 0 (tensor cores), 1 (SIMT) or 2 (BF16 form)");
     Dict *D;
-    if ((rc = get_dict(c, b, dict_id, st, &D))) return rc;
+    if ((rc = get_dict(c, b, dict_id, st, &D, gemm != 2, gemm == 2))) return rc;
     const DictDev &d = D->d;
     if ((rc = c->Y.reserve(sizeof(__nv_bfloat16) * (size_t)L * d.Kpad))) return rc;
     CK(launch_gather_blocks(b, d.Kpad, blocks, L, (__nv_bfloat16 *)c->Y.p, nullptr, c->num_sms, st));
@@ -1179,10 +1202,11 @@ int aqmp_correlate(int b, int dict_id, const uint8_t *blocks, int64_t L, float *
     ca.capacity = (unsigned)L;
     ca.c0 = (float2 *)corr;
     CUtensorMap ym;
-    if (gemm == 0) {
+    if (gemm == 0 || gemm == 2) {
         if ((rc = encode_bf16_map(&ym, c->Y.p, (unsigned long long)L, d.Kpad, 64))) return rc;
         ca.tmap_Y = &ym;
-        CK(g_prof.run(kname("corr_tc", b), st, [&] { return launch_corr_tc(ca, st); }));
+        if (gemm == 0) CK(g_prof.run(kname("corr_tc", b), st, [&] { return launch_corr_tc(ca, st); }));
+        else CK(g_prof.run(kname("corr_bf16", b), st, [&] { return launch_corr_tc_bf16(ca, st); }));
     } else {
         CK(g_prof.run(kname("corr_simt", b), st, [&] { return launch_corr_simt(ca, st); }));
     }

@@ -68,6 +68,9 @@ struct DictDev {
     float2 *W, *WT;              // b x b (hi, lo)
     float *basis;                // [2][b][b] FP32 1-D bases (DCT, Haar) for decoding
     void *tmap_limbs;            // CUtensorMap for the tensor-core kernel (host copy)
+    __nv_bfloat16 *Dbf;          // [Mpad][Kpad] bf16(D) (reduced-precision form; built on demand)
+    float *Sbf;                  // [M] row sums of bf16(D)
+    void *tmap_bf16;             // CUtensorMap of Dbf (host copy)
 };
 
 // Initial correlation (corr_simt.cu / corr_tc.cu): c0[l][j] for l < *count.
@@ -83,6 +86,8 @@ struct CorrArgs {
 };
 cudaError_t launch_corr_simt(const CorrArgs &a, cudaStream_t st);
 cudaError_t launch_corr_tc(const CorrArgs &a, cudaStream_t st);
+// Reduced-precision form: one BF16 pass of bf16(D), FP32 accumulation (c0 low words 0).
+cudaError_t launch_corr_tc_bf16(const CorrArgs &a, cudaStream_t st);
 bool corr_tc_available();
 cudaError_t launch_wait_selftest(Counters *ctr, unsigned long long limit_ns, cudaStream_t st);
 
@@ -167,6 +172,8 @@ cudaError_t launch_color(const ColorArgs &a, bool to_planes, int num_sms, cudaSt
 // basis_dev = [2][b][b] (DCT, Haar); fam0 selects the family of a
 // single-family dictionary (0 = DCT, 1 = Haar).
 cudaError_t build_fixed_tables_fam(DictDev &d, const double *basis_dev, int fam0, cudaStream_t st);
+// bf16(D) and its row sums for the reduced-precision form.
+cudaError_t build_bf16_tables(DictDev &d, const double *basis_dev, int fam0, cudaStream_t st);
 // FP32 copy of the FP64 bases (decoder tables).
 cudaError_t launch_basis_to_float(const double *basis_dev, float *out, int count, cudaStream_t st);
 

@@ -8,6 +8,8 @@
 // D_fix = round(D 2^48), and stored three ways: as 8 balanced base-64 BF16
 // digits for the tensor cores, as a (Dh, Dl) pair for the SIMT kernel, and
 // through its per-atom sum for the centring correction.
+#include <algorithm>
+
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
@@ -86,6 +88,50 @@ cudaError_t build_fixed_tables_fam(DictDev &d, const double *basis_dev, int fam0
     int sblocks = (d.M + 7) / 8;
     if (sblocks > 4096) sblocks = 4096;
     fixed_sums_kernel<<<sblocks, 256, 0, st>>>(d.b, d.n, d.M, d.nf, fam0, basis_dev, d.Sh, d.Sl);
+    return cudaGetLastError();
+}
+
+// bf16(D[j][v]) rounded to nearest from the FP64 entry, zero padding to
+// [Mpad][Kpad], and one warp per atom for the row sum of the BF16 values
+// (summed in FP64, rounded once to FP32).
+__global__ void bf16_table_kernel(int b, int n, int M, int nf, int fam0, const double *basis, int Mpad, int Kpad,
+                                  __nv_bfloat16 *Dbf) {
+    const long long total = (long long)Mpad * Kpad;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(idx / Kpad), v = (int)(idx - (long long)j * Kpad);
+        double d = 0.0;
+        if (j < M && v < n) {
+            const int fam = nf == 2 ? j / n : fam0;
+            const int f = j - (nf == 2 ? (j / n) * n : 0);
+            const int p = f % b, q = f / b, m = v / b, i = v - m * b;
+            const double *B = basis + (size_t)fam * b * b;
+            d = B[p * b + i] * B[q * b + m];
+        }
+        Dbf[idx] = __double2bfloat16(d);
+    }
+}
+
+__global__ void bf16_sums_kernel(int n, int M, int Kpad, const __nv_bfloat16 *Dbf, float *Sbf) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < M; j += warps) {
+        double s = 0.0;
+        for (int v = lane; v < n; v += 32) s += (double)__bfloat162float(Dbf[(size_t)j * Kpad + v]);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (lane == 0) Sbf[j] = (float)s;
+    }
+}
+
+cudaError_t build_bf16_tables(DictDev &d, const double *basis_dev, int fam0, cudaStream_t st) {
+    const long long total = (long long)d.Mpad * d.Kpad;
+    int blocks = (int)std::min<long long>((total + 255) / 256, 8192);
+    bf16_table_kernel<<<blocks, 256, 0, st>>>(d.b, d.n, d.M, d.nf, fam0, basis_dev, d.Mpad, d.Kpad, d.Dbf);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    int sblocks = std::min((d.M + 7) / 8, 4096);
+    bf16_sums_kernel<<<sblocks, 256, 0, st>>>(d.n, d.M, d.Kpad, d.Dbf, d.Sbf);
     return cudaGetLastError();
 }
 

@@ -52,3 +52,28 @@ def test_tensor_core_matches_simt_and_fp64(lib, b, dict_id, L):
         bound = (2.0 ** -47 * np.sum(np.abs(y)) + 2.0 ** -46 * np.abs(ref) + 1e-12
                  + y.size * 2.0 ** -53 * (Dabs @ np.abs(y)))
         assert np.all(np.abs(got - ref) <= bound), (l, np.max(np.abs(got - ref) - bound))
+
+
+@pytest.mark.parametrize("b,dict_id,L", [(8, 0, 65), (32, 0, 70), (64, 2, 5), (128, 0, 3)])
+def test_bf16_form_is_within_its_rounding_bound(lib, b, dict_id, L):
+    """The reduced-precision form: one BF16 pass of bf16(D) with FP32
+    accumulation.  Against the FP64 D^T y: bf16 rounding of each entry
+    (2^-9 relative), FP32 accumulation over n terms of the centred pixels,
+    and the FP32 centring term."""
+    host = _blocks(L, b, seed=b * 7 + L + dict_id)
+    dev = torch.from_numpy(host).cuda()
+    got = lib.aqmp_correlate(b, dict_id, dev, gemm=2).cpu().numpy()
+    assert np.all(got[:, :, 1] == 0.0)
+    D = oracle.dictionary(b, dict_id)
+    Dabs = np.abs(D)
+    worst = 0.0
+    for l in range(L):
+        y = oracle.unravel(host[l])
+        ref = D @ y
+        bound = (2.0 ** -8 * (Dabs @ np.abs(y)) + y.size * 2.0 ** -23 * (Dabs @ np.abs(y - 128.0))
+                 + 2.0 ** -20 * (np.abs(ref) + 128.0 * Dabs.sum(axis=1)) + 1e-6)
+        err = np.abs(got[l, :, 0].astype(np.float64) - ref)
+        assert np.all(err <= bound), (l, float(np.max(err - bound)))
+        worst = max(worst, float(np.max(err)))
+    # an approximation, not the exact form (a constant block can come out exact)
+    assert worst > 0.0

@@ -64,3 +64,22 @@ def test_fp32_form_is_valid_and_close_to_the_exact_form(lib, tmp_path):
     os.makedirs("gpurun_out", exist_ok=True)
     with open("gpurun_out/fp32_form_report.json", "w") as f:
         json.dump(report, f, indent=1)
+
+
+@pytest.mark.parametrize("max_block", [64, 128])
+def test_bf16_form_tiles_and_stays_close_to_the_exact_form(lib, max_block):
+    """The reduced-precision form (BF16 correlation, FP32 pursuit): a valid
+    quadtree whose reconstruction is within a fraction of a dB of the exact
+    (certified) form's."""
+    img = synthetic.piecewise_scene(256, 256, seed=3)
+    dev = torch.from_numpy(img).cuda()
+    codes = {p: lib.aqmp_encode_planes([dev], 2.0, max_block=max_block, precision=p)
+             for p in (lib.AQMP_PREC_EXACT, lib.AQMP_PREC_BF16)}
+    psnr = {}
+    for p, code in codes.items():
+        leaves, atoms, lo = code.copy()
+        assert int(np.sum(leaves["b"].astype(np.int64) ** 2)) == img.size
+        out = torch.empty(img.shape, dtype=torch.float32, device="cuda")
+        code.decode(0, out)
+        psnr[p] = oracle.psnr(out.cpu().numpy().astype(np.float64), img)
+    assert abs(psnr[lib.AQMP_PREC_BF16] - psnr[lib.AQMP_PREC_EXACT]) < 0.5
