@@ -98,7 +98,7 @@ def run_refine(args):
         print(json.dumps({"metric": "coefficient refinement Adam steps/s", "value": world / step_s,
                           "unit": "steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                           "ms_per_step": 1e3 * step_s, "higher_is_better": True, "scaling": "weak",
-                          "vs_baseline": None, "dtype": "f32 synthesis, f64 SSIM statistics", "data": "synthetic",
+                          "vs_baseline": None, "dtype": "f32 synthesis, f32x2 SSIM window sums, f64 window formula", "data": "synthetic",
                           "config": {"workload": REFINE_WORKLOAD, "planes": 16, "coefficients": int(st["n_atoms"]),
                                      "leaves": int(st["n_leaves"])},
                           "ssim_plain_mp": hist[0], "ssim_refined": final, "ssim_gain": final - hist[0],

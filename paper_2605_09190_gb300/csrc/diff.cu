@@ -19,7 +19,8 @@
 //   f_my = f (2 mx / A1 - 2 mx / A2 - 2 my / B1 + 2 my / B2),
 //   f_Exy = 2 f / A2,   f_Eyy = -f / B2,
 // i.e. the per-window partials filtered back with the (symmetric, separable)
-// window.  The window statistics and partials are accumulated in FP64.
+// window.  The window statistics and the back-filtered partials are
+// accumulated in double-float; the per-window formula runs in FP64.
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -81,34 +82,54 @@ __global__ void synth_backward_kernel(const LeafRec *leaves, unsigned long long 
     }
 }
 
+// The 11-tap passes run in double-float on the FP32 pipes (GB300's FP64
+// rate is a small fraction of its FP32 rate): each tap adds g v with the
+// weight g as a (hi, lo) pair and v a pixel, an exact pixel product, or a
+// stored pair, so the window sums keep ~2^-46 relative accuracy and
+// E[x^2] - mu^2 is formed in FP64 from them without losing the variance.
+// Intermediate planes hold (hi, lo) float pairs in the 8-byte slots.
+__constant__ float2 c_gauss_df[11];
+
+__device__ __forceinline__ df gw(int j) {
+    const float2 g = c_gauss_df[j];
+    return df{-g.x, -g.y};                          // negated: s - (-g) v = s + g v
+}
+
+__device__ __forceinline__ df df_of(double d) {
+    const float hi = (float)d;
+    return df{hi, (float)(d - (double)hi)};
+}
+
 // Horizontal 11-tap pass of the five products (x, y, x^2, y^2, x y) over the
 // valid columns: H[k][row][a] for a < w - 10.
-__global__ void ssim_hpass_kernel(const float *x, const float *y, int h, int w, long long pitch, double *H) {
+__global__ void ssim_hpass_kernel(const float *x, const float *y, int h, int w, long long pitch, float2 *H) {
     const int wo = w - 10;
     const long long plane = (long long)h * wo;
     for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < plane;
          idx += (long long)gridDim.x * blockDim.x) {
         const int r = (int)(idx / wo), a = (int)(idx - (long long)r * wo);
-        double sx = 0, sy = 0, sxx = 0, syy = 0, sxy = 0;
+        df sx{0.0f, 0.0f}, sy = sx, sxx = sx, syy = sx, sxy = sx;
+#pragma unroll
         for (int j = 0; j < 11; ++j) {
-            const double g = c_gauss[j];
-            const double xv = x[(long long)r * pitch + a + j], yv = y[(long long)r * pitch + a + j];
-            sx += g * xv;
-            sy += g * yv;
-            sxx += g * xv * xv;
-            syy += g * yv * yv;
-            sxy += g * xv * yv;
+            const df g = gw(j);
+            const float xv = x[(long long)r * pitch + a + j], yv = y[(long long)r * pitch + a + j];
+            sx = df_sub_mul(sx, g, df{xv, 0.0f});
+            sy = df_sub_mul(sy, g, df{yv, 0.0f});
+            sxx = df_sub_mul(sxx, g, df_two_prod(xv, xv));
+            syy = df_sub_mul(syy, g, df_two_prod(yv, yv));
+            sxy = df_sub_mul(sxy, g, df_two_prod(xv, yv));
         }
-        H[idx] = sx;
-        H[plane + idx] = sy;
-        H[2 * plane + idx] = sxx;
-        H[3 * plane + idx] = syy;
-        H[4 * plane + idx] = sxy;
+        H[idx] = make_float2(sx.hi, sx.lo);
+        H[plane + idx] = make_float2(sy.hi, sy.lo);
+        H[2 * plane + idx] = make_float2(sxx.hi, sxx.lo);
+        H[3 * plane + idx] = make_float2(syy.hi, syy.lo);
+        H[4 * plane + idx] = make_float2(sxy.hi, sxy.lo);
     }
 }
 
-// Vertical pass, SSIM per window, its partials (scaled) and the mean.
-__global__ void ssim_window_kernel(const double *H, int h, int w, double *P, double *sum, double gscale) {
+// Vertical pass, SSIM per window, its partials (scaled) and the mean.  The
+// window formula runs in FP64 from the double-float sums, with one division.
+__global__ void ssim_window_kernel(const float2 *H, int h, int w, double *P, double *sum, double gscale) {
     const int wo = w - 10, ho = h - 10;
     const long long hplane = (long long)h * wo, wins = (long long)ho * wo;
     const double C1 = (0.01 * 255.0) * (0.01 * 255.0), C2 = (0.03 * 255.0) * (0.03 * 255.0);
@@ -116,22 +137,32 @@ __global__ void ssim_window_kernel(const double *H, int h, int w, double *P, dou
     for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < wins;
          idx += (long long)gridDim.x * blockDim.x) {
         const int r = (int)(idx / wo), a = (int)(idx - (long long)r * wo);
-        double m[5] = {0, 0, 0, 0, 0};
+        df m[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) m[k] = df{0.0f, 0.0f};
+#pragma unroll
         for (int i = 0; i < 11; ++i) {
-            const double g = c_gauss[i];
+            const df g = gw(i);
             const long long o = (long long)(r + i) * wo + a;
 #pragma unroll
-            for (int k = 0; k < 5; ++k) m[k] += g * H[k * hplane + o];
+            for (int k = 0; k < 5; ++k) {
+                const float2 v = H[k * hplane + o];
+                m[k] = df_sub_mul(m[k], g, df{v.x, v.y});
+            }
         }
-        const double mx = m[0], my = m[1];
-        const double A1 = 2 * mx * my + C1, A2 = 2 * (m[4] - mx * my) + C2;
-        const double B1 = mx * mx + my * my + C1, B2 = (m[2] - mx * mx) + (m[3] - my * my) + C2;
-        const double f = (A1 * A2) / (B1 * B2);
+        const double mx = df_to_double(m[0]), my = df_to_double(m[1]);
+        const double exx = df_to_double(m[2]), eyy = df_to_double(m[3]), exy = df_to_double(m[4]);
+        const double A1 = 2 * mx * my + C1, A2 = 2 * (exy - mx * my) + C2;
+        const double B1 = mx * mx + my * my + C1, B2 = (exx - mx * mx) + (eyy - my * my) + C2;
+        const double A12 = A1 * A2, B12 = B1 * B2;
+        const double r1 = 1.0 / (A12 * B12);                 // 1 / (A1 A2 B1 B2)
+        const double f = A12 * A12 * r1;                      // A1 A2 / (B1 B2)
         local += f;
         if (P) {
-            P[idx] = gscale * f * (2 * mx / A1 - 2 * mx / A2 - 2 * my / B1 + 2 * my / B2);   // f_my
-            P[wins + idx] = gscale * (-f / B2);                                            // f_Eyy
-            P[2 * wins + idx] = gscale * (2 * f / A2);                                     // f_Exy
+            const double iA1 = A2 * B12 * r1, iA2 = A1 * B12 * r1, iB1 = A12 * B2 * r1, iB2 = A12 * B1 * r1;
+            P[idx] = gscale * f * (2 * mx * iA1 - 2 * mx * iA2 - 2 * my * iB1 + 2 * my * iB2);   // f_my
+            P[wins + idx] = gscale * (-f * iB2);                                              // f_Eyy
+            P[2 * wins + idx] = gscale * (2 * f * iA2);                                       // f_Exy
         }
     }
     // block sum, one atomic per block
@@ -148,49 +179,55 @@ __global__ void ssim_window_kernel(const double *H, int h, int w, double *P, dou
 
 // Back through the vertical pass: V[k][row][a] = sum_i g[i] P[k][row - i][a]
 // over the windows whose first row is row - i (full height, valid columns).
-__global__ void ssim_vback_kernel(const double *P, int h, int w, double *V) {
+__global__ void ssim_vback_kernel(const double *P, int h, int w, float2 *V) {
     const int wo = w - 10, ho = h - 10;
     const long long wins = (long long)ho * wo, vplane = (long long)h * wo;
     for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < vplane;
          idx += (long long)gridDim.x * blockDim.x) {
         const int r = (int)(idx / wo), a = (int)(idx - (long long)r * wo);
-        double s0 = 0, s1 = 0, s2 = 0;
+        df s0{0.0f, 0.0f}, s1 = s0, s2 = s0;
+#pragma unroll
         for (int i = 0; i < 11; ++i) {
             const int wr = r - i;
             if (wr < 0 || wr >= ho) continue;
-            const double g = c_gauss[i];
+            const df g = gw(i);
             const long long o = (long long)wr * wo + a;
-            s0 += g * P[o];
-            s1 += g * P[wins + o];
-            s2 += g * P[2 * wins + o];
+            s0 = df_sub_mul(s0, g, df_of(P[o]));
+            s1 = df_sub_mul(s1, g, df_of(P[wins + o]));
+            s2 = df_sub_mul(s2, g, df_of(P[2 * wins + o]));
         }
-        V[idx] = s0;
-        V[vplane + idx] = s1;
-        V[2 * vplane + idx] = s2;
+        V[idx] = make_float2(s0.hi, s0.lo);
+        V[vplane + idx] = make_float2(s1.hi, s1.lo);
+        V[2 * vplane + idx] = make_float2(s2.hi, s2.lo);
     }
 }
 
 // Back through the horizontal pass and the products:
 // grad_y[r][c] = G1 + 2 y G2 + x G3 with G_k[r][c] = sum_j g[j] V[k][r][c - j].
-__global__ void ssim_hback_kernel(const double *V, const float *x, const float *y, int h, int w, long long pitch,
+__global__ void ssim_hback_kernel(const float2 *V, const float *x, const float *y, int h, int w, long long pitch,
                                   float *grad) {
     const int wo = w - 10;
     const long long vplane = (long long)h * wo, npix = (long long)h * w;
     for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < npix;
          idx += (long long)gridDim.x * blockDim.x) {
         const int r = (int)(idx / w), c = (int)(idx - (long long)r * w);
-        double g1 = 0, g2 = 0, g3 = 0;
+        df g1{0.0f, 0.0f}, g2 = g1, g3 = g1;
+#pragma unroll
         for (int j = 0; j < 11; ++j) {
             const int a = c - j;
             if (a < 0 || a >= wo) continue;
-            const double g = c_gauss[j];
+            const df g = gw(j);
             const long long o = (long long)r * wo + a;
-            g1 += g * V[o];
-            g2 += g * V[vplane + o];
-            g3 += g * V[2 * vplane + o];
+            const float2 v1 = V[o], v2 = V[vplane + o], v3 = V[2 * vplane + o];
+            g1 = df_sub_mul(g1, g, df{v1.x, v1.y});
+            g2 = df_sub_mul(g2, g, df{v2.x, v2.y});
+            g3 = df_sub_mul(g3, g, df{v3.x, v3.y});
         }
-        const double xv = x[(long long)r * pitch + c], yv = y[(long long)r * pitch + c];
-        grad[(long long)r * pitch + c] = (float)(g1 + 2.0 * yv * g2 + xv * g3);
+        const float xv = x[(long long)r * pitch + c], yv = y[(long long)r * pitch + c];
+        // g1 + 2 y g2 + x g3
+        df t = df_sub_mul(g1, df{-2.0f * yv, 0.0f}, g2);
+        t = df_sub_mul(t, df{-xv, 0.0f}, g3);
+        grad[(long long)r * pitch + c] = __fadd_rn(t.hi, t.lo);
     }
 }
 
@@ -204,7 +241,14 @@ cudaError_t upload_gauss11(cudaStream_t st) {
         s += g[i];
     }
     for (int i = 0; i < 11; ++i) g[i] /= s;
-    return cudaMemcpyToSymbolAsync(c_gauss, g, sizeof g, 0, cudaMemcpyHostToDevice, st);
+    float2 gf[11];
+    for (int i = 0; i < 11; ++i) {
+        gf[i].x = (float)g[i];
+        gf[i].y = (float)(g[i] - (double)gf[i].x);
+    }
+    cudaError_t e = cudaMemcpyToSymbolAsync(c_gauss, g, sizeof g, 0, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyToSymbolAsync(c_gauss_df, gf, sizeof gf, 0, cudaMemcpyHostToDevice, st);
 }
 
 cudaError_t launch_synth_forward(const LeafRec *leaves, unsigned long long n_leaves, const AtomRec *atoms,
@@ -238,16 +282,17 @@ cudaError_t launch_synth_backward(const LeafRec *leaves, unsigned long long n_le
 cudaError_t launch_ssim(const float *x, const float *y, int h, int w, long long pitch, double *H, double *P,
                         double *V, double *sum, float *grad, double gscale, int num_sms, cudaStream_t st) {
     const unsigned grid = (unsigned)num_sms * 8;
-    ssim_hpass_kernel<<<grid, 256, 0, st>>>(x, y, h, w, pitch, H);
+    float2 *Hf = reinterpret_cast<float2 *>(H), *Vf = reinterpret_cast<float2 *>(V);   // (hi, lo) in 8-byte slots
+    ssim_hpass_kernel<<<grid, 256, 0, st>>>(x, y, h, w, pitch, Hf);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const long long wins = (long long)(h - 10) * (w - 10);
     const double scale = grad ? gscale / (double)wins : 0.0;
-    ssim_window_kernel<<<grid, 256, 0, st>>>(H, h, w, grad ? P : nullptr, sum, scale);
+    ssim_window_kernel<<<grid, 256, 0, st>>>(Hf, h, w, grad ? P : nullptr, sum, scale);
     if ((e = cudaGetLastError()) != cudaSuccess || !grad) return e;
-    ssim_vback_kernel<<<grid, 256, 0, st>>>(P, h, w, V);
+    ssim_vback_kernel<<<grid, 256, 0, st>>>(P, h, w, Vf);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    ssim_hback_kernel<<<grid, 256, 0, st>>>(V, x, y, h, w, pitch, grad);
+    ssim_hback_kernel<<<grid, 256, 0, st>>>(Vf, x, y, h, w, pitch, grad);
     return cudaGetLastError();
 }
 

@@ -22,28 +22,33 @@ class SynthesisSSIM(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, alpha, code, refs):
-        recons, vals = [], []
+        # When alpha needs a gradient, the SSIM kernels return d SSIM / d y
+        # in the same pass (the window statistics are computed once); the
+        # backward only scales it and runs the synthesis adjoint.
+        want = ctx.needs_input_grad[0]
+        grads, vals = [], []
         for plane, ref in refs:
             out = torch.empty_like(ref)
             aqmp.aqmp_synth_forward(code, plane, alpha, out)
             s = torch.zeros((), dtype=torch.float64, device=ref.device)
-            aqmp.aqmp_ssim(ref, out, s)
-            recons.append(out)
+            if want:
+                gy = torch.empty_like(out)
+                aqmp.aqmp_ssim(ref, out, s, gy, 1.0)
+                grads.append(gy)
+            else:
+                aqmp.aqmp_ssim(ref, out, s)
             vals.append(s)
-        ctx.code, ctx.refs, ctx.recons = code, refs, recons
+        ctx.code, ctx.refs, ctx.grads = code, refs, grads
         ctx.n_alpha = alpha.shape[0]
         return torch.stack(vals).mean()
 
     @staticmethod
     def backward(ctx, grad):
-        g = float(grad)
         grad_alpha = torch.zeros(ctx.n_alpha, dtype=torch.float32, device=grad.device)
-        for (plane, ref), out in zip(ctx.refs, ctx.recons):
-            gy = torch.empty_like(out)
-            s = torch.zeros((), dtype=torch.float64, device=ref.device)
-            aqmp.aqmp_ssim(ref, out, s, gy, g / len(ctx.refs))
+        for (plane, _), gy in zip(ctx.refs, ctx.grads):
             aqmp.aqmp_synth_backward(ctx.code, plane, gy, grad_alpha)
-        return grad_alpha, None, None
+        # the mean over planes and the upstream gradient, on the device
+        return grad_alpha * (grad / len(ctx.refs)).to(torch.float32), None, None
 
 
 def synthesis_ssim(alpha, code, refs):
