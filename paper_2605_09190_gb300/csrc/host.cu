@@ -233,6 +233,12 @@ std::string kname(const char *k, int b) { return std::string(k) + "_b" + std::to
 // recomputing the correlation is harmless; K2: alternately over encodes),
 // and the one with the lowest timing is kept.  The lowest of two timings
 // discards a kernel's first, cold launch.
+// Sides from which the correlation is not autotuned: at side 128 the
+// integer SIMT kernel takes about 6x the tensor-core time (245 against
+// 38 ms for 3072 leaves), so timing it would only add a second to the first
+// encode.
+constexpr int kCorrTunedMax = 128;
+
 struct Tuner {
     enum Kind { CORR = 0, MP = 1 };
     static constexpr int kSamples = 2;
@@ -692,7 +698,8 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
         if (!tune) return true;
         for (int l = 0; l < nlev; ++l) {
             const int b = P.max_block >> l;
-            if (!simt && !bf16 && c->tuner.slot(Tuner::CORR, b, P.dict_id, P.precision, cap[l]).chosen < 0)
+            if (!simt && !bf16 && b < kCorrTunedMax &&
+                c->tuner.slot(Tuner::CORR, b, P.dict_id, P.precision, cap[l]).chosen < 0)
                 return false;
             if (!alt_threads && !omp && mp_has_variant(b, dicts[l]->d.nf) &&
                 c->tuner.slot(Tuner::MP, b, P.dict_id, P.precision, cap[l]).chosen < 0)
@@ -764,7 +771,7 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
             CK(g_prof.run(kname("corr_bf16", b), st, [&] { return launch_corr_tc_bf16(ca, st); }));
         } else if (simt) {
             CK(corr_simt());
-        } else if (!tune) {
+        } else if (!tune || b >= kCorrTunedMax) {
             CK(corr_tc());
         } else {
             Tuner::Slot &ts = c->tuner.slot(Tuner::CORR, b, P.dict_id, P.precision, cap[l]);
