@@ -18,16 +18,16 @@
 // rank r), and each thread loads its row entry from the owning peer through
 // distributed shared memory.
 //
-// Each step every CTA reduces its own top-2 summary (the same summaries,
-// window rule and certification as the single-CTA kernel), the summaries
-// are exchanged through distributed shared memory -- a 16-byte slot per CTA
-// in every peer, written remotely, with an mbarrier per slot that each peer
-// arrives on remotely -- and every CTA merges the same values into the same
-// choice.  The energy, the stop test and the choice then run identically on
-// every CTA, so the cluster stays in lock step with no further exchange.  A
-// step chosen from the other family updates all of a CTA's elements through
-// W (the rank-1 Gram column); a step of its own family zeroes one element of
-// one CTA.  Rank 0 records the steps and emits or splits the leaf.
+// Each step every warp reduces its own top-2 summary (the same summaries,
+// window rule and certification as the single-CTA kernel) and stores it into
+// every CTA of the cluster through distributed shared memory -- a 16-byte
+// slot per warp and CTA, written by st.async, which completes its bytes on
+// the receiving CTA's mbarrier -- so after one wait every CTA merges the same
+// values into the same choice.  The energy, the stop test and the choice then
+// run identically on every CTA, and the cluster stays in lock step with no
+// further exchange.  Each step updates the other family's elements on every
+// CTA and zeroes the chosen element on its owner.  Rank 0 records the steps
+// and emits or splits the leaf.
 //
 // Every exchange wait is bounded: on expiry the CTA records AQMP_E_TIMEOUT,
 // stays resident for a grace period (so that peers, which poll the error
