@@ -95,6 +95,8 @@ mp_kernel(MPArgs a) {
     StepRec *sSteps = reinterpret_cast<StepRec *>(sRj + NW);
 
     const LevelArgs &lv = a.lv;
+    __shared__ unsigned long long sCnt[3];              // per-CTA work counters (T == 32)
+    if (T == 32 && threadIdx.x < 3) sCnt[threadIdx.x] = 0ull;
     if (NF == 2) {
         for (int i = threadIdx.x; i < B * B; i += blockDim.x) {
             sW[i] = a.W[i];
@@ -470,7 +472,22 @@ mp_kernel(MPArgs a) {
         }
         if (T > 32) __syncthreads(); else __syncwarp();
     }
-    if (lane == 0 && n_attempts) {
+    if (T == 32) {
+        // one warp per leaf: the CTA's groups add their counters in shared
+        // memory first, so the exit costs three global atomics per CTA, not
+        // per warp (thousands of warps finish together at the small sides)
+        if (lane == 0 && n_attempts) {
+            atomicAdd(&sCnt[0], n_attempts);
+            atomicAdd(&sCnt[1], n_steps);
+            atomicAdd(&sCnt[2], n_windows);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && sCnt[0]) {
+            atomicAdd(&a.ctr->attempts[lv.level], sCnt[0]);
+            atomicAdd(&a.ctr->iterations[lv.level], sCnt[1]);
+            if (sCnt[2]) atomicAdd(&a.ctr->window_steps[lv.level], sCnt[2]);
+        }
+    } else if (lane == 0 && n_attempts) {
         atomicAdd(&a.ctr->attempts[lv.level], n_attempts);
         atomicAdd(&a.ctr->iterations[lv.level], n_steps);
         if (n_windows) atomicAdd(&a.ctr->window_steps[lv.level], n_windows);
