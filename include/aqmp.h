@@ -229,7 +229,8 @@ int aqmp_synth_backward(const aqmp_code *code, int plane, const float *grad_out,
 /* Mean SSIM (Section 3; K1 = 0.01, K2 = 0.03, L = 255, 11x11 Gaussian
  * window of sigma 1.5, valid region) of `y` against the reference `x`, both
  * h x w FP32 images with `pitch` elements per row, h, w >= 11.  Window
- * statistics are accumulated in FP64.  *ssim (device, FP64) receives the
+ * sums are accumulated in double-float (~2^-46 relative), the per-window
+ * formula in FP64.  *ssim (device, FP64) receives the
  * mean; with grad_y != NULL, grad_y (h x w, pitch) receives
  * grad_scale * d(mean SSIM)/dy. */
 int aqmp_ssim(const float *x, const float *y, int h, int w, int64_t pitch, double *ssim,
