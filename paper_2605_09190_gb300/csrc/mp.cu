@@ -524,6 +524,264 @@ static cudaError_t launch_mp_t(const MPArgs &a, int num_sms, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Rank-1 update of the other family's b^2 elements, starting at element O,
+// of a thread that holds a whole leaf: element (p', q') takes u[p'] W[q*][q'].
+template <int B, int M, int O, bool DF>
+__device__ __forceinline__ void update_other(float (&ch)[M], float (&cl)[M], const df (&u)[B], const float2 *Wq) {
+#pragma unroll
+    for (int f = 0; f < B * B; ++f) {
+        const float2 w = Wq[f / B];
+        if (DF) {
+            const df r = df_sub_mul(df{ch[O + f], cl[O + f]}, u[f % B], df{w.x, w.y});
+            ch[O + f] = r.hi;
+            cl[O + f] = r.lo;
+        } else {
+            ch[O + f] = __fmaf_rn(-u[f % B].hi, w.x, ch[O + f]);
+        }
+    }
+}
+
+// Side 4, one thread per leaf: a side-4 leaf has only 2 b^2 = 32 correlations,
+// which fit one thread's registers, so the thread runs the whole pursuit
+// with no shuffle, reduction or shared-memory exchange, and each warp runs
+// 32 leaves side by side.  The arithmetic per element and the decision rules
+// (top-2 summary, window, full-precision decision, certification band,
+// energy test) are those of mp_kernel, element for element, so the two give
+// the same result bit for bit.  Emission is aggregated per warp (one atomic
+// for the warp's leaf slots, one for its atoms, one for its split children)
+// and the work counters per CTA.
+template <int NF, bool DF>
+__global__ void __launch_bounds__(128) mp_thread_kernel(MPArgs a) {
+    constexpr int B = 4, n = B * B, M = NF * n;
+    __shared__ float2 sW[2 * B * B];                     // W then W^T
+    __shared__ unsigned long long sCnt[3];
+    extern __shared__ __align__(16) unsigned char smem[];
+    StepRec *steps = reinterpret_cast<StepRec *>(smem) + (size_t)threadIdx.x * a.lv.k;
+
+    const LevelArgs &lv = a.lv;
+    if (NF == 2)
+        for (int i = threadIdx.x; i < 2 * B * B; i += blockDim.x) sW[i] = i < B * B ? a.W[i] : a.WT[i - B * B];
+    if (threadIdx.x < 3) sCnt[threadIdx.x] = 0ull;
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31;
+    const unsigned count = *lv.count;
+    const int k = lv.k;
+    const unsigned stride = gridDim.x * blockDim.x;
+    unsigned long long n_attempts = 0, n_steps = 0, n_windows = 0;
+
+    for (unsigned base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < count; base += stride) {
+        const unsigned leaf = base + (unsigned)lane;
+        const bool active = leaf < count;
+        int t = 0;
+        bool conv = false, tie = false;
+        QueueEntry qe{0u, 0u, 0u, 0u};
+        if (active) {
+            qe = lv.queue[leaf];
+            const float tol = a.planes[qe.plane].tol;
+            const df eps2 = df_scale(df_two_prod(tol, tol), (float)n);
+            const uint32_t e0 = a.e0[leaf];
+            df En = df_from_i64((long long)e0);
+            const df thrE = df_sub(eps2, df_scale(df_from_i64((long long)e0), 0x1p-32f));
+            const float bandE_f = ldexpf((float)e0, -37);
+            const float eps2_f = __fmul_rn(__fmul_rn(tol, tol), (float)n);
+            const float S_f = sqrtf((float)e0);
+            const float pre = ldexpf(S_f, -32) * 1.05f + ldexpf(S_f, -37) * 1.05f;
+
+            float ch[M], cl[M];
+            const float2 *cp = a.c0 + (size_t)leaf * M;
+#pragma unroll
+            for (int j = 0; j < M; ++j) {
+                const float2 v = cp[j];
+                ch[j] = v.x;
+                cl[j] = DF ? v.y : 0.0f;
+            }
+            int windows = 0;
+            for (;;) {
+                // (a6) accuracy test before every step, strict
+                const bool below = DF ? df_lt(En, thrE) : (En.hi < eps2_f);
+                if (DF && fabsf(En.hi - thrE.hi) <= bandE_f * 1.01f + 0x1p-20f * fabsf(thrE.hi)) {
+                    if (fabs(df_to_double(En) - df_to_double(thrE)) < ldexp((double)e0, -37)) tie = true;
+                }
+                if (below) { conv = true; break; }
+                if (t == k) break;
+
+                // (a3) argmax: the top-2 summary of all elements
+                Top2 best = top2_empty();
+#pragma unroll
+                for (int j = 0; j < M; ++j) top2_fold(best, ch[j], cl[j], (uint32_t)j);
+                if ((best.P >> 32) == 0ull) break;   // every correlation is exactly zero
+                uint32_t j1 = top2_index(best);
+                const float amax = top2_amax(best);
+                df alpha = df{top2_negative(best) ? -amax : amax, best.lo1};
+                const float window = amax * 0x1p-20f + pre;
+                if (DF && __uint_as_float(best.k2) >= amax - window) {
+                    ++windows;
+                    const double tieC = ldexp((double)S_f, -32);
+                    const double bandC = ldexp((double)S_f, -37);
+                    unsigned long long mk = 0ull;
+#pragma unroll
+                    for (int j = 0; j < M; ++j) {
+                        if (fabsf(ch[j]) >= amax - window) {
+                            const double m = fabs((double)ch[j] + (double)cl[j]);
+                            const unsigned long long key = (unsigned long long)__double_as_longlong(m);
+                            if (key > mk) mk = key;
+                        }
+                    }
+                    const double edge = __longlong_as_double((long long)mk) - tieC;
+                    uint32_t lower = kNone;
+                    float wh = 0.0f, wl = 0.0f;
+#pragma unroll
+                    for (int j = 0; j < M; ++j) {
+                        if (fabsf(ch[j]) >= amax - window) {
+                            const double m = fabs((double)ch[j] + (double)cl[j]);
+                            if (fabs(m - edge) < bandC) tie = true;
+                            if (m >= edge && (uint32_t)j < lower) {
+                                lower = (uint32_t)j;
+                                wh = ch[j];
+                                wl = cl[j];
+                            }
+                        }
+                    }
+                    j1 = lower;
+                    alpha = df{wh, wl};
+                }
+                steps[t] = StepRec{j1, alpha.hi, alpha.lo};
+
+                // (a5) energy
+                if (DF) En = df_sub(En, df_mul(alpha, alpha));
+                else En = df{__fmaf_rn(-alpha.hi, alpha.hi, En.hi), 0.0f};
+
+                // (a4) the other family through W, the chosen element zeroed
+                if (NF == 2) {
+                    const int fam1 = (int)(j1 >= (uint32_t)n);
+                    const int f1 = (int)j1 - fam1 * n;
+                    const int p1 = f1 % B, q1 = f1 / B;
+                    const float2 *V = sW + fam1 * B * B;
+                    df u[B];
+#pragma unroll
+                    for (int p = 0; p < B; ++p) {
+                        const float2 vp = V[p1 * B + p];
+                        u[p] = DF ? df_mul(alpha, df{vp.x, vp.y}) : df{__fmul_rn(alpha.hi, vp.x), 0.0f};
+                    }
+                    // element (p', q') of the other family takes u[p'] W[q1][q']
+                    if (fam1) update_other<B, M, 0, DF>(ch, cl, u, V + q1 * B);
+                    else update_other<B, M, n, DF>(ch, cl, u, V + q1 * B);
+                }
+#pragma unroll
+                for (int j = 0; j < M; ++j)
+                    if ((uint32_t)j == j1) { ch[j] = 0.0f; cl[j] = 0.0f; }
+                ++t;
+            }
+            n_attempts += 1;
+            n_steps += (unsigned long long)t;
+            n_windows += (unsigned long long)windows;
+        }
+
+        // (a7) emission and splits, aggregated over the warp
+        const bool emit = active && (conv || lv.is_last);
+        const bool split = active && !emit;
+        const unsigned below_mask = (1u << lane) - 1u;
+        const unsigned emask = __ballot_sync(0xffffffffu, emit), smask = __ballot_sync(0xffffffffu, split);
+        unsigned toff = emit ? (unsigned)t : 0u;               // exclusive prefix of the emitted steps
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned v = __shfl_up_sync(0xffffffffu, toff, off);
+            if (lane >= off) toff += v;
+        }
+        const unsigned total_t = __shfl_sync(0xffffffffu, toff, 31);
+        toff -= emit ? (unsigned)t : 0u;
+        unsigned long long slot0 = 0ull, off0 = 0ull;
+        unsigned q0 = 0u;
+        bool ok = true;
+        if (lane == 0) {
+            if (emask) {
+                slot0 = atomicAdd(&a.ctr->n_leaves, (unsigned long long)__popc(emask));
+                off0 = atomicAdd(&a.ctr->n_atoms, (unsigned long long)total_t);
+                if (slot0 + __popc(emask) > a.leaf_cap || off0 + total_t > a.atom_cap) {
+                    raise_error(a.ctr, kDevErrQueueOverflow, 1u);
+                    ok = false;
+                }
+            }
+            if (smask) {
+                q0 = atomicAdd(lv.next_count, 4u * (unsigned)__popc(smask));
+                if (q0 + 4u * (unsigned)__popc(smask) > lv.next_capacity) raise_error(a.ctr, kDevErrQueueOverflow, 2u);
+            }
+        }
+        slot0 = __shfl_sync(0xffffffffu, slot0, 0);
+        off0 = __shfl_sync(0xffffffffu, off0, 0);
+        q0 = __shfl_sync(0xffffffffu, q0, 0);
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (emit && ok) {
+            const unsigned long long slot = slot0 + (unsigned long long)__popc(emask & below_mask);
+            const unsigned long long o = off0 + toff;
+            const uint8_t flags = (uint8_t)((tie ? 1u : 0u) | (qe.flags & 2u));
+            LeafRec rec;
+            rec.plane = qe.plane;
+            rec.y = qe.y;
+            rec.x = qe.x;
+            rec.atom_off = (uint32_t)o;
+            rec.b = (uint16_t)B;
+            rec.n_atoms = (uint16_t)t;
+            rec.converged = conv ? 1 : 0;
+            rec.flags = flags;
+            rec.reserved = 0;
+            a.leaves[slot] = rec;
+            const unsigned long long cell = cell_of(a.cells, a.planes[qe.plane], qe.y, qe.x);
+            if (cell != ~0ull) a.cells.cell[cell] = (uint32_t)slot + 1u;
+            if (flags) atomicAdd(&a.ctr->near_tie_leaves, 1ull);
+            for (int i = 0; i < t; ++i) {
+                const StepRec st = steps[i];
+                a.atoms[o + i] = AtomRec{st.j, st.hi};
+                a.alpha_lo[o + i] = st.lo;
+                a.atom_leaf[o + i] = (uint32_t)slot;
+            }
+        }
+        if (split) {
+            const unsigned qs = q0 + 4u * (unsigned)__popc(smask & below_mask);
+            if (qs + 4u <= lv.next_capacity) {
+                const uint32_t h = B / 2;
+                const uint32_t fl = (qe.flags & 2u) | (tie ? 2u : 0u);
+                lv.next_queue[qs + 0] = QueueEntry{qe.plane, qe.y, qe.x, fl};
+                lv.next_queue[qs + 1] = QueueEntry{qe.plane, qe.y, qe.x + h, fl};
+                lv.next_queue[qs + 2] = QueueEntry{qe.plane, qe.y + h, qe.x, fl};
+                lv.next_queue[qs + 3] = QueueEntry{qe.plane, qe.y + h, qe.x + h, fl};
+            }
+        }
+    }
+    // work counters: per CTA in shared memory, then three global atomics
+    if (n_attempts) {
+        atomicAdd(&sCnt[0], n_attempts);
+        atomicAdd(&sCnt[1], n_steps);
+        atomicAdd(&sCnt[2], n_windows);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && sCnt[0]) {
+        atomicAdd(&a.ctr->attempts[lv.level], sCnt[0]);
+        atomicAdd(&a.ctr->iterations[lv.level], sCnt[1]);
+        if (sCnt[2]) atomicAdd(&a.ctr->window_steps[lv.level], sCnt[2]);
+    }
+}
+
+template <int NF, bool DF>
+static cudaError_t launch_mp_thread_t(const MPArgs &a, int num_sms, cudaStream_t st) {
+    constexpr int block = 128;
+    const size_t smem = (size_t)block * a.lv.k * sizeof(StepRec);
+    auto kern = mp_thread_kernel<NF, DF>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    long long need = ((long long)a.lv.capacity + block - 1) / block;
+    long long grid = (long long)num_sms * per_sm;
+    if (need < grid) grid = need;
+    if (grid < 1) grid = 1;
+    kern<<<(unsigned)grid, block, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
 // Threads per leaf for the two largest sides (compile-time knobs; the other
 // sides use one warp per leaf).
 #ifndef AQMP_MP_T32
@@ -545,6 +803,8 @@ static cudaError_t launch_mp_t(const MPArgs &a, int num_sms, cudaStream_t st) {
 template <bool DF>
 static cudaError_t launch_mp_prec(const MPArgs &a, int nf, int variant, int num_sms, cudaStream_t st) {
     const int b = a.lv.b;
+    if (b == 4 && a.lv.is_last)            // every side-4 leaf is emitted: one thread per leaf
+        return nf == 2 ? launch_mp_thread_t<2, DF>(a, num_sms, st) : launch_mp_thread_t<1, DF>(a, num_sms, st);
     if (nf == 2) {
         switch (b) {
             case 4: return launch_mp_t<4, 32, 2, DF>(a, num_sms, st);
