@@ -541,6 +541,12 @@ __device__ __forceinline__ void update_other(float (&ch)[M], float (&cl)[M], con
     }
 }
 
+// Whether the energy lies within 2^-37 ||y||^2 of the threshold in FP64; out
+// of line, so that its FP64 work runs only when the FP32 pre-test asks.
+__device__ __noinline__ bool energy_in_band(df En, df thrE, uint32_t e0) {
+    return fabs(df_to_double(En) - df_to_double(thrE)) < ldexp((double)e0, -37);
+}
+
 // Side 4, one thread per leaf: a side-4 leaf has only 2 b^2 = 32 correlations,
 // which fit one thread's registers, so the thread runs the whole pursuit
 // with no shuffle, reduction or shared-memory exchange, and each warp runs
@@ -601,7 +607,7 @@ __global__ void __launch_bounds__(128) mp_thread_kernel(MPArgs a) {
                 // (a6) accuracy test before every step, strict
                 const bool below = DF ? df_lt(En, thrE) : (En.hi < eps2_f);
                 if (DF && fabsf(En.hi - thrE.hi) <= bandE_f * 1.01f + 0x1p-20f * fabsf(thrE.hi)) {
-                    if (fabs(df_to_double(En) - df_to_double(thrE)) < ldexp((double)e0, -37)) tie = true;
+                    if (energy_in_band(En, thrE, e0)) tie = true;
                 }
                 if (below) { conv = true; break; }
                 if (t == k) break;
@@ -615,7 +621,22 @@ __global__ void __launch_bounds__(128) mp_thread_kernel(MPArgs a) {
                 const float amax = top2_amax(best);
                 df alpha = df{top2_negative(best) ? -amax : amax, best.lo1};
                 const float window = amax * 0x1p-20f + pre;
+                uint32_t cand = 0u;                       // atoms in the window, by FP32 test
                 if (DF && __uint_as_float(best.k2) >= amax - window) {
+#pragma unroll
+                    for (int j = 0; j < M; ++j)
+                        if (fabsf(ch[j]) >= amax - window) cand |= 1u << j;
+                }
+                if (DF && NF == 2 && cand == (1u | (1u << n)) && __float_as_uint(ch[0]) == __float_as_uint(ch[n]) &&
+                    __float_as_uint(cl[0]) == __float_as_uint(cl[n])) {
+                    // the DCT DC atom and the identical Haar scaling atom, alone
+                    // in the window with the same value: the full-precision rule
+                    // below picks index 0 and flags nothing (the two are exactly
+                    // tied, 2^5 tie bands from the certification band)
+                    ++windows;
+                    j1 = 0u;
+                    alpha = df{ch[0], cl[0]};
+                } else if (cand) {
                     ++windows;
                     const double tieC = ldexp((double)S_f, -32);
                     const double bandC = ldexp((double)S_f, -37);
