@@ -1,19 +1,24 @@
 """Benchmark of the AQMP encoder hot path on GB300.
 
-Workload (one "step"): the 512x512 8-bit piecewise-planar synthetic scene
-(20 step edges, a 128x128 band-limited texture patch, Gaussian noise sigma 3),
-encoded at the four RMSE tolerances {1, 2, 4, 8} in one batched call (four
-planes, each with its own tolerance), quadtree 64 -> 4, budget k = b^2 / 4,
-dictionary DCT-II + Haar (M = 2 b^2), exact arithmetic.  The metric is
-encoder megapixels/s: the pixels of all planes encoded per second of
+Default workload (one "step" = one encode call): 64 synthetic RGB images of
+uneven sizes, width U{256..2048} x height U{256..1536} in multiples of 64,
+channel c of image i the gradient scene (linear gradient, two step edges of
+height 60, a disk, Gaussian noise sigma 2) of seed 3 i + c, encoded per
+channel as 192 planes in one call at RMSE tolerance 2, quadtree 64 -> 4,
+budget k = b^2 / 4, dictionary DCT-II + Haar (M = 2 b^2), exact arithmetic.
+The metric is encoder megapixels/s: the channel pixels encoded per second of
 encode time, inputs already in device memory.  ``e2e`` repeats it through the
 same public call with pinned host inputs and a host copy of every result
 inside the timed region.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload uneven64|uneven64-piecewise|sweep512|precision4096|omp512|refine16]
 
-Under torchrun every rank encodes its own copy of the workload (independent
-problems: weak scaling); rank 0 prints one JSON line.
+Under torchrun the batch is the first 64 N images of the same seeded stream
+(weak scaling: 64 images per rank), split into contiguous ranges of (plane,
+root row) balanced by pixels; every rank encodes its range with no exchange,
+and the leaf and atom records are gathered at the end of each end-to-end
+step.  Rank 0 prints one JSON line.
 """
 from __future__ import annotations
 
@@ -31,29 +36,356 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-TOLS = [1.0, 2.0, 4.0, 8.0]
-H = W = 512
-MAX_BLOCK, MIN_BLOCK = 64, 4
-SEED = 1
 METRIC = "encoder megapixels/s"
-WORKLOAD = ("piecewise-planar synthetic 512x512 gray, RMSE tol sweep {1,2,4,8} batched as 4 planes, "
-            "quadtree 64->4, k=b^2/4, DCT-II+Haar dictionary (M=2b^2)")
+MAX_BLOCK, MIN_BLOCK = 64, 4
+L2_BYTES = 129 << 20
 L2_FLUSH_BYTES = 256 << 20
+IMAGES_PER_RANK = 64
+SWEEP_TOLS = [1.0, 2.0, 4.0, 8.0]
+NUM_SMS = 152
+FP32_LANES = 128                     # FP32 FMA lanes per SM
+MAX_SM_MHZ = 2070.0
 
-# FP32 operations of one double-float Gram-entry update c <- c - u w
-# (exact product 2, cross terms 2, TwoSum 6, low-word sum 2, renormalise 3)
-DF_UPDATE_OPS = 15
+WORKLOADS = {
+    "uneven64": ("64 synthetic RGB images (gradient scene per channel: linear gradient, two step edges of height 60, "
+                 "a disk, Gaussian noise sigma 2; seed 3i+c), width U{256..2048} x height U{256..1536} in multiples "
+                 "of 64, encoded per channel as 192 planes in one call, RMSE tol 2, quadtree 64->4, k=b^2/4, "
+                 "DCT-II+Haar (M=2b^2)"),
+    "uneven64-piecewise": ("the same 64 uneven RGB images with the 512x512 workload's piecewise scene per channel "
+                           "(Voronoi planes, 20 edges, texture patch, noise sigma 3), 192 planes in one call, RMSE "
+                           "tol 2, quadtree 64->4, k=b^2/4, DCT-II+Haar"),
+    "sweep512": ("piecewise-planar synthetic 512x512 gray, RMSE tol sweep {1,2,4,8} batched as 4 planes, "
+                 "quadtree 64->4, k=b^2/4, DCT-II+Haar dictionary (M=2b^2)"),
+}
 
 
-def workload_planes():
+# ------------------------------------------------------------- workloads
+
+def workload_planes(name: str, rank: int = 0, world: int = 1):
+    """This rank's planes (2-D uint8 numpy arrays), their tolerances, the
+    pieces of the global workload they are (see ``shard.partition``) and the
+    global plane shapes."""
+    from paper_2605_09190_gb300 import shard, synthetic
+    if name == "sweep512":
+        img = synthetic.piecewise_scene(512, 512, seed=1)
+        return [img] * len(SWEEP_TOLS), list(SWEEP_TOLS), None, None
+    scene = synthetic.gradient_scene if name == "uneven64" else synthetic.piecewise_scene
+    n_img = IMAGES_PER_RANK * world
+    sizes = synthetic.uneven_sizes(n_img, seed=0)
+    shapes = [hw for hw in sizes for _ in range(3)]
+    pieces = shard.partition(shapes, MAX_BLOCK, world)[rank]
+    need = sorted({p // 3 for p, _, _ in pieces})
+    imgs = {}
+    for i in need:                              # only the images this rank's pieces touch
+        (h, w, chans), = synthetic.uneven_rgb_batch(n_img, seed=0, scene=scene, first=i, count=1)
+        imgs[i] = chans
+    full = {p: imgs[p // 3][p % 3] for p, _, _ in pieces}
+    planes = [full[p][r0 * MAX_BLOCK:(r0 + n) * MAX_BLOCK] for p, r0, n in pieces]
+    return planes, [2.0] * len(planes), pieces, shapes
+
+
+def sample_roots(planes, count: int, seed: int):
+    """`count` (plane, root index) pairs drawn without replacement, seeded."""
+    rng = np.random.default_rng(seed)
+    per = [(p.shape[0] // MAX_BLOCK) * (p.shape[1] // MAX_BLOCK) for p in planes]
+    flat = rng.choice(sum(per), size=min(count, sum(per)), replace=False)
+    out, base = {}, np.cumsum([0] + per)
+    for f in sorted(int(x) for x in flat):
+        p = int(np.searchsorted(base, f, side="right") - 1)
+        out.setdefault(p, []).append(f - int(base[p]))
+    return out
+
+
+# ------------------------------------------------------------- distributed
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def dist_init(backend: str) -> int:
+    """Join the process group when launched by torchrun; returns the world size."""
+    _, world, _ = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        if not dist.is_initialized():
+            dist.init_process_group(backend)
+    return world
+
+
+def max_over_ranks(x: float, device=None) -> float:
+    """Largest value of `x` over all ranks (identity when not distributed).
+    Only timings and the final gather of records cross ranks: the encoder's
+    data path has no collective."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, device=None) -> float:
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def weak_scaling_value(pixels_per_rank: int, steps: int, max_seconds: float, world: int) -> float:
+    """Whole-job megapixels/s when every rank encodes `pixels_per_rank`
+    pixels per step: the pixels of all ranks over the slowest rank's time."""
+    return world * pixels_per_rank * steps / 1e6 / max_seconds
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- roofline
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+def profiled_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
+    None when the kernel's sources changed since that capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        entry = json.load(f).get(kernel)
+    if not entry:
+        return None
+    h = hashlib.sha256()
+    for src in entry["sources"]:
+        with open(os.path.join(ROOT, "paper_2605_09190_gb300", "csrc", src), "rb") as f:
+            h.update(f.read())
+    return entry["dram_bytes_per_launch"] if h.hexdigest() == entry["sources_sha256"] else None
+
+
+def fp32_peak_tflops(mhz: float = MAX_SM_MHZ) -> float:
+    """FP32 FMA peak in flops (an FMA counts 2): 152 SMs x 128 lanes x 2 x clock."""
+    return NUM_SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12
+
+
+def level_of(b: int, max_block: int) -> int:
+    return int(np.log2(max_block // b))
+
+
+def roofline(name, launches, total_ms, stats_sum, peaks, peak_kind, sm_mhz, max_block, step_floor_ns=None):
+    """Roofline entry of one kernel, from its live event-timed launches and
+    the algorithmic work of SURVEY-style counting:
+
+    * pursuit (``mp*``): 6 n flops per atom-iteration (2M for a dense Gram
+      column, 2n for the residual) against the FP32 FMA peak in flops; the
+      latency view adds the level's longest pursuit (its serial chain of
+      steps) against the launch time;
+    * correlation (``corr*``): the GEMM's 4 n^2 flops per leaf for the dense
+      kernels and 8 b^3 (two b x b x b products per family, both families)
+      for the separable ones, against the BF16 dense tensor peak;
+    * gather: n bytes in, 2 Kpad + 4 bytes out per leaf, against HBM."""
+    kind, b = name.rsplit("_b", 1)
+    b = int(b)
+    lvl = level_of(b, max_block)
+    n = b * b
+    M = 2 * n
+    per_launch_s = total_ms / 1e3 / max(1, launches)
+    attempts = stats_sum["attempts_per_level"][lvl] / max(1, launches)
+    iters = stats_sum["iterations_per_level"][lvl] / max(1, launches)
+    r = {"kernel": name, "launch_ms": per_launch_s * 1e3}
+    if kind.startswith("mp"):
+        flops = 6.0 * n * iters
+        peak = fp32_peak_tflops()
+        ach = flops / per_launch_s / 1e12
+        exact = not kind.startswith("mp_fp32")
+        r.update({"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                  "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (max SM clock)",
+                  "work": "6n flops per atom-iteration (SURVEY 8d dense-Gram count), n = b^2",
+                  "atom_iterations_per_launch": iters,
+                  "issued_fp32_ops_per_alg_flop": (15.0 * n if exact else 1.0 * n) / (6.0 * n),
+                  "issued_note": ("the library updates only the other family's n correlations per step "
+                                  "(structured Gram), each a double-float multiply-subtract of 15 FP32 ops"
+                                  if exact else "one FP32 FMA per updated correlation (n per step)")})
+        if sm_mhz:
+            r["frac_at_sampled_clock"] = ach / fp32_peak_tflops(sm_mhz)
+        chain = stats_sum.get("max_leaf_steps_per_level", [0] * 8)[lvl]
+        if chain:
+            lat = {"longest_pursuit_steps": chain, "ns_per_step_of_longest": per_launch_s * 1e9 / chain}
+            if step_floor_ns:
+                lat["step_floor_ns"] = step_floor_ns
+                lat["chain_frac"] = chain * step_floor_ns / (per_launch_s * 1e9)
+            r["latency"] = lat
+    elif kind.startswith("corr"):
+        sep = kind.startswith("corr_sep")
+        flops = (8.0 * b ** 3 if sep else 4.0 * n * n) * attempts
+        peak = peaks.get("bf16_tflops", 1900.0)
+        ach = flops / per_launch_s / 1e12
+        kpad = max(64, (n + 63) // 64 * 64)
+        alg_bytes = (0 if sep else 2.0 * M * n) + attempts * (2.0 * kpad + 8.0 * M)
+        r.update({"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                  "peak_source": f"bf16_tflops ({peak_kind})",
+                  "work": ("8 b^3 flops per leaf (B Y B^T for both families)" if sep
+                           else "4 n^2 flops per leaf (dense D^T y for M = 2n atoms)"),
+                  "leaves_per_launch": attempts, "algorithmic_bytes": alg_bytes})
+    else:
+        kpad = max(64, (n + 63) // 64 * 64)
+        byts = attempts * (n + 2 * kpad + 4)
+        peak = peaks.get("hbm_gbs", 6800.0)
+        ach = byts / per_launch_s / 1e9
+        r.update({"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                  "peak_source": f"hbm_gbs ({peak_kind})", "algorithmic_bytes": byts})
+    r["traffic"] = profiled_traffic(name)
+    if r["traffic"] and r.get("algorithmic_bytes"):
+        r["traffic_ratio"] = r["traffic"] / r["algorithmic_bytes"]
+    return r
+
+
+def critical_path(stats_sum):
+    """Sum over the levels of the longest pursuit: the encode's serial chain
+    of MP steps (a level's launches wait for the level before)."""
+    return int(sum(stats_sum.get("max_leaf_steps_per_level", [])))
+
+
+# ------------------------------------------------------------- GPU helpers
+
+KERNEL_PASSES = 3
+
+
+def kernel_breakdown(aqmp, encode, flush):
+    """Untimed pass with every kernel bracketed by CUDA events (their
+    records lengthen the step, so the timed steps bracket only the dominant
+    kernel): per-kernel totals over KERNEL_PASSES calls, the dominant kernel
+    and the launches per call."""
+    aqmp.aqmp_profile_filter(None)
+    aqmp.aqmp_profile_reset()
+    aqmp.aqmp_profile_enable(True)
+    for _ in range(KERNEL_PASSES):
+        flush()
+        encode().free()
+    aqmp.aqmp_profile_enable(False)
+    prof = aqmp.aqmp_profile_read()
+    top = max(prof.items(), key=lambda kv: kv[1][1])[0]
+    per_call = sum(v[0] for v in prof.values()) / KERNEL_PASSES
+    return {k: (v[0] / KERNEL_PASSES, v[1] / KERNEL_PASSES) for k, v in prof.items()}, top, per_call
+
+
+def autotune_choices(aqmp):
+    """The autotuner's settled choices, by kernel and side."""
+    return {f'{e["kind"]}_b{e["side"]}': (("tcgen05", "simt") if e["kind"] == "corr"
+                                          else ("default", "alternate"))[e["chosen"]]
+            for e in aqmp.aqmp_autotune_read() if e["chosen"] >= 0}
+
+
+def settle_autotuner(aqmp, encode, most=8):
+    """Set-up, untimed: the library's autotuner measures its kernel
+    candidates on the first calls of a configuration (the pursuit's over four
+    calls); run the encode until every choice point met has been decided."""
+    for _ in range(most):
+        encode().free()
+        if all(e["chosen"] >= 0 for e in aqmp.aqmp_autotune_read()):
+            return
+
+
+def pursuit_step_floor_ns(aqmp, torch, b: int):
+    """Per-step time of one pursuit alone on the GPU: one noise block of side
+    b at tolerance 0 runs its whole budget k = b^2/4 with nothing else
+    resident; the kernel's event time over k (untimed set-up)."""
     from paper_2605_09190_gb300 import synthetic
-    img = synthetic.piecewise_scene(H, W, seed=SEED)
-    return [img] * len(TOLS)
+    plane = torch.from_numpy(synthetic.noise_plane(b, b, seed=11)).cuda()
+    enc = lambda: aqmp.aqmp_encode_planes([plane], 0.0, min_block=b, max_block=b)  # noqa: E731
+    settle_autotuner(aqmp, enc)
+    aqmp.aqmp_profile_filter(f"mp_b{b}")
+    aqmp.aqmp_profile_reset()
+    aqmp.aqmp_profile_enable(True)
+    steps = 0
+    for _ in range(3):
+        c = enc()
+        steps += c.stats()["atom_iterations"]
+        c.free()
+    aqmp.aqmp_profile_enable(False)
+    prof = aqmp.aqmp_profile_read()
+    aqmp.aqmp_profile_filter(None)
+    key = f"mp_b{b}"
+    return prof[key][1] * 1e6 / steps if key in prof and steps else None
 
 
-UNEVEN_WORKLOAD = ("64 synthetic RGB images (piecewise scenes of the 512x512 workload, a seed per channel), width U{256..2048} x "
-                   "height U{256..1536} in multiples of 64, encoded per channel as 192 planes in one call, "
-                   "RMSE tol 2, quadtree 64->4, k=b^2/4, DCT-II+Haar")
+def add_stats(acc, st):
+    if acc is None:
+        return {k: (list(v) if isinstance(v, list) else v) for k, v in st.items()}
+    for k, v in st.items():
+        if k.startswith("max_"):
+            acc[k] = [max(a, b) for a, b in zip(acc[k], v)]
+        elif isinstance(v, list):
+            acc[k] = [a + b for a, b in zip(acc[k], v)]
+        else:
+            acc[k] += v
+    return acc
 
 
 REFINE_WORKLOAD = ("16 synthetic 512x512 gray images (piecewise scenes, seeds 0..15), MP support fixed at RMSE "
@@ -106,98 +438,247 @@ def run_refine(args):
     return 0
 
 
-KERNEL_PASSES = 3
 
 
-def kernel_breakdown(aqmp, encode, flush):
-    """Untimed pass with every kernel bracketed by CUDA events (their
-    records lengthen the step, so the timed steps bracket only the dominant
-    kernel): per-kernel totals over KERNEL_PASSES calls, the dominant kernel
-    and the launches per call."""
-    aqmp.aqmp_profile_filter(None)
-    aqmp.aqmp_profile_reset()
-    aqmp.aqmp_profile_enable(True)
-    for _ in range(KERNEL_PASSES):
-        flush()
-        encode().free()
-    aqmp.aqmp_profile_enable(False)
-    prof = aqmp.aqmp_profile_read()
-    top = max(prof.items(), key=lambda kv: kv[1][1])[0]
-    per_call = sum(v[0] for v in prof.values()) / KERNEL_PASSES
-    return {k: (v[0] / KERNEL_PASSES, v[1] / KERNEL_PASSES) for k, v in prof.items()}, top, per_call
+# --------------------------------------------------------------- CPU side
+
+def oracle_sample(planes, tols, roots, threads: int):
+    """Time the FP64 oracle on the root blocks `roots` ({plane: [root]}) of
+    `planes`; returns (MP/s, seconds, pixels)."""
+    import oracle
+    oracle.dictionary(MAX_BLOCK, 0)                       # tables built outside the timing
+    idx = sorted(roots)
+    sub = [planes[p] for p in idx]
+    t0 = time.perf_counter()
+    oracle.encode(sub, [tols[p] for p in idx], min_block=MIN_BLOCK, max_block=MAX_BLOCK,
+                  roots=[roots[p] for p in idx], threads=threads)
+    dt = time.perf_counter() - t0
+    px = sum(len(v) for v in roots.values()) * MAX_BLOCK * MAX_BLOCK
+    return px / 1e6 / dt, dt, px
 
 
-def autotune_choices(aqmp):
-    """The autotuner's settled choices, by kernel and side."""
-    return {f'{e["kind"]}_b{e["side"]}': (("tcgen05", "simt") if e["kind"] == "corr"
-                                          else ("default", "alternate"))[e["chosen"]]
-            for e in aqmp.aqmp_autotune_read() if e["chosen"] >= 0}
+def cpu_baseline(name, planes, tols, budget_s: float = 15.0):
+    """The oracle, as it stands, on the host cores: batches of `cores` seeded
+    root blocks until about `budget_s` seconds of CPU work; per-pixel
+    throughput of the sample."""
+    threads = os.cpu_count() or 1
+    total_px, total_s, batches = 0, 0.0, 0
+    while total_s < budget_s and batches < 64:
+        roots = sample_roots(planes, threads, seed=1000 + batches)
+        _, dt, px = oracle_sample(planes, tols, roots, threads)
+        total_px += px
+        total_s += dt
+        batches += 1
+    return {"value": total_px / 1e6 / total_s, "unit": "MP/s", "cores": threads, "kind": "oracle",
+            "sample": f"{total_px // (MAX_BLOCK * MAX_BLOCK)} seeded root blocks (64x64) of the {name} workload "
+                      f"in {batches} batches of {threads} (one per core), {total_s:.1f} s wall; MP/s = sampled "
+                      f"pixels / time"}
 
 
-def settle_autotuner(aqmp, encode, most=8):
-    """Set-up, untimed: the library's autotuner measures its kernel
-    candidates on the first calls of a configuration (the pursuit's over four
-    calls); run the encode until every choice point met has been decided."""
-    for _ in range(most):
-        encode().free()
-        if all(e["chosen"] >= 0 for e in aqmp.aqmp_autotune_read()):
-            return
+def run_reference(args):
+    """The reference arm: the FP64 oracle (there is no reference code: the
+    reference is a paper) on the host cores, each step a bounded seeded
+    sample of the workload's root blocks, on rank 0 only."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    name = args.workload if args.workload in WORKLOADS else "uneven64"
+    planes, tols, _, _ = workload_planes(name, 0, 1)
+    threads = os.cpu_count() or 1
+    times, px = [], 0
+    for i in range(args.warmup + args.steps):
+        roots = sample_roots(planes, threads, seed=i)
+        _, dt, p = oracle_sample(planes, tols, roots, threads)
+        if i >= args.warmup:
+            times.append(dt)
+            px += p
+    total = sum(times)
+    value = px / 1e6 / total
+    sample = f"per step: {threads} seeded root blocks (64x64) of the workload, one per host core"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "MP/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOADS[name], "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "MP/s", "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "MP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
 
 
-def run_uneven(args):
-    """The 64-image uneven batch: one step encodes all 192 planes at once."""
+# --------------------------------------------------------------- GPU side
+
+def run_ours(args):
+    """Encode throughput of one of the WORKLOADS (see the module docstring)."""
     import torch
-    from paper_2605_09190_gb300 import aqmp, build_lib, synthetic
+    from paper_2605_09190_gb300 import aqmp, build_lib, shard
+
+    name = args.workload
     rank, world, local = dist_env()
     torch.cuda.set_device(local if world > 1 else 0)
     dist_init("nccl")
+    gloo = None
+    if world > 1:
+        import torch.distributed as dist
+        gloo = dist.new_group(backend="gloo")          # host-side gather of the records
     build_lib.build()
-    batch = synthetic.uneven_rgb_batch(64, seed=rank)
-    planes = [torch.from_numpy(p).cuda() for (_, _, chans) in batch for p in chans]
-    npix = sum(int(p.numel()) for p in planes)
+    aqmp.load_library()
+    planes, tols, pieces, _ = workload_planes(name, rank, world)
+    dev = [torch.from_numpy(np.ascontiguousarray(p)).cuda() for p in planes]
+    npix = int(sum(p.size for p in planes))
+    total_px = int(sum_over_ranks(npix, device="cuda"))
+    small = npix < 2 * L2_BYTES
+    flush_buf = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda") if small else None
+    flush = (lambda: flush_buf.zero_()) if small else (lambda: None)  # noqa: E731
     stream = torch.cuda.current_stream()
-    encode = lambda: aqmp.aqmp_encode_planes(planes, 2.0, min_block=MIN_BLOCK, max_block=MAX_BLOCK)  # noqa: E731
+    kw = dict(min_block=MIN_BLOCK, max_block=MAX_BLOCK)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+            torch.cuda.synchronize()
+
+    def timed_form(precision, steps, warmup, record=None):
+        encode = lambda: aqmp.aqmp_encode_planes(dev, tols, precision=precision, **kw)  # noqa: E731
+        settle_autotuner(aqmp, encode)
+        for _ in range(warmup):
+            flush()
+            encode().free()
+        barrier()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        stops = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        stats = None
+        for i in range(steps):
+            flush()
+            starts[i].record(stream)
+            code = encode()
+            stops[i].record(stream)
+            stats = add_stats(stats, code.stats())
+            code.free()
+        barrier()
+        ms = [a.elapsed_time(b) for a, b in zip(starts, stops)]
+        return max_over_ranks(sum(ms) / 1e3, device="cuda"), stats
+
+    encode = lambda: aqmp.aqmp_encode_planes(dev, tols, **kw)  # noqa: E731
     settle_autotuner(aqmp, encode)
-    breakdown, top, launches_per_step = kernel_breakdown(aqmp, encode, lambda: None)
+    breakdown, top, launches_per_step = kernel_breakdown(aqmp, encode, flush)
+    step_floor = None
+    if top.startswith("mp_b"):
+        step_floor = pursuit_step_floor_ns(aqmp, torch, int(top.rsplit("_b", 1)[1]))
+    # warm-up in the timed configuration: only the dominant kernel bracketed
     aqmp.aqmp_profile_filter(top)
     aqmp.aqmp_profile_enable(True)
     for _ in range(args.warmup):
+        flush()
         encode().free()
     aqmp.aqmp_profile_reset()
-    ms, iters = [], 0
-    torch.cuda.synchronize()
     with ClockSampler(local) as clocks:
-        for _ in range(args.steps):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            code = aqmp.aqmp_encode_planes(planes, 2.0, min_block=MIN_BLOCK, max_block=MAX_BLOCK)
-            e1.record(stream)
-            iters += code.stats()["atom_iterations"]
-            code.free()
-            torch.cuda.synchronize()
-            ms.append(e0.elapsed_time(e1))
+        total_s, stats_sum = timed_form(aqmp.AQMP_PREC_EXACT, args.steps, 0)
     aqmp.aqmp_profile_enable(False)
-    prof = aqmp.aqmp_profile_read()
+    profile = aqmp.aqmp_profile_read()
     aqmp.aqmp_profile_filter(None)
-    total_s = max_over_ranks(sum(ms) / 1e3, device="cuda")
+    value = total_px * args.steps / 1e6 / total_s
+    iters_per_s = sum_over_ranks(stats_sum["atom_iterations"], device="cuda") / total_s
+
+    # the other forms on the same workload, same timing rules
+    forms = {"exact (bf16-limb tensor GEMM + f32x2 certified pursuit)": value}
+    form_stats = {}
+    for label, prec in (("fp32 (same GEMM rounded to fp32 + fp32 pursuit, not certified)", aqmp.AQMP_PREC_FP32),
+                        ("bf16 (one bf16 tensor pass + fp32 pursuit, not certified)", aqmp.AQMP_PREC_BF16)):
+        s, st = timed_form(prec, args.steps, args.warmup)
+        forms[label] = total_px * args.steps / 1e6 / s
+        form_stats[label] = {"leaves_per_step": st["n_leaves"] / args.steps,
+                             "atoms_per_step": st["n_atoms"] / args.steps}
+
+    per_tol = None
+    if name == "sweep512":
+        per_tol = {}
+        for t in SWEEP_TOLS:
+            one = [dev[SWEEP_TOLS.index(t)]]
+            enc1 = lambda: aqmp.aqmp_encode_planes(one, t, **kw)  # noqa: E731
+            settle_autotuner(aqmp, enc1)
+            ms = []
+            for _ in range(args.warmup + args.steps):
+                flush()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                c = enc1()
+                e1.record(stream)
+                c.free()
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            per_tol[str(t)] = one[0].numel() * args.steps / 1e6 / (sum(ms[args.warmup:]) / 1e3)
+
+    # end to end: pinned host input -> encode -> host copy of the result
+    # (-> gather of every rank's records when sharded)
+    host = [torch.from_numpy(np.ascontiguousarray(p)).pin_memory() for p in planes]
+    e2e_times, d2h = [], 0
+    barrier()
+    for i in range(args.steps):
+        flush()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        code = aqmp.aqmp_encode_planes(host, tols, **kw)
+        leaves, atoms, lo = code.copy()
+        if world > 1:
+            leaves = shard.globalize(leaves, pieces, MAX_BLOCK)
+            leaves, atoms, lo = shard.gather(leaves, atoms, lo, group=gloo)
+        e2e_times.append(time.perf_counter() - t0)
+        d2h = leaves.nbytes + atoms.nbytes + lo.nbytes
+        code.free()
+    e2e_s = max_over_ranks(sum(e2e_times), device="cuda")
+    e2e = {"value": total_px * args.steps / 1e6 / e2e_s, "unit": "MP/s",
+           "h2d_bytes_per_step": int(npix), "d2h_bytes_per_step": int(d2h)}
+
+    clk = clocks.summary()
+    peaks, peak_kind = load_peaks()
+    roof = None
+    if top in profile:
+        roof = roofline(top, profile[top][0], profile[top][1], stats_sum, peaks, peak_kind, clk.get("sm_mhz"),
+                        MAX_BLOCK, step_floor)
+    tot = max(1e-12, sum(x[1] for x in breakdown.values()))
+    kernels = {k: {"launches": v[0], "ms": round(v[1], 4), "share": round(v[1] / tot, 4)}
+               for k, v in sorted(breakdown.items(), key=lambda kv: -kv[1][1])}
+    # the roofline of every kernel with more than 5% of the step (from the profiled pass)
+    others = {}
+    for k, v in breakdown.items():
+        if v[1] / tot > 0.05 and k != top:
+            st1 = {kk: ([x / args.steps for x in vv] if isinstance(vv, list) and not kk.startswith("max_")
+                        else vv) for kk, vv in stats_sum.items()}
+            rr = roofline(k, v[0], v[1], st1, peaks, peak_kind, clk.get("sm_mhz"), MAX_BLOCK)
+            others[k] = {kk: rr[kk] for kk in ("bound", "achieved", "peak", "unit", "frac", "launch_ms")}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(name, planes, tols)
+
     if rank == 0:
-        tot = sum(v[1] for v in breakdown.values())
-        print(json.dumps({"metric": METRIC, "value": weak_scaling_value(npix, args.steps, total_s, world),
-                          "unit": "MP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-                          "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
-                          "scaling": "weak", "vs_baseline": None, "dtype": "bf16-limb tensor GEMM + f32x2 pursuit",
-                          "data": "synthetic",
-                          "config": {"workload": UNEVEN_WORKLOAD, "planes_per_step": len(planes),
-                                     "pixels_per_step": npix, "input": "device-resident",
-                                     "l2": "inputs (198 M px) and working set exceed L2"},
-                          "atom_iterations_per_s": world * iters / total_s,
-                          "kernels": {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / tot, 4)}
-                                      for k, v in sorted(breakdown.items(), key=lambda kv: -kv[1][1])},
-                          "timed_kernel": {top: {"launches": prof[top][0], "ms": round(prof[top][1], 3)}}
-                          if top in prof else None,
-                          "autotune": autotune_choices(aqmp),
-                          "gpu_launches": int(round(launches_per_step * args.steps)),
-                          "clocks": clocks.summary()}))
+        line = {"metric": METRIC, "value": value, "unit": "MP/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "bf16-limb tensor GEMM + f32x2 pursuit",
+                "data": "synthetic",
+                "config": {"workload": WORKLOADS[name], "name": name, "planes_per_rank": len(planes),
+                           "pixels_per_step": total_px, "input": "device-resident",
+                           "l2": ("flushed between steps (256 MB write)" if small
+                                  else f"inputs ({npix / 1e6:.0f} MB per rank) exceed L2 (129 MB)"),
+                           "parallelism": (f"sharded x{world}: contiguous (plane, root row) ranges of a "
+                                           f"{IMAGES_PER_RANK * world}-image batch, records gathered at the end"
+                                           if pieces is not None and world > 1 else
+                                           ("single GPU" if world == 1 else f"independent replicas x{world}"))},
+                "atom_iterations_per_s": iters_per_s,
+                "atom_iterations_per_step": stats_sum["atom_iterations"] / args.steps,
+                "leaves_per_step": stats_sum["n_leaves"] / args.steps,
+                "critical_path_steps": critical_path(stats_sum),
+                "near_tie_leaves": stats_sum["near_tie_leaves"],
+                "window_step_fraction": sum(stats_sum["window_steps_per_level"]) / max(1, stats_sum["atom_iterations"]),
+                "autotune": autotune_choices(aqmp), "forms": forms, "form_stats": form_stats,
+                "per_tolerance_mps": per_tol,
+                "roofline": roof, "roofline_other_kernels": others, "kernels": kernels,
+                "gpu_launches": int(round(launches_per_step * args.steps)),
+                "e2e": e2e, "clocks": clk, "cpu_baseline": cpu}
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
     return 0
 
 
@@ -214,13 +695,13 @@ def run_omp(args):
     torch.cuda.set_device(local if world > 1 else 0)
     dist_init("nccl")
     build_lib.build()
-    dev = [torch.from_numpy(p).cuda() for p in workload_planes()]
+    dev = [torch.from_numpy(p).cuda() for p in workload_planes("sweep512")[0]]
     npix = sum(int(p.numel()) for p in dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
     def timed(omp):
-        encode = lambda: aqmp.aqmp_encode_planes(dev, TOLS, min_block=MIN_BLOCK, max_block=16, omp=omp)  # noqa: E731
+        encode = lambda: aqmp.aqmp_encode_planes(dev, SWEEP_TOLS, min_block=MIN_BLOCK, max_block=16, omp=omp)  # noqa: E731
         settle_autotuner(aqmp, encode)
         breakdown, top, per_call = kernel_breakdown(aqmp, encode, lambda: flush.zero_())
         for _ in range(args.warmup):
@@ -369,345 +850,6 @@ def run_precision(args):
     return 0
 
 
-def dist_env():
-    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
-        int(os.environ.get("LOCAL_RANK", "0"))
-
-
-def dist_init(backend: str) -> int:
-    """Join the process group when launched by torchrun; returns the world size."""
-    _, world, _ = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-        if not dist.is_initialized():
-            dist.init_process_group(backend)
-    return world
-
-
-def max_over_ranks(x: float, device=None) -> float:
-    """Largest value of `x` over all ranks (identity when not distributed).
-    Only timings cross ranks: the encoder's data path has no collective."""
-    import torch
-    import torch.distributed as dist
-    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
-        return float(x)
-    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
-
-
-def weak_scaling_value(pixels_per_rank: int, steps: int, max_seconds: float, world: int) -> float:
-    """Whole-job megapixels/s: every rank encodes its own copy of the
-    workload, so the pixels of all ranks over the slowest rank's time."""
-    return world * pixels_per_rank * steps / 1e6 / max_seconds
-
-
-# ------------------------------------------------------------------ clocks
-
-class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons while running."""
-
-    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
-
-    def __init__(self, index: int):
-        self.index = index
-        self.proc = None
-        self.lines = []
-
-    def __enter__(self):
-        try:
-            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
-                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.thread = threading.Thread(target=self._read, daemon=True)
-            self.thread.start()
-        except OSError:
-            self.proc = None
-        return self
-
-    def _read(self):
-        for line in self.proc.stdout:
-            self.lines.append(line.strip())
-
-    def __exit__(self, *exc):
-        if self.proc:
-            self.proc.terminate()
-            try:
-                self.proc.wait(timeout=5)
-            except subprocess.TimeoutExpired:
-                self.proc.kill()
-        return False
-
-    def summary(self):
-        sm, mx, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            f = [x.strip() for x in ln.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                mx = float(f[2])
-            except ValueError:
-                continue
-            for name, val in zip(names, f[5:9]):
-                if val.lower().startswith("active"):
-                    reasons.add(name)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
-                "reasons": sorted(reasons), "samples": len(sm)}
-
-
-# ---------------------------------------------------------------- roofline
-
-def load_peaks():
-    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(p):
-        with open(p) as f:
-            d = json.load(f)
-        return d, "measured"
-    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
-            "sm_max_mhz": 2070.0}, "fallback"
-
-
-def profiled_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
-    None when the kernel's sources changed since that capture."""
-    import hashlib
-    path = os.path.join(ROOT, "profiles", "traffic.json")
-    if not os.path.exists(path):
-        return None
-    with open(path) as f:
-        entry = json.load(f).get(kernel)
-    if not entry:
-        return None
-    h = hashlib.sha256()
-    for src in entry["sources"]:
-        with open(os.path.join(ROOT, "paper_2605_09190_gb300", "csrc", src), "rb") as f:
-            h.update(f.read())
-    return entry["dram_bytes_per_launch"] if h.hexdigest() == entry["sources_sha256"] else None
-
-
-def roofline(profile, stats_sum, steps, peaks, peak_kind, sm_mhz):
-    """Roofline entry of the kernel with the largest share of device time."""
-    if not profile:
-        return None, None
-    name, (launches, total_ms) = max(profile.items(), key=lambda kv: kv[1][1])
-    b = int(name.rsplit("_b", 1)[1])
-    kind = name.rsplit("_b", 1)[0]
-    lvl = int(np.log2(MAX_BLOCK // b))
-    n = b * b
-    M = 2 * n
-    per_launch_s = total_ms / 1e3 / max(1, launches)
-    if kind == "mp":
-        iters = stats_sum["iterations_per_level"][lvl] / max(1, launches)
-        ops = iters * n * DF_UPDATE_OPS                      # cross-family Gram update
-        clock = 2070.0                                       # FP32 lanes x max SM clock
-        peak = 152 * 128 * clock * 1e6 / 1e12                # T FP32 ops/s
-        ach = ops / per_launch_s / 1e12
-        r = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP32-ops/s", "frac": ach / peak,
-             "traffic": None, "kernel": name, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz"}
-    elif kind.startswith("corr"):
-        leaves = stats_sum["attempts_per_level"][lvl] / max(1, launches)
-        flops = 2.0 * M * n * leaves
-        peak = peaks.get("bf16_tflops", 1900.0)
-        ach = flops / per_launch_s / 1e12
-        r = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-             "traffic": None, "kernel": name, "peak_source": f"bf16_tflops ({peak_kind})"}
-    else:
-        leaves = stats_sum["attempts_per_level"][lvl] / max(1, launches)
-        byts = leaves * (n + 2 * ((n + 63) // 64 * 64) + 4)
-        peak = peaks.get("hbm_gbs", 6800.0)
-        ach = byts / per_launch_s / 1e9
-        r = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-             "traffic": None, "kernel": name, "peak_source": f"hbm_gbs ({peak_kind})"}
-    r["launch_ms"] = per_launch_s * 1e3
-    r["traffic"] = profiled_traffic(name)
-    return r, name
-
-
-# --------------------------------------------------------------- CPU side
-
-def oracle_sample(roots_per_tol: int, tols, threads: int):
-    """Time the FP64 oracle on `roots_per_tol` root blocks of each plane."""
-    import oracle
-    planes = workload_planes()[:len(tols)]
-    nroots = (H // MAX_BLOCK) * (W // MAX_BLOCK)
-    pick = [int(round(i * (nroots - 1) / max(1, roots_per_tol - 1))) for i in range(roots_per_tol)]
-    oracle.dictionary(MAX_BLOCK, 0)                       # build tables outside the timing
-    t0 = time.perf_counter()
-    enc = oracle.encode(planes, tols, min_block=MIN_BLOCK, max_block=MAX_BLOCK, roots=[pick] * len(tols),
-                        threads=threads)
-    dt = time.perf_counter() - t0
-    px = len(tols) * len(pick) * MAX_BLOCK * MAX_BLOCK
-    return px / 1e6 / dt, dt, pick, enc
-
-
-def run_reference(args):
-    rank, world, _ = dist_env()
-    if rank != 0:
-        return 0
-    threads = os.cpu_count() or 1
-    per_step_roots = threads
-    times, px = [], 0
-    order = [8.0, 4.0, 2.0, 1.0]
-    for i in range(args.warmup + args.steps):
-        tol = order[i % 4]
-        mps, dt, pick, _ = oracle_sample(per_step_roots, [tol], threads)
-        if i >= args.warmup:
-            times.append(dt)
-            px += len(pick) * MAX_BLOCK * MAX_BLOCK
-    total = sum(times)
-    value = px / 1e6 / total
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "MP/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / max(1, args.steps),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": f"per step: {per_step_roots} of the 64 root blocks "
-                                                      f"at one tolerance, cycling 8,4,2,1"},
-            "cpu_baseline": {"value": value, "unit": "MP/s", "cores": threads, "kind": "oracle",
-                             "sample": f"{per_step_roots} root blocks (64x64) per step, one tolerance per step"},
-            "e2e": {"value": value, "unit": "MP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line))
-    return 0
-
-
-# --------------------------------------------------------------- GPU side
-
-def run_ours(args):
-    import torch
-    from paper_2605_09190_gb300 import aqmp, build_lib
-
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local if world > 1 else 0)
-    dist_init("nccl")
-    build_lib.build()
-    lib = aqmp.load_library()  # noqa: F841
-    planes = workload_planes()
-    dev = [torch.from_numpy(p).cuda() for p in planes]
-    npix = sum(p.size for p in planes)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    stream = torch.cuda.current_stream()
-
-    def barrier():
-        torch.cuda.synchronize()
-        if world > 1:
-            torch.distributed.barrier()
-            torch.cuda.synchronize()
-
-    encode = lambda: aqmp.aqmp_encode_planes(dev, TOLS, min_block=MIN_BLOCK, max_block=MAX_BLOCK)  # noqa: E731
-    settle_autotuner(aqmp, encode)
-    breakdown, top, launches_per_step = kernel_breakdown(aqmp, encode, lambda: flush.zero_())
-    # warm-up in the timed configuration: only the dominant kernel bracketed
-    aqmp.aqmp_profile_filter(top)
-    aqmp.aqmp_profile_enable(True)
-    for _ in range(args.warmup):
-        flush.zero_()
-        encode().free()
-
-    # timed: device-resident input, L2 flushed between steps (outside the events)
-    aqmp.aqmp_profile_reset()
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    stops = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    stats_sum = None
-    barrier()
-    with ClockSampler(local) as clocks:
-        for i in range(args.steps):
-            flush.zero_()
-            starts[i].record(stream)
-            code = aqmp.aqmp_encode_planes(dev, TOLS, min_block=MIN_BLOCK, max_block=MAX_BLOCK)
-            stops[i].record(stream)
-            st = code.stats()
-            code.free()
-            if stats_sum is None:
-                stats_sum = {k: (list(v) if isinstance(v, list) else v) for k, v in st.items()}
-            else:
-                for k, v in st.items():
-                    if isinstance(v, list):
-                        stats_sum[k] = [a + b for a, b in zip(stats_sum[k], v)]
-                    else:
-                        stats_sum[k] += v
-        barrier()
-    aqmp.aqmp_profile_enable(False)
-    profile = aqmp.aqmp_profile_read()
-    aqmp.aqmp_profile_filter(None)
-    step_ms = [a.elapsed_time(b) for a, b in zip(starts, stops)]
-    total_s = max_over_ranks(sum(step_ms) / 1e3, device="cuda")
-    value = weak_scaling_value(npix, args.steps, total_s, world)
-    iters_per_s = world * stats_sum["atom_iterations"] / total_s
-
-    # the plain FP32 form on the same workload, for comparison (same timing rules)
-    fp32_ms = []
-    barrier()
-    for i in range(args.warmup + args.steps):
-        flush.zero_()
-        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        s0.record(stream)
-        code = aqmp.aqmp_encode_planes(dev, TOLS, min_block=MIN_BLOCK, max_block=MAX_BLOCK,
-                                       precision=aqmp.AQMP_PREC_FP32)
-        s1.record(stream)
-        code.free()
-        torch.cuda.synchronize()
-        if i >= args.warmup:
-            fp32_ms.append(s0.elapsed_time(s1))
-    fp32_value = weak_scaling_value(npix, args.steps, max_over_ranks(sum(fp32_ms) / 1e3, device="cuda"), world)
-
-    # end to end: pinned host input -> encode -> host copy of the result
-    host = [torch.from_numpy(p).pin_memory() for p in planes]
-    e2e_times, d2h = [], 0
-    barrier()
-    for i in range(args.steps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        code = aqmp.aqmp_encode_planes(host, TOLS, min_block=MIN_BLOCK, max_block=MAX_BLOCK)
-        leaves, atoms, lo = code.copy()
-        e2e_times.append(time.perf_counter() - t0)
-        d2h = leaves.nbytes + atoms.nbytes + lo.nbytes
-        code.free()
-    e2e_s = max_over_ranks(sum(e2e_times), device="cuda")
-    e2e = {"value": weak_scaling_value(npix, args.steps, e2e_s, world), "unit": "MP/s",
-           "h2d_bytes_per_step": int(npix), "d2h_bytes_per_step": int(d2h)}
-
-    clk = clocks.summary()
-    peaks, peak_kind = load_peaks()
-    roof, _ = roofline(profile, stats_sum, args.steps, peaks, peak_kind, clk.get("sm_mhz"))
-    launches = int(round(launches_per_step * args.steps))
-    kernels = {k: {"launches": v[0], "ms": round(v[1], 4),
-                   "share": round(v[1] / max(1e-12, sum(x[1] for x in breakdown.values())), 4)}
-               for k, v in sorted(breakdown.items(), key=lambda kv: -kv[1][1])}
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        threads = os.cpu_count() or 1
-        roots = max(1, min(8, threads // 2))
-        mps, dt, pick, _ = oracle_sample(roots, TOLS, threads)
-        cpu = {"value": mps, "unit": "MP/s", "cores": min(threads, roots * len(TOLS)), "kind": "oracle",
-               "sample": f"root blocks {pick} (64x64) of each of the 4 tolerance planes, {dt:.1f} s wall"}
-
-    if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": "MP/s", "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "bf16-limb tensor GEMM + f32x2 pursuit",
-                "data": "synthetic",
-                "config": {"workload": WORKLOAD, "planes_per_step": len(planes), "pixels_per_step": int(npix),
-                           "input": "device-resident", "l2": "flushed between steps (256 MB write)",
-                           "parallelism": f"independent replicas x{world}"},
-                "atom_iterations_per_s": iters_per_s,
-                "atom_iterations_per_step": stats_sum["atom_iterations"] / args.steps,
-                "leaves_per_step": stats_sum["n_leaves"] / args.steps,
-                "near_tie_leaves": stats_sum["near_tie_leaves"],
-                "window_step_fraction": sum(stats_sum["window_steps_per_level"]) / max(1, stats_sum["atom_iterations"]),
-                "autotune": autotune_choices(aqmp),
-                "forms": {"exact (bf16-limb tensor GEMM + f32x2 certified pursuit)": value,
-                          "fp32 (same GEMM rounded to fp32 + fp32 pursuit, not certified)": fp32_value},
-                "roofline": roof, "kernels": kernels, "gpu_launches": launches,
-                "e2e": e2e, "clocks": clk, "cpu_baseline": cpu}
-        print(json.dumps(line))
-    if world > 1:
-        torch.distributed.destroy_process_group()
-    return 0
 
 
 def main():
@@ -717,19 +859,18 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["sweep512", "uneven64", "refine16", "omp512", "precision4096"],
-                    default="sweep512",
-                    help="sweep512: the 512x512 tolerance sweep (default); uneven64: 64 uneven RGB images; "
-                         "refine16: coefficient refinement on 16 images (steps = Adam steps); "
-                         "omp512: the sweep's planes with 16x16 roots, Orthogonal Matching Pursuit; "
-                         "precision4096: one 4096x4096 RGB image, exact vs plain FP32 form")
+    ap.add_argument("--workload", choices=list(WORKLOADS) + ["refine16", "omp512", "precision4096"],
+                    default="uneven64",
+                    help="uneven64: 64 uneven RGB gradient images (default); uneven64-piecewise: the same sizes "
+                         "with piecewise content; sweep512: the 512x512 tolerance sweep; refine16: coefficient "
+                         "refinement on 16 images (steps = Adam steps); omp512: the sweep's planes with 16x16 "
+                         "roots, Orthogonal Matching Pursuit; precision4096: one 4096x4096 RGB image, the "
+                         "exact form against the FP32 and BF16 forms")
     ap.add_argument("--root", type=int, default=0,
                     help="precision4096 only: root block side (default 128; 64 for comparison)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload == "uneven64":
-        return run_uneven(args)
     if args.workload == "refine16":
         return run_refine(args)
     if args.workload == "omp512":

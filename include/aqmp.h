@@ -158,6 +158,9 @@ typedef struct {
     uint64_t window_steps_per_level[8];   /* steps decided in full precision because
                                            * another atom lay within the decision
                                            * window of the largest (exact form) */
+    uint64_t max_leaf_steps_per_level[8]; /* steps of the level's longest pursuit: the
+                                           * level's serial chain (its launch cannot
+                                           * end before that pursuit does) */
 } aqmp_stats;
 
 typedef struct aqmp_code aqmp_code;   /* opaque, library-owned result */
@@ -292,8 +295,11 @@ void aqmp_autotune_reset(void);   /* forget every choice (they are measured agai
  * library holds until exit (about 10 MB).  Limits: b in {4, 8, 16} and at
  * most 65536 blocks (b = 4, 8) or 16384 blocks (b = 16) per call; larger
  * requests return AQMP_E_ARG.  The first call on a device looks up the
- * arrays' device addresses and should come before any stream capture.
- * Calls share the arrays and synchronise `stream` before returning; GPU work
+ * arrays' device addresses and should come before any stream capture.  A
+ * call cannot be captured into a CUDA graph (it waits for `stream` and reads
+ * a status word back): on a capturing stream it returns AQMP_E_UNSUPPORTED
+ * and leaves the stream untouched.  Calls share the arrays and synchronise
+ * `stream` before returning, on an error too once work was queued; GPU work
  * of two calls must not overlap (this function serialises its callers). */
 int aqmp_correlate_noalloc(int b, int dict_id, const uint8_t *blocks, int64_t L, float *corr,
                            void *stream);

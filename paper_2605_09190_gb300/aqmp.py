@@ -56,7 +56,7 @@ class aqmp_stats(ctypes.Structure):
     _fields_ = [("n_leaves", ctypes.c_uint64), ("n_atoms", ctypes.c_uint64), ("attempts", ctypes.c_uint64),
                 ("atom_iterations", ctypes.c_uint64), ("near_tie_leaves", ctypes.c_uint64),
                 ("attempts_per_level", ctypes.c_uint64 * 8), ("iterations_per_level", ctypes.c_uint64 * 8),
-                ("window_steps_per_level", ctypes.c_uint64 * 8)]
+                ("window_steps_per_level", ctypes.c_uint64 * 8), ("max_leaf_steps_per_level", ctypes.c_uint64 * 8)]
 
 
 LEAF_DTYPE = np.dtype([("plane", np.uint32), ("y", np.uint32), ("x", np.uint32), ("atom_off", np.uint32),
@@ -275,7 +275,8 @@ def aqmp_code_stats(code: Code) -> dict:
             "atom_iterations": s.atom_iterations, "near_tie_leaves": s.near_tie_leaves,
             "attempts_per_level": list(s.attempts_per_level),
             "iterations_per_level": list(s.iterations_per_level),
-            "window_steps_per_level": list(s.window_steps_per_level)}
+            "window_steps_per_level": list(s.window_steps_per_level),
+            "max_leaf_steps_per_level": list(s.max_leaf_steps_per_level)}
 
 
 def _pinned(n: int, dtype) -> np.ndarray:

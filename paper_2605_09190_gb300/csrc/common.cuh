@@ -56,6 +56,7 @@ struct Counters {
     unsigned long long attempts[kMaxLevels];
     unsigned long long iterations[kMaxLevels];
     unsigned long long window_steps[kMaxLevels];   // steps decided in full precision
+    unsigned int max_steps[kMaxLevels];     // longest pursuit of the level (steps)
     unsigned int queue_count[kMaxLevels + 1];
     unsigned int work_next[kMaxLevels];     // dynamic leaf assignment per level
     unsigned int error;                // first AQMP_E_* code raised on the device

@@ -311,6 +311,7 @@ struct Ctx {
     bool gauss_ready = false;
     Tuner tuner;
     Counters *host_ctr = nullptr;             // pinned
+    cudaMemPool_t out_pool = nullptr;         // encode outputs (aqmp_code arrays)
     unsigned char *host_call = nullptr;       // pinned: plane descriptors + output pointers
     size_t host_call_cap = 0;
     // Captured encodes, one per configuration (see aqmp_encode_planes).
@@ -354,12 +355,16 @@ int get_ctx(Ctx **out) {
             return fail(AQMP_E_CUDA, "device %d is sm_%d%d; this library is built for sm_103a only", dev,
                         c->cc_major, c->cc_minor);
         CK(cudaMallocHost(&c->host_ctr, sizeof(Counters)));
-        // keep freed output blocks cached in the stream-ordered pool
-        cudaMemPool_t pool;
-        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
-            unsigned long long keep = ~0ull;
-            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
-        }
+        // the encode outputs come from a pool of the library's own, which
+        // keeps freed blocks cached (the process-wide default pool, which
+        // other code of the process may use, is left as it is)
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        CK(cudaMemPoolCreate(&c->out_pool, &props));
+        unsigned long long keep = ~0ull;
+        CK(cudaMemPoolSetAttribute(c->out_pool, cudaMemPoolAttrReleaseThreshold, &keep));
         slot = std::move(c);
     }
     *out = slot.get();
@@ -646,9 +651,12 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
     if ((rc = c->order_status.reserve(sizeof(unsigned long long) * status_words))) return rc;
     auto code = std::make_unique<aqmp_code>();
     code->device = c->device;
-    CK(cudaMallocAsync((void **)&code->leaves, sizeof(LeafRec) * std::max<unsigned long long>(1, leaf_cap), st));
-    CK(cudaMallocAsync((void **)&code->atoms, sizeof(AtomRec) * std::max<unsigned long long>(1, atom_cap), st));
-    CK(cudaMallocAsync((void **)&code->alpha_lo, sizeof(float) * std::max<unsigned long long>(1, atom_cap), st));
+    CK(cudaMallocFromPoolAsync((void **)&code->leaves, sizeof(LeafRec) * std::max<unsigned long long>(1, leaf_cap),
+                               c->out_pool, st));
+    CK(cudaMallocFromPoolAsync((void **)&code->atoms, sizeof(AtomRec) * std::max<unsigned long long>(1, atom_cap),
+                               c->out_pool, st));
+    CK(cudaMallocFromPoolAsync((void **)&code->alpha_lo, sizeof(float) * std::max<unsigned long long>(1, atom_cap),
+                               c->out_pool, st));
     if ((rc = c->counters.reserve(sizeof(Counters)))) return rc;
 
     // plane descriptors (and host pixels copied in)
@@ -933,6 +941,7 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
         s.attempts_per_level[l] = h.attempts[l];
         s.iterations_per_level[l] = h.iterations[l];
         s.window_steps_per_level[l] = h.window_steps[l];
+        s.max_leaf_steps_per_level[l] = h.max_steps[l];
         s.attempts += h.attempts[l];
         s.atom_iterations += h.iterations[l];
     }

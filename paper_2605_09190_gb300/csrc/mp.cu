@@ -96,7 +96,9 @@ mp_kernel(MPArgs a) {
 
     const LevelArgs &lv = a.lv;
     __shared__ unsigned long long sCnt[3];              // per-CTA work counters (T == 32)
+    __shared__ unsigned sMaxT;
     if (T == 32 && threadIdx.x < 3) sCnt[threadIdx.x] = 0ull;
+    if (threadIdx.x == 0) sMaxT = 0u;
     if (NF == 2) {
         for (int i = threadIdx.x; i < B * B; i += blockDim.x) {
             sW[i] = a.W[i];
@@ -113,6 +115,7 @@ mp_kernel(MPArgs a) {
     const int k = lv.k;
     unsigned *work = &a.ctr->work_next[lv.level];
     unsigned long long n_attempts = 0, n_steps = 0, n_windows = 0;
+    unsigned max_t = 0;
 
     for (;;) {
         // dynamic assignment: the next unclaimed leaf of this level
@@ -405,6 +408,7 @@ mp_kernel(MPArgs a) {
         n_attempts += 1;
         n_steps += (unsigned long long)t;
         n_windows += (unsigned long long)windows;
+        max_t = max(max_t, (unsigned)t);
         const bool emit = conv || lv.is_last;
         uint32_t off = 0, eslot = 0;
         if (emit) {
@@ -480,17 +484,20 @@ mp_kernel(MPArgs a) {
             atomicAdd(&sCnt[0], n_attempts);
             atomicAdd(&sCnt[1], n_steps);
             atomicAdd(&sCnt[2], n_windows);
+            atomicMax(&sMaxT, max_t);
         }
         __syncthreads();
         if (threadIdx.x == 0 && sCnt[0]) {
             atomicAdd(&a.ctr->attempts[lv.level], sCnt[0]);
             atomicAdd(&a.ctr->iterations[lv.level], sCnt[1]);
             if (sCnt[2]) atomicAdd(&a.ctr->window_steps[lv.level], sCnt[2]);
+            atomicMax(&a.ctr->max_steps[lv.level], sMaxT);
         }
     } else if (lane == 0 && n_attempts) {
         atomicAdd(&a.ctr->attempts[lv.level], n_attempts);
         atomicAdd(&a.ctr->iterations[lv.level], n_steps);
         if (n_windows) atomicAdd(&a.ctr->window_steps[lv.level], n_windows);
+        atomicMax(&a.ctr->max_steps[lv.level], max_t);
     }
 }
 
@@ -561,6 +568,7 @@ __global__ void __launch_bounds__(128) mp_thread_kernel(MPArgs a) {
     constexpr int B = 4, n = B * B, M = NF * n;
     __shared__ float2 sW[2 * B * B];                     // W then W^T
     __shared__ unsigned long long sCnt[3];
+    __shared__ unsigned sMaxT;
     extern __shared__ __align__(16) unsigned char smem[];
     StepRec *steps = reinterpret_cast<StepRec *>(smem) + (size_t)threadIdx.x * a.lv.k;
 
@@ -568,6 +576,7 @@ __global__ void __launch_bounds__(128) mp_thread_kernel(MPArgs a) {
     if (NF == 2)
         for (int i = threadIdx.x; i < 2 * B * B; i += blockDim.x) sW[i] = i < B * B ? a.W[i] : a.WT[i - B * B];
     if (threadIdx.x < 3) sCnt[threadIdx.x] = 0ull;
+    if (threadIdx.x == 0) sMaxT = 0u;
     __syncthreads();
 
     const int lane = threadIdx.x & 31;
@@ -575,6 +584,7 @@ __global__ void __launch_bounds__(128) mp_thread_kernel(MPArgs a) {
     const int k = lv.k;
     const unsigned stride = gridDim.x * blockDim.x;
     unsigned long long n_attempts = 0, n_steps = 0, n_windows = 0;
+    unsigned max_t = 0;
 
     for (unsigned base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < count; base += stride) {
         const unsigned leaf = base + (unsigned)lane;
@@ -697,6 +707,7 @@ __global__ void __launch_bounds__(128) mp_thread_kernel(MPArgs a) {
             n_attempts += 1;
             n_steps += (unsigned long long)t;
             n_windows += (unsigned long long)windows;
+            max_t = max(max_t, (unsigned)t);
         }
 
         // (a7) emission and splits, aggregated over the warp
@@ -775,12 +786,14 @@ __global__ void __launch_bounds__(128) mp_thread_kernel(MPArgs a) {
         atomicAdd(&sCnt[0], n_attempts);
         atomicAdd(&sCnt[1], n_steps);
         atomicAdd(&sCnt[2], n_windows);
+        atomicMax(&sMaxT, max_t);
     }
     __syncthreads();
     if (threadIdx.x == 0 && sCnt[0]) {
         atomicAdd(&a.ctr->attempts[lv.level], sCnt[0]);
         atomicAdd(&a.ctr->iterations[lv.level], sCnt[1]);
         if (sCnt[2]) atomicAdd(&a.ctr->window_steps[lv.level], sCnt[2]);
+        atomicMax(&a.ctr->max_steps[lv.level], sMaxT);
     }
 }
 

@@ -238,6 +238,7 @@ __global__ void __launch_bounds__(kCT, 1) mp_cluster_kernel(MPArgs a) {
     const int k = lv.k;
     unsigned *work = &a.ctr->work_next[lv.level];
     unsigned long long n_attempts = 0, n_steps = 0, n_windows = 0;
+    unsigned max_t = 0;
     int seq = 0, sseq = 0;
     bool aborted = false;
     const int warp = lane >> 5;
@@ -469,6 +470,7 @@ __global__ void __launch_bounds__(kCT, 1) mp_cluster_kernel(MPArgs a) {
         if (rank == 0) {
             n_attempts += 1;
             n_steps += (unsigned long long)t;
+            max_t = max(max_t, (unsigned)t);
             n_windows += (unsigned long long)windows;
             const bool emit = conv || lv.is_last;
             if (emit) {
@@ -529,6 +531,7 @@ __global__ void __launch_bounds__(kCT, 1) mp_cluster_kernel(MPArgs a) {
         atomicAdd(&a.ctr->attempts[lv.level], n_attempts);
         atomicAdd(&a.ctr->iterations[lv.level], n_steps);
         if (n_windows) atomicAdd(&a.ctr->window_steps[lv.level], n_windows);
+        atomicMax(&a.ctr->max_steps[lv.level], max_t);
     }
     if (aborted && threadIdx.x == 0) {
         raise_error(a.ctr, kDevErrTimeout, 11u);

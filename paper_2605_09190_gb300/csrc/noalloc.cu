@@ -19,12 +19,15 @@
 // In host code the arrays' names are host-side stand-ins, not device
 // addresses, so the first call on each device looks their device addresses up
 // with cudaGetSymbolAddress (with that device current) and keeps them; that
-// first call should come before any stream capture.  Every call shares the
-// arrays and they keep the previous call's contents: the table region is
-// cleared before it is rebuilt, the error word at every call, and each call
-// rewrites every scratch byte it reads.  Calls whose GPU work overlaps would
-// race on the arrays; this entry point serialises its callers and
-// synchronises the stream before returning, so calls made through it never
+// first call should come before any stream capture.  No call can be captured
+// into a CUDA graph: every call waits for its stream and reads a status word
+// back, so a call on a capturing stream returns AQMP_E_UNSUPPORTED without
+// touching the stream.  Every call shares the arrays and they keep the
+// previous call's contents: the table region is cleared before it is rebuilt,
+// the error word at every call, and each call rewrites every scratch byte it
+// reads.  Calls whose GPU work overlaps would race on the arrays; this entry
+// point serialises its callers and synchronises the stream before returning
+// (on an error too, once it has queued work), so calls made through it never
 // overlap.
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -129,6 +132,7 @@ __global__ void static_tables_kernel(int b, int nf, int fam0, const double *basi
 
 extern "C" int aqmp_correlate_noalloc(int b, int dict_id, const uint8_t *blocks, int64_t L, float *corr,
                                       void *stream) {
+    set_error(AQMP_OK, "");
     if (b != 4 && b != 8 && b != 16)
         return set_error(AQMP_E_ARG, "aqmp_correlate_noalloc: block side must be 4, 8 or 16");
     if (dict_id < 0 || dict_id > 2) return set_error(AQMP_E_DICT, "unknown dictionary id");
@@ -142,37 +146,58 @@ extern "C" int aqmp_correlate_noalloc(int b, int dict_id, const uint8_t *blocks,
     if (L > max_blocks)
         return set_error(AQMP_E_ARG, "aqmp_correlate_noalloc: more blocks than the static scratch holds");
     if (L == 0) return AQMP_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    // every call waits for its stream and reads a status word back, which a
+    // stream capture cannot record: refuse before touching the stream
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess)
+        return set_error(AQMP_E_CUDA, "aqmp_correlate_noalloc: cannot query the stream");
+    if (cap != cudaStreamCaptureStatusNone)
+        return set_error(AQMP_E_UNSUPPORTED, "aqmp_correlate_noalloc: the stream is being captured");
 
     std::lock_guard<std::mutex> lock(g_mu);
     Slot *slot;
     int rc = device_slot(&slot);
     if (rc != AQMP_OK) return rc;
-    cudaStream_t st = (cudaStream_t)stream;
-#define NA_CK(call)                                                              \
-    do {                                                                         \
-        if ((call) != cudaSuccess) return set_error(AQMP_E_CUDA, #call " failed"); \
+    // Errors before the first enqueue return at once; errors after it wait
+    // for the stream first, so that no work of this call still writes the
+    // shared arrays when the next caller takes the lock.
+    bool queued = false;
+    auto fail_after = [&](int code, const char *msg) {
+        if (queued) cudaStreamSynchronize(st);
+        return set_error(code, msg);
+    };
+#define NA_CK(call)                                                                   \
+    do {                                                                              \
+        if ((call) != cudaSuccess) return fail_after(AQMP_E_CUDA, #call " failed");   \
     } while (0)
 
-    if (slot->table_b != b || slot->table_dict != dict_id) {
+    // tensor maps first: they need only the arrays' addresses
+    CUtensorMap ymap;
+    if ((rc = bf16_tensor_map(&ymap, slot->scratch, (unsigned long long)L, Kpad, 64))) return rc;
+    const bool rebuild = slot->table_b != b || slot->table_dict != dict_id;
+    if (rebuild) {
+        if ((rc = bf16_tensor_map(&slot->limb_map, slot->limbs, (unsigned long long)kLimbs * Mpad, Kpad, 128)))
+            return rc;
+        slot->table_b = 0;                      // the tables are stale until the rebuild completes
+        slot->table_dict = -1;
         std::vector<double> basis;
         fp64_bases(b, basis);
+        queued = true;
         NA_CK(cudaMemsetAsync(slot->limbs, 0, sizeof(g_limbs), st));
         NA_CK(cudaMemcpyAsync(slot->basis, basis.data(), sizeof(double) * basis.size(), cudaMemcpyHostToDevice, st));
         static_tables_kernel<<<(M + 7) / 8, 256, 0, st>>>(b, nf, dict_id == AQMP_DICT_HAAR ? 1 : 0,
                                                            (const double *)slot->basis, Mpad, Kpad,
                                                            (__nv_bfloat16 *)slot->limbs, (long long *)slot->sums);
         NA_CK(cudaGetLastError());
-        if ((rc = bf16_tensor_map(&slot->limb_map, slot->limbs, (unsigned long long)kLimbs * Mpad, Kpad, 128)))
-            return rc;
         NA_CK(cudaStreamSynchronize(st));       // the host basis buffer goes out of scope
         slot->table_b = b;
         slot->table_dict = dict_id;
     }
+    queued = true;
     NA_CK(cudaMemsetAsync(slot->counters, 0, sizeof(Counters), st));
     // gather into the static scratch (every byte read below is rewritten)
     NA_CK(launch_gather_blocks(b, Kpad, blocks, L, (__nv_bfloat16 *)slot->scratch, nullptr, slot->sms, st));
-    CUtensorMap ymap;
-    if ((rc = bf16_tensor_map(&ymap, slot->scratch, (unsigned long long)L, Kpad, 64))) return rc;
     DictDev d{};
     d.b = b;
     d.n = n;

@@ -259,6 +259,7 @@ __global__ void __launch_bounds__(256, 1) omp_kernel(MPArgs a) {
         if (lane == 0) {
             atomicAdd(&a.ctr->attempts[lv.level], 1ull);
             atomicAdd(&a.ctr->iterations[lv.level], (unsigned long long)nS);
+            atomicMax(&a.ctr->max_steps[lv.level], (unsigned)nS);
         }
         const bool emit = conv || lv.is_last;
         uint32_t off = kNoAtom, eslot = 0;

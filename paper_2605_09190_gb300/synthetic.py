@@ -89,17 +89,32 @@ def noise_plane(h: int, w: int, seed: int = 0, mean: float = 128.0, sigma: float
     return _finish(rng.normal(mean, sigma, size=(h, w)))
 
 
-def uneven_rgb_batch(n_images: int = 64, seed: int = 0, wmin: int = 256, wmax: int = 2048,
-                     hmin: int = 256, hmax: int = 1536, step: int = 64, scene=None):
-    """`n_images` RGB images of uneven sizes, width and height drawn uniformly
-    from multiples of `step`; channel c of image i is the piecewise scene (the
-    512x512 workload's generator) of seed `seed + 3 i + c`, or `scene(h, w,
-    seed=...)` when given.  Returns a list of (h, w, [R, G, B]) tuples."""
-    make = scene or piecewise_scene
+def uneven_sizes(n_images: int, seed: int = 0, wmin: int = 256, wmax: int = 2048,
+                 hmin: int = 256, hmax: int = 1536, step: int = 64):
+    """(h, w) of the `n_images` images of an uneven batch: width and height
+    drawn uniformly from the multiples of `step` in [wmin, wmax] x [hmin,
+    hmax], image by image from one PCG64 stream seeded with `seed`."""
     rng = np.random.default_rng(seed)
     out = []
-    for i in range(n_images):
+    for _ in range(n_images):
         w = int(rng.integers(wmin // step, wmax // step + 1)) * step
         h = int(rng.integers(hmin // step, hmax // step + 1)) * step
-        out.append((h, w, [make(h, w, seed=seed + 3 * i + c) for c in range(3)]))
+        out.append((h, w))
     return out
+
+
+def uneven_rgb_batch(n_images: int = 64, seed: int = 0, wmin: int = 256, wmax: int = 2048,
+                     hmin: int = 256, hmax: int = 1536, step: int = 64, scene=None, first: int = 0,
+                     count: int | None = None):
+    """RGB images of uneven sizes (``uneven_sizes``); channel c of image i is
+    ``scene(h, w, seed=seed + 3 i + c)`` -- the piecewise scene (the 512x512
+    workload's generator) unless another scene is given, e.g.
+    ``gradient_scene``.  Only images [first, first + count) of the
+    `n_images`-image batch are drawn (a shard of it; the sizes of the others
+    are still consumed from the stream, so a shard is the same images as in
+    the whole batch).  Returns a list of (h, w, [R, G, B]) tuples."""
+    make = scene or piecewise_scene
+    sizes = uneven_sizes(n_images, seed, wmin, wmax, hmin, hmax, step)
+    last = n_images if count is None else min(n_images, first + count)
+    return [(h, w, [make(h, w, seed=seed + 3 * i + c) for c in range(3)])
+            for i, (h, w) in enumerate(sizes) if first <= i < last]
