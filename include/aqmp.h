@@ -60,6 +60,13 @@ extern "C" {
                                       (FP32 accumulation, no exact digits), then
                                       the FP32 form's pursuit; decisions not
                                       certified */
+#define AQMP_PREC_FP8       3      /* the FP8 form: one E4M3 tensor-core pass
+                                      (kind::f8f6f4) of e4m3(D s_j) against
+                                      e4m3((y - 128) s_l), s_j and s_l powers of
+                                      two per atom and per block (the largest
+                                      keeping the values within 448), FP32
+                                      accumulation, rescaled; then the FP32
+                                      form's pursuit; decisions not certified */
 
 /* aqmp_params.flags */
 #define AQMP_FLAG_INPUT_DEVICE  1u /* plane pointers are device addresses */

@@ -26,6 +26,7 @@ AQMP_DICT_DCT_HAAR, AQMP_DICT_DCT, AQMP_DICT_HAAR = 0, 1, 2
 AQMP_PREC_EXACT = 0
 AQMP_PREC_FP32 = 1
 AQMP_PREC_BF16 = 2
+AQMP_PREC_FP8 = 3
 AQMP_FLAG_INPUT_DEVICE = 1
 AQMP_FLAG_SIMT_GEMM = 2
 AQMP_FLAG_NO_AUTOTUNE = 4

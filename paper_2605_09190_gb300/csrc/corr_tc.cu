@@ -128,6 +128,8 @@ __device__ __forceinline__ unsigned long long smem_desc(uint32_t addr) {
 // kind::f16 instruction descriptor: BF16 x BF16 -> F32, both K-major.
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kN >> 3) << 17) |
                             ((uint32_t)(kM >> 4) << 24);
+// kind::f8f6f4 instruction descriptor: E4M3 x E4M3 (format code 0) -> F32.
+constexpr uint32_t kIdesc8 = (1u << 4) | ((uint32_t)(kN >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, unsigned long long adesc, unsigned long long bdesc,
                                          uint32_t accumulate) {
@@ -136,6 +138,18 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, unsigned long long ade
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
         ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+        : "memory");
+}
+
+// One E4M3 MMA step of K = 32 (32 bytes of each 128-byte row, as K = 16
+// of BF16, so the descriptors advance the same way).
+__device__ __forceinline__ void mma_e4m3(uint32_t tmem_d, unsigned long long adesc, unsigned long long bdesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(kIdesc8), "r"(accumulate)
         : "memory");
 }
 
@@ -159,13 +173,18 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
 // L = kLimbs: the exact form above.  L = 1: the reduced-precision form --
 // one BF16 matrix bf16(D) against the centred pixels, FP32 accumulation,
 // c0 = acc + 128 Sbf[j] (Sbf the row sums of bf16(D)), low word 0.
-template <int L>
+// FP8 (with L = 1): the FP8 form -- one E4M3 matrix e4m3(D s_j) against
+// e4m3(y~ s_l), FP32 accumulation, c0 = acc / (s_j s_l) + 128 Sbf[j] with
+// Sbf the dequantised row sums; a K block is 128 elements (one 128-byte row).
+template <int L, bool FP8 = false>
 __global__ void __launch_bounds__(tc::kThreads, 1)
 corr_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M,
                int Mpad, int kb0, int KB, int mode, const long long *__restrict__ Sh,
                const long long *__restrict__ Sl, const float *__restrict__ Sbf, const unsigned *count_dev,
-               long long fixed_count, float2 *__restrict__ c0, Counters *ctr) {
+               long long fixed_count, float2 *__restrict__ c0, Counters *ctr,
+               const float *__restrict__ inv_s_atom = nullptr, const float *__restrict__ inv_s_leaf = nullptr) {
     using namespace tc;
+    constexpr int kKe = FP8 ? 2 * kK : kK;               // elements per 128-byte row
     const long long count = count_dev ? (long long)*count_dev : fixed_count;
     const long long leaf0 = (long long)blockIdx.x * kN;
     if (leaf0 >= count) return;                        // uniform: nothing to do
@@ -209,12 +228,12 @@ corr_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         for (int kb = 0; kb < KB && !*abort_flag; ++kb) {
             if (!mbar_wait(emptyB(sb), pb ^ 1u, abort_flag)) break;
             mbar_expect_tx(fullB(sb), kTileB);
-            tma_load_2d(sB + sb * kTileB, &tmB, fullB(sb), (kb0 + kb) * kK, (int)leaf0);
+            tma_load_2d(sB + sb * kTileB, &tmB, fullB(sb), (kb0 + kb) * kKe, (int)leaf0);
             if (++sb == kStagesB) { sb = 0; pb ^= 1u; }
             for (int s = 0; s < L; ++s) {
                 if (!mbar_wait(emptyA(sa), pa ^ 1u, abort_flag)) break;
                 mbar_expect_tx(fullA(sa), kTileA);
-                tma_load_2d(sA + sa * kTileA, &tmA, fullA(sa), (kb0 + kb) * kK, s * Mpad + m0);
+                tma_load_2d(sA + sa * kTileA, &tmA, fullA(sa), (kb0 + kb) * kKe, s * Mpad + m0);
                 if (++sa == kStagesA) { sa = 0; pa ^= 1u; }
             }
         }
@@ -231,9 +250,14 @@ corr_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
                 const unsigned long long ad = smem_desc(sA + sa * kTileA);
                 const unsigned long long bd = smem_desc(sB + sb * kTileB);
 #pragma unroll
-                for (int kk = 0; kk < kK / 16; ++kk)
-                    mma_bf16(tmem + (uint32_t)(s * kN), ad + 2ull * kk, bd + 2ull * kk,
-                             (kb > 0 || kk > 0) ? 1u : 0u);
+                for (int kk = 0; kk < kK / 16; ++kk) {
+                    if (FP8)
+                        mma_e4m3(tmem + (uint32_t)(s * kN), ad + 2ull * kk, bd + 2ull * kk,
+                                 (kb > 0 || kk > 0) ? 1u : 0u);
+                    else
+                        mma_bf16(tmem + (uint32_t)(s * kN), ad + 2ull * kk, bd + 2ull * kk,
+                                 (kb > 0 || kk > 0) ? 1u : 0u);
+                }
                 mma_commit(emptyA(sa));
                 if (++sa == kStagesA) { sa = 0; pa ^= 1u; }
             }
@@ -252,6 +276,7 @@ corr_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
         const int m = m0 + warp * 32 + lane;
         const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
         const float centre = m < M ? 128.0f * Sbf[m] : 0.0f;
+        const float inv_a = (FP8 && m < M) ? inv_s_atom[m] : 1.0f;
         for (int nb = 0; nb < kN; nb += 8) {
             float P[8];
             tmem_ld8(lane_addr + (uint32_t)nb, P);
@@ -260,7 +285,10 @@ corr_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
                     const long long leaf = leaf0 + nb + i;
-                    if (leaf < count) c0[leaf * M + m] = make_float2(P[i] + centre, 0.0f);
+                    if (leaf < count) {
+                        const float v = FP8 ? P[i] * inv_a * inv_s_leaf[leaf] : P[i];
+                        c0[leaf * M + m] = make_float2(v + centre, 0.0f);
+                    }
                 }
             }
         }
@@ -328,6 +356,23 @@ cudaError_t launch_corr_tc_bf16(const CorrArgs &a, cudaStream_t st) {
     corr_tc_kernel<1><<<grid, tc::kThreads, tc::kSmemBytes, st>>>(*ma, *mb, d.M, d.Mpad, 0, d.Kpad / tc::kK,
                                                                   kCorrSingle, nullptr, nullptr, d.Sbf, a.count,
                                                                   a.fixed_count, a.c0, a.ctr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_corr_tc_fp8(const CorrArgs &a, const float *inv_sl, cudaStream_t st) {
+    const DictDev &d = *a.d;
+    if (!d.tmap_fp8 || !d.S8 || !d.inv_s8 || !inv_sl) return cudaErrorInvalidValue;
+    const long long rows = a.count ? (long long)a.capacity : a.fixed_count;
+    dim3 grid((unsigned)((rows + tc::kN - 1) / tc::kN), (unsigned)(d.Mpad / tc::kM));
+    if (grid.x == 0) return cudaSuccess;
+    auto kern = corr_tc_kernel<1, true>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes);
+    if (e != cudaSuccess) return e;
+    const CUtensorMap *ma = reinterpret_cast<const CUtensorMap *>(d.tmap_fp8);
+    const CUtensorMap *mb = reinterpret_cast<const CUtensorMap *>(a.tmap_Y);
+    kern<<<grid, tc::kThreads, tc::kSmemBytes, st>>>(*ma, *mb, d.M, d.Mpad, 0, kpad_fp8(d.n) / 128, kCorrSingle,
+                                                     nullptr, nullptr, d.S8, a.count, a.fixed_count, a.c0, a.ctr,
+                                                     d.inv_s8, inv_sl);
     return cudaGetLastError();
 }
 

@@ -7,6 +7,7 @@
 // correlation by adding 128 sum_v D_fix[j][v].
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -39,12 +40,43 @@ __global__ void __launch_bounds__(256) gather_kernel(GatherArgs a) {
             tile[i * stride + m] = (uint8_t)p;
         }
         if (TPL == 32) __syncwarp(); else __syncthreads();
-        __nv_bfloat162 *dst = reinterpret_cast<__nv_bfloat162 *>(a.Y + (size_t)leaf * a.Kpad);
-        for (int v = 2 * t; v < a.Kpad; v += 2 * TPL) {          // unravel order, BF16 pairs
-            float v0 = 0.0f, v1 = 0.0f;
-            if (v < n) v0 = (float)((int)tile[(v % B) * stride + v / B] - 128);
-            if (v + 1 < n) v1 = (float)((int)tile[((v + 1) % B) * stride + (v + 1) / B] - 128);
-            dst[v >> 1] = __floats2bfloat162_rn(v0, v1);
+        if (a.Y8) {
+            // FP8 form: centred pixels times the block's power-of-two scale
+            // s_l (the largest with max |y~| s_l <= 448), rounded to E4M3
+            uint32_t amax = 0;
+            for (int idx = t; idx < n; idx += TPL) {
+                const int d = (int)tile[(idx / B) * stride + idx % B] - 128;
+                amax = max(amax, (uint32_t)(d < 0 ? -d : d));
+            }
+            for (int off = 16; off > 0; off >>= 1) amax = max(amax, __shfl_xor_sync(0xffffffffu, amax, off));
+            if (NW > 1) {
+                if (lane == 0) s_ss[threadIdx.x >> 5] = amax;
+                __syncthreads();
+                amax = 0;
+                for (int w = 0; w < NW; ++w) amax = max(amax, s_ss[w]);
+                __syncthreads();
+            }
+            int ex = 0;
+            while (amax > 0 && ((unsigned long long)amax << (ex + 1)) <= 448ull) ++ex;
+            const float sl = (float)(1 << ex);
+            const int K8 = kpad_fp8(n);
+            uint8_t *dst8 = a.Y8 + (size_t)leaf * K8;
+            for (int v = t; v < K8; v += TPL) {
+                __nv_fp8_storage_t q8 = 0;
+                if (v < n)
+                    q8 = __nv_cvt_float_to_fp8((float)((int)tile[(v % B) * stride + v / B] - 128) * sl,
+                                               __NV_SATFINITE, __NV_E4M3);
+                dst8[v] = q8;
+            }
+            if (t == 0) a.inv_sl[leaf] = 1.0f / sl;
+        } else {
+            __nv_bfloat162 *dst = reinterpret_cast<__nv_bfloat162 *>(a.Y + (size_t)leaf * a.Kpad);
+            for (int v = 2 * t; v < a.Kpad; v += 2 * TPL) {      // unravel order, BF16 pairs
+                float v0 = 0.0f, v1 = 0.0f;
+                if (v < n) v0 = (float)((int)tile[(v % B) * stride + v / B] - 128);
+                if (v + 1 < n) v1 = (float)((int)tile[((v + 1) % B) * stride + (v + 1) / B] - 128);
+                dst[v >> 1] = __floats2bfloat162_rn(v0, v1);
+            }
         }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, off);
@@ -122,6 +154,45 @@ cudaError_t launch_gather_blocks(int b, int Kpad, const uint8_t *blocks, long lo
     if (blocks_needed > cap) blocks_needed = cap;
     if (blocks_needed < 1) blocks_needed = 1;
     gather_blocks_kernel<<<(unsigned)blocks_needed, 256, 0, st>>>(b, Kpad, blocks, L, Y, e0);
+    return cudaGetLastError();
+}
+
+// The same for the FP8 form: e4m3(y~ s_l) with the block's power-of-two
+// scale s_l (max |y~| s_l <= 448), zero padded to kpad_fp8(n), and 1 / s_l.
+__global__ void gather_blocks_fp8_kernel(int b, const uint8_t *blocks, long long L, uint8_t *Y8, float *inv_sl) {
+    const int lane = threadIdx.x & 31;
+    const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const int n = b * b, K8 = kpad_fp8(n);
+    for (long long leaf = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; leaf < L; leaf += warps) {
+        const uint8_t *base = blocks + leaf * n;
+        uint32_t amax = 0;
+        for (int v = lane; v < n; v += 32) {
+            const int d = (int)base[v] - 128;
+            amax = max(amax, (uint32_t)(d < 0 ? -d : d));
+        }
+        for (int off = 16; off > 0; off >>= 1) amax = max(amax, __shfl_xor_sync(0xffffffffu, amax, off));
+        int ex = 0;
+        while (amax > 0 && ((unsigned long long)amax << (ex + 1)) <= 448ull) ++ex;
+        const float sl = (float)(1 << ex);
+        for (int v = lane; v < K8; v += 32) {
+            __nv_fp8_storage_t q8 = 0;
+            if (v < n) {
+                const int m = v / b, i = v - m * b;
+                q8 = __nv_cvt_float_to_fp8((float)((int)base[i * b + m] - 128) * sl, __NV_SATFINITE, __NV_E4M3);
+            }
+            Y8[leaf * K8 + v] = q8;
+        }
+        if (lane == 0) inv_sl[leaf] = 1.0f / sl;
+    }
+}
+
+cudaError_t launch_gather_blocks_fp8(int b, const uint8_t *blocks, long long L, uint8_t *Y8, float *inv_sl,
+                                     int num_sms, cudaStream_t st) {
+    long long blocks_needed = (L + 7) / 8;
+    long long cap = (long long)num_sms * 8;
+    if (blocks_needed > cap) blocks_needed = cap;
+    if (blocks_needed < 1) blocks_needed = 1;
+    gather_blocks_fp8_kernel<<<(unsigned)blocks_needed, 256, 0, st>>>(b, blocks, L, Y8, inv_sl);
     return cudaGetLastError();
 }
 

@@ -136,6 +136,23 @@ int encode_bf16_map(CUtensorMap *map, const void *base, unsigned long long rows,
     return AQMP_OK;
 }
 
+// 2-D byte tensor [rows][cols] (cols contiguous) read in boxes of box_rows x
+// 128 bytes with the 128-byte swizzle (the FP8 operands).
+int encode_u8_map(CUtensorMap *map, const void *base, unsigned long long rows, unsigned long long cols,
+                  unsigned box_rows) {
+    auto enc = tensor_map_encoder();
+    if (!enc) return fail(AQMP_E_CUDA, "cuTensorMapEncodeTiled is unavailable");
+    cuuint64_t dims[2] = {cols, rows};
+    cuuint64_t strides[1] = {cols};
+    cuuint32_t box[2] = {128, box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(AQMP_E_CUDA, "cuTensorMapEncodeTiled (bytes) failed (%d)", (int)r);
+    return AQMP_OK;
+}
+
 // ------------------------------------------------------------ context
 
 // Bumped whenever a workspace buffer moves: captured graphs hold its
@@ -225,7 +242,8 @@ std::string kname(const char *k, int b) { return std::string(k) + "_b" + std::to
 // ------------------------------------------------------------ autotuner
 //
 // Choice points whose candidates give the same result bit for bit: the
-// initial correlation on the tensor cores or the integer SIMT path (K1), and
+// separable exact correlation on the tensor cores or on the integer SIMT
+// path (K1, at the sides with a tensor-core kernel), and
 // the pursuit's launch shape (K2: threads per leaf, or resident CTAs per SM
 // at side 64).  Each is keyed by (kind, side,
 // dictionary, precision, log2 capacity); its candidates are timed with CUDA
@@ -233,11 +251,6 @@ std::string kname(const char *k, int b) { return std::string(k) + "_b" + std::to
 // recomputing the correlation is harmless; K2: alternately over encodes),
 // and the one with the lowest timing is kept.  The lowest of two timings
 // discards a kernel's first, cold launch.
-// Sides from which the correlation is not autotuned: at side 128 the
-// integer SIMT kernel takes about 6x the tensor-core time (245 against
-// 38 ms for 3072 leaves), so timing it would only add a second to the first
-// encode.
-constexpr int kCorrTunedMax = 128;
 
 struct Tuner {
     enum Kind { CORR = 0, MP = 1 };
@@ -292,12 +305,15 @@ struct Tuner {
 
 struct Dict {
     DictDev d{};
-    DeviceBuf limbs, dh, dl, sh, sl, w, basis, basis64;
+    DeviceBuf limbs, dh, dl, sh, sl, w, basis, basis64, sep;
     CUtensorMap tmap;
     bool tables = false;         // fixed-point correlation tables built (16 M n B + 8 M n B)
     DeviceBuf dbf, sbf;          // reduced-precision form: bf16(D) and its row sums
     CUtensorMap tmap_bf;
     bool bf16 = false;
+    DeviceBuf d8, s8;            // FP8 form: e4m3(D s_j), 1 / s_j and row sums
+    CUtensorMap tmap_f8;
+    bool fp8 = false;
 };
 
 struct Ctx {
@@ -306,7 +322,7 @@ struct Ctx {
     int cc_major = 0, cc_minor = 0;
     std::mutex mu;
     std::map<int, std::unique_ptr<Dict>> dicts;
-    DeviceBuf planes, staging, queues, Y, e0, c0, counters, ssim_ws;
+    DeviceBuf planes, staging, queues, Y, e0, c0, counters, ssim_ws, Y8, inv_sl;
     DeviceBuf leaves_ws, atoms_ws, lo_ws, atom_leaf, cells, perm, new_off, order_status;   // emission -> canonical order
     bool gauss_ready = false;
     Tuner tuner;
@@ -378,7 +394,8 @@ int num_families(int dict_id) { return dict_id == AQMP_DICT_DCT_HAAR ? 2 : 1; }
 // (Dh, Dl): 24 M n bytes, 12.9 GB at side 128) only when `tables` is set,
 // so that decoding and synthesis never build them; bf16(D) (2 M Kpad bytes)
 // only when `bf16` is set (the reduced-precision form).
-int get_dict(Ctx *c, int b, int dict_id, cudaStream_t st, Dict **out, bool tables = true, bool bf16 = false) {
+int get_dict(Ctx *c, int b, int dict_id, cudaStream_t st, Dict **out, bool tables = true, bool bf16 = false,
+             bool fp8 = false) {
     const int key = b * 16 + dict_id;
     auto it = c->dicts.find(key);
     Dict *D = nullptr;
@@ -400,9 +417,39 @@ int get_dict(Ctx *c, int b, int dict_id, cudaStream_t st, Dict **out, bool table
         d.W = (float2 *)Dn->w.p;
         d.WT = d.W + b * b;
         d.basis = (float *)Dn->basis.p;
+        d.fam0 = dict_id == AQMP_DICT_HAAR ? 1 : 0;
 
         std::vector<double> basis;
         make_bases(b, basis);
+
+        // separable fixed-point dictionary: Bf = round(B 2^48) per 1-D row,
+        // as 24-bit limbs (lo in [-2^23, 2^23), hi), its transpose, and the
+        // row sums (both families; a few hundred KB at most)
+        {
+            const size_t bb = (size_t)b * b;
+            std::vector<int32_t> limbs(2 * 2 * 2 * bb);            // Bs then BsT, (lo, hi) pairs
+            std::vector<long long> rows(2 * (size_t)b, 0);
+            for (int F = 0; F < 2; ++F)
+                for (int p = 0; p < b; ++p)
+                    for (int i = 0; i < b; ++i) {
+                        const long long f = std::llrint(std::ldexp(basis[F * bb + (size_t)p * b + i], 48));
+                        const long long lo = ((f + (1ll << 23)) & ((1ll << 24) - 1)) - (1ll << 23);
+                        const long long hi = (f - lo) / (1ll << 24);
+                        const size_t at = F * bb + (size_t)p * b + i, atT = 2 * bb + F * bb + (size_t)i * b + p;
+                        limbs[2 * at] = (int32_t)lo;
+                        limbs[2 * at + 1] = (int32_t)hi;
+                        limbs[2 * atT] = (int32_t)lo;
+                        limbs[2 * atT + 1] = (int32_t)hi;
+                        rows[F * b + p] += f;
+                    }
+            int rc0;
+            if ((rc0 = Dn->sep.reserve(sizeof(int32_t) * limbs.size() + sizeof(long long) * rows.size()))) return rc0;
+            d.Bs = (int2 *)Dn->sep.p;
+            d.BsT = d.Bs + 2 * bb;
+            d.Rs = (long long *)(d.BsT + 2 * bb);
+            CK(cudaMemcpyAsync(d.Bs, limbs.data(), sizeof(int32_t) * limbs.size(), cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(d.Rs, rows.data(), sizeof(long long) * rows.size(), cudaMemcpyHostToDevice, st));
+        }
         // W = C H^T with exact structural zeros: entries below 2^-40 are the
         // rounding of an exact zero (e.g. W[p][0] = <C_p, H_0> = 0 for p > 0)
         std::vector<float> w(4 * (size_t)b * b);      // W then W^T, (hi, lo) interleaved
@@ -466,6 +513,21 @@ int get_dict(Ctx *c, int b, int dict_id, cudaStream_t st, Dict **out, bool table
         CK(cudaStreamSynchronize(st));
         D->bf16 = true;
     }
+    if (fp8 && !D->fp8) {
+        DictDev &d = D->d;
+        const int K8 = kpad_fp8(d.n);
+        int rc;
+        if ((rc = D->d8.reserve((size_t)d.Mpad * K8))) return rc;
+        if ((rc = D->s8.reserve(sizeof(float) * 2 * (size_t)d.M))) return rc;
+        d.D8 = (uint8_t *)D->d8.p;
+        d.inv_s8 = (float *)D->s8.p;
+        d.S8 = d.inv_s8 + d.M;
+        CK(build_fp8_tables(d, (const double *)D->basis64.p, d.fam0, st));
+        if ((rc = encode_u8_map(&D->tmap_f8, d.D8, (unsigned long long)d.Mpad, K8, 128))) return rc;
+        d.tmap_fp8 = &D->tmap_f8;
+        CK(cudaStreamSynchronize(st));
+        D->fp8 = true;
+    }
     *out = D;
     return AQMP_OK;
 }
@@ -479,7 +541,8 @@ int check_params(const aqmp_params *p) {
         return fail(AQMP_E_ARG, "block sizes must be powers of two with 4 <= min_block <= max_block");
     if (p->max_block > kMaxSide) return fail(AQMP_E_UNSUPPORTED, "max_block above %d is not built", kMaxSide);
     if (p->dict_id < 0 || p->dict_id > 2) return fail(AQMP_E_DICT, "unknown dictionary id %d", p->dict_id);
-    if (p->precision != AQMP_PREC_EXACT && p->precision != AQMP_PREC_FP32 && p->precision != AQMP_PREC_BF16)
+    if (p->precision != AQMP_PREC_EXACT && p->precision != AQMP_PREC_FP32 && p->precision != AQMP_PREC_BF16 &&
+        p->precision != AQMP_PREC_FP8)
         return fail(AQMP_E_UNSUPPORTED, "unknown precision %d", p->precision);
     return AQMP_OK;
 }
@@ -579,6 +642,7 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
     const bool alt_threads = (P.flags & AQMP_FLAG_ALT_THREADS) != 0;
     const bool omp = (P.flags & AQMP_FLAG_OMP) != 0;
     const bool bf16 = P.precision == AQMP_PREC_BF16;
+    const bool fp8 = P.precision == AQMP_PREC_FP8;
     if (omp) {
         if (P.max_block > 16 || P.precision != AQMP_PREC_EXACT)
             return fail(AQMP_E_UNSUPPORTED, "OMP needs max_block <= 16 and the exact precision");
@@ -610,16 +674,17 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
     const int nlev = ilog2(P.max_block) - ilog2(P.min_block) + 1;
     std::vector<Dict *> dicts(nlev);
     for (int l = 0; l < nlev; ++l)
-        if ((rc = get_dict(c, P.max_block >> l, P.dict_id, st, &dicts[l], !bf16, bf16))) return rc;
+        if ((rc = get_dict(c, P.max_block >> l, P.dict_id, st, &dicts[l], false, bf16, fp8))) return rc;
 
     // capacities
     std::vector<unsigned long long> cap(nlev), qoff(nlev + 1, 0);
-    unsigned long long ymax = 0, cmax = 0, emax = 0;
+    unsigned long long ymax = 0, cmax = 0, emax = 0, y8max = 0;
     for (int l = 0; l < nlev; ++l) {
         const int b = P.max_block >> l;
         cap[l] = npix / ((unsigned long long)b * b);
         qoff[l + 1] = qoff[l] + cap[l];
         ymax = std::max(ymax, cap[l] * dicts[l]->d.Kpad);
+        y8max = std::max(y8max, cap[l] * (unsigned long long)kpad_fp8(dicts[l]->d.n));
         cmax = std::max(cmax, cap[l] * dicts[l]->d.M);
         emax = std::max(emax, cap[l]);
     }
@@ -634,6 +699,10 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
     if ((rc = c->queues.reserve(sizeof(QueueEntry) * qoff[nlev]))) return rc;
     if ((rc = c->Y.reserve(sizeof(__nv_bfloat16) * ymax))) return rc;
     if ((rc = c->e0.reserve(sizeof(uint32_t) * emax))) return rc;
+    if (fp8) {
+        if ((rc = c->Y8.reserve(y8max))) return rc;
+        if ((rc = c->inv_sl.reserve(sizeof(float) * emax))) return rc;
+    }
     if ((rc = c->c0.reserve(sizeof(float2) * cmax))) return rc;
     // the pursuit kernels emit into the workspace; the ordering pass writes
     // the outputs, allocated per call from the stream-ordered pool at their
@@ -706,7 +775,7 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
         if (!tune) return true;
         for (int l = 0; l < nlev; ++l) {
             const int b = P.max_block >> l;
-            if (!simt && !bf16 && b < kCorrTunedMax &&
+            if (!simt && !bf16 && !fp8 && corr_sep_tc_available(b, dicts[l]->d.nf) &&
                 c->tuner.slot(Tuner::CORR, b, P.dict_id, P.precision, cap[l]).chosen < 0)
                 return false;
             if (!alt_threads && !omp && mp_has_variant(b, dicts[l]->d.nf) &&
@@ -758,7 +827,8 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
         lv.next_capacity = lv.is_last ? 0u : (unsigned)cap[l + 1];
 
         GatherArgs ga{b, d.n, d.Kpad, lv.queue, lv.count, lv.capacity, (const PlaneDesc *)c->planes.p,
-                      (__nv_bfloat16 *)c->Y.p, (uint32_t *)c->e0.p};
+                      (__nv_bfloat16 *)c->Y.p, (uint32_t *)c->e0.p, fp8 ? (uint8_t *)c->Y8.p : nullptr,
+                      fp8 ? (float *)c->inv_sl.p : nullptr};
         CK(g_prof.run(kname("gather", b), st, [&] { return launch_gather(ga, c->num_sms, st); }));
 
         CorrArgs ca{};
@@ -769,17 +839,31 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
         ca.capacity = lv.capacity;
         ca.c0 = (float2 *)c->c0.p;
         ca.ctr = ctr;
-        if ((rc = encode_bf16_map(&ymaps[l], c->Y.p, cap[l], d.Kpad, 64))) return rc;
+        if (fp8) {
+            if ((rc = encode_u8_map(&ymaps[l], c->Y8.p, cap[l], kpad_fp8(d.n), 64))) return rc;
+        } else if ((rc = encode_bf16_map(&ymaps[l], c->Y.p, cap[l], d.Kpad, 64))) {
+            return rc;
+        }
         ca.tmap_Y = &ymaps[l];
-        auto corr_tc = [&] { return g_prof.run(kname("corr_tc", b), st, [&] { return launch_corr_tc(ca, st); }); };
-        auto corr_simt = [&] {
-            return g_prof.run(kname("corr_simt", b), st, [&] { return launch_corr_simt(ca, st); });
+        // exact correlation with the separable fixed-point dictionary: on the
+        // tensor cores where a kernel for the side exists, else (and with
+        // AQMP_FLAG_SIMT_GEMM) on the integer SIMT pipes; the two give the
+        // same bits, so the autotuner may time both
+        auto corr_tc = [&] {
+            return g_prof.run(kname("corr_septc", b), st, [&] { return launch_corr_sep_tc(ca, st); });
         };
+        auto corr_simt = [&] {
+            return g_prof.run(kname("corr_sep", b), st, [&] { return launch_corr_sep_simt(ca, st); });
+        };
+        const bool tc_ok = corr_sep_tc_available(b, d.nf);
         if (bf16) {
             CK(g_prof.run(kname("corr_bf16", b), st, [&] { return launch_corr_tc_bf16(ca, st); }));
-        } else if (simt) {
+        } else if (fp8) {
+            CK(g_prof.run(kname("corr_fp8", b), st,
+                          [&] { return launch_corr_tc_fp8(ca, (const float *)c->inv_sl.p, st); }));
+        } else if (simt || !tc_ok) {
             CK(corr_simt());
-        } else if (!tune || b >= kCorrTunedMax) {
+        } else if (!tune) {
             CK(corr_tc());
         } else {
             Tuner::Slot &ts = c->tuner.slot(Tuner::CORR, b, P.dict_id, P.precision, cap[l]);
@@ -1197,6 +1281,9 @@ int aqmp_correlate(int b, int dict_id, const uint8_t *blocks, int64_t L, float *
     if (!is_pow2(b) || b < 4 || b > kMaxSide) return fail(AQMP_E_ARG, "side must be a power of two in [4, %d]", kMaxSide);
     if (dict_id < 0 || dict_id > 2) return fail(AQMP_E_DICT, "unknown dictionary id %d", dict_id);
     if (L < 0 || (L > 0 && (!blocks || !corr))) return fail(AQMP_E_ARG, "bad pointers");
+    if (gemm < 0 || gemm > 5)
+        return fail(AQMP_E_ARG, "gemm must be 0 (separable, best kernel), 1 (separable SIMT), 2 (BF16 form), "
+                                "3 (dense tensor cores), 4 (dense SIMT) or 5 (FP8 form)");
     if (L == 0) return AQMP_OK;
     if (L > 0x7fffffffLL) return fail(AQMP_E_UNSUPPORTED, "too many blocks");
     Ctx *c;
@@ -1204,12 +1291,23 @@ int aqmp_correlate(int b, int dict_id, const uint8_t *blocks, int64_t L, float *
     if ((rc = get_ctx(&c))) return rc;
     std::lock_guard<std::mutex> lock(c->mu);
     cudaStream_t st = (cudaStream_t)stream;
-    if (gemm < 0 || gemm > 2) return fail(AQMP_E_ARG, "gemm must be 0 (tensor cores), 1 (SIMT) or 2 (BF16 form)");
+    const bool dense = gemm == 3 || gemm == 4;
     Dict *D;
-    if ((rc = get_dict(c, b, dict_id, st, &D, gemm != 2, gemm == 2))) return rc;
+    if ((rc = get_dict(c, b, dict_id, st, &D, dense, gemm == 2, gemm == 5))) return rc;
     const DictDev &d = D->d;
-    if ((rc = c->Y.reserve(sizeof(__nv_bfloat16) * (size_t)L * d.Kpad))) return rc;
-    CK(launch_gather_blocks(b, d.Kpad, blocks, L, (__nv_bfloat16 *)c->Y.p, nullptr, c->num_sms, st));
+    CUtensorMap ym;
+    if (gemm == 5) {
+        if ((rc = c->Y8.reserve((size_t)L * kpad_fp8(d.n)))) return rc;
+        if ((rc = c->inv_sl.reserve(sizeof(float) * (size_t)L))) return rc;
+        if ((rc = encode_u8_map(&ym, c->Y8.p, (unsigned long long)L, kpad_fp8(d.n), 64))) return rc;
+        CK(launch_gather_blocks_fp8(b, blocks, L, (uint8_t *)c->Y8.p, (float *)c->inv_sl.p, c->num_sms, st));
+    } else {
+        if ((rc = c->Y.reserve(sizeof(__nv_bfloat16) * (size_t)L * d.Kpad))) return rc;
+        if (gemm != 1 && gemm != 4) {
+            if ((rc = encode_bf16_map(&ym, c->Y.p, (unsigned long long)L, d.Kpad, 64))) return rc;
+        }
+        CK(launch_gather_blocks(b, d.Kpad, blocks, L, (__nv_bfloat16 *)c->Y.p, nullptr, c->num_sms, st));
+    }
     CorrArgs ca{};
     ca.d = &d;
     ca.Y = (const __nv_bfloat16 *)c->Y.p;
@@ -1217,14 +1315,26 @@ int aqmp_correlate(int b, int dict_id, const uint8_t *blocks, int64_t L, float *
     ca.fixed_count = L;
     ca.capacity = (unsigned)L;
     ca.c0 = (float2 *)corr;
-    CUtensorMap ym;
-    if (gemm == 0 || gemm == 2) {
-        if ((rc = encode_bf16_map(&ym, c->Y.p, (unsigned long long)L, d.Kpad, 64))) return rc;
-        ca.tmap_Y = &ym;
-        if (gemm == 0) CK(g_prof.run(kname("corr_tc", b), st, [&] { return launch_corr_tc(ca, st); }));
-        else CK(g_prof.run(kname("corr_bf16", b), st, [&] { return launch_corr_tc_bf16(ca, st); }));
-    } else {
-        CK(g_prof.run(kname("corr_simt", b), st, [&] { return launch_corr_simt(ca, st); }));
+    ca.tmap_Y = &ym;
+    cudaError_t e = cudaSuccess;
+    switch (gemm) {
+        case 0:
+            e = corr_sep_tc_available(b, d.nf)
+                    ? g_prof.run(kname("corr_septc", b), st, [&] { return launch_corr_sep_tc(ca, st); })
+                    : g_prof.run(kname("corr_sep", b), st, [&] { return launch_corr_sep_simt(ca, st); });
+            break;
+        case 1: e = g_prof.run(kname("corr_sep", b), st, [&] { return launch_corr_sep_simt(ca, st); }); break;
+        case 2: e = g_prof.run(kname("corr_bf16", b), st, [&] { return launch_corr_tc_bf16(ca, st); }); break;
+        case 3: e = g_prof.run(kname("corr_tc", b), st, [&] { return launch_corr_tc(ca, st); }); break;
+        case 4: e = g_prof.run(kname("corr_simt", b), st, [&] { return launch_corr_simt(ca, st); }); break;
+        case 5:
+            e = g_prof.run(kname("corr_fp8", b), st,
+                           [&] { return launch_corr_tc_fp8(ca, (const float *)c->inv_sl.p, st); });
+            break;
+    }
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(st);
+        return fail(AQMP_E_CUDA, "correlation kernel: %s", cudaGetErrorString(e));
     }
     CK(cudaStreamSynchronize(st));
     {

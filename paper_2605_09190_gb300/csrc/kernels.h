@@ -52,16 +52,25 @@ struct GatherArgs {
     const PlaneDesc *planes;
     __nv_bfloat16 *Y;            // [capacity][Kpad]
     uint32_t *e0;                // [capacity]
+    uint8_t *Y8;                 // FP8 form: e4m3(y~ s_l) [capacity][kpad_fp8(n)], or NULL
+    float *inv_sl;               // FP8 form: 1 / s_l per leaf
 };
 cudaError_t launch_gather(const GatherArgs &a, int num_sms, cudaStream_t st);
 
 // Same, for L contiguous row-major b x b blocks (aqmp_correlate).
 cudaError_t launch_gather_blocks(int b, int Kpad, const uint8_t *blocks, long long L,
                                  __nv_bfloat16 *Y, uint32_t *e0, int num_sms, cudaStream_t st);
+cudaError_t launch_gather_blocks_fp8(int b, const uint8_t *blocks, long long L, uint8_t *Y8, float *inv_sl,
+                                     int num_sms, cudaStream_t st);
 
 // Fixed-point dictionary tables of one side (tables.cu).
 struct DictDev {
     int b, n, M, Mpad, Kpad, nf;
+    int fam0;                    // family of a single-family dictionary (0 = DCT, 1 = Haar)
+    // separable fixed-point dictionary (sep.cuh), both families always:
+    int2 *Bs;                    // [2][b][b] Bf[F][p][i] as 24-bit limbs (lo, hi)
+    int2 *BsT;                   // [2][b][b] its transpose, BsT[F][m][q] = Bf[F][q][m]
+    long long *Rs;               // [2][b] row sums R[F][p] = sum_i Bf[F][p][i]
     __nv_bfloat16 *limbs;        // [kLimbs][Mpad][Kpad] balanced base-64 digits
     int32_t *Dh, *Dl;            // [M][n]: D_fix = Dh 2^24 + Dl, Dl in [-2^23, 2^23)
     long long *Sh, *Sl;          // per atom: sum_v D_fix = Sh 2^24 + Sl (canonical)
@@ -71,7 +80,16 @@ struct DictDev {
     __nv_bfloat16 *Dbf;          // [Mpad][Kpad] bf16(D) (reduced-precision form; built on demand)
     float *Sbf;                  // [M] row sums of bf16(D)
     void *tmap_bf16;             // CUtensorMap of Dbf (host copy)
+    // FP8 form (built on demand): e4m3(D[j][v] s_j) with a power-of-two scale
+    // per atom, its inverse and the row sums of the dequantised entries
+    uint8_t *D8;                 // [Mpad][K8] e4m3 bytes, K8 = kpad_fp8(n)
+    float *inv_s8;               // [M] 1 / s_j
+    float *S8;                   // [M] sum_v e4m3(D[j][v] s_j) / s_j
+    void *tmap_fp8;              // CUtensorMap of D8 (host copy)
 };
+
+// K padding of the FP8 form: one 128-byte swizzle row holds 128 elements.
+__host__ __device__ inline int kpad_fp8(int n) { return n < 128 ? 128 : (n + 127) / 128 * 128; }
 
 // Initial correlation (corr_simt.cu / corr_tc.cu): c0[l][j] for l < *count.
 struct CorrArgs {
@@ -85,9 +103,19 @@ struct CorrArgs {
     const void *tmap_Y;          // CUtensorMap of Y (tensor-core kernel only)
 };
 cudaError_t launch_corr_simt(const CorrArgs &a, cudaStream_t st);
+// Exact correlation with the separable fixed-point dictionary (corr_sep.cu):
+// B Y B^T per family in integers, T 2^-96 rounded once into a double-float.
+cudaError_t launch_corr_sep_simt(const CorrArgs &a, cudaStream_t st);
+// The same on the tensor cores (corr_sep_tc.cu), bit for bit, at the sides
+// where corr_sep_tc_available() says a kernel exists.
+cudaError_t launch_corr_sep_tc(const CorrArgs &a, cudaStream_t st);
+bool corr_sep_tc_available(int b, int nf);
 cudaError_t launch_corr_tc(const CorrArgs &a, cudaStream_t st);
 // Reduced-precision form: one BF16 pass of bf16(D), FP32 accumulation (c0 low words 0).
 cudaError_t launch_corr_tc_bf16(const CorrArgs &a, cudaStream_t st);
+// FP8 form: one E4M3 pass (kind::f8f6f4) of the per-atom scaled e4m3(D)
+// against the per-leaf scaled e4m3 pixels, FP32 accumulation, rescaled.
+cudaError_t launch_corr_tc_fp8(const CorrArgs &a, const float *inv_sl, cudaStream_t st);
 bool corr_tc_available();
 cudaError_t launch_wait_selftest(Counters *ctr, unsigned long long limit_ns, cudaStream_t st);
 
@@ -174,6 +202,8 @@ cudaError_t launch_color(const ColorArgs &a, bool to_planes, int num_sms, cudaSt
 cudaError_t build_fixed_tables_fam(DictDev &d, const double *basis_dev, int fam0, cudaStream_t st);
 // bf16(D) and its row sums for the reduced-precision form.
 cudaError_t build_bf16_tables(DictDev &d, const double *basis_dev, int fam0, cudaStream_t st);
+// e4m3(D s_j), 1 / s_j and the dequantised row sums for the FP8 form.
+cudaError_t build_fp8_tables(DictDev &d, const double *basis_dev, int fam0, cudaStream_t st);
 // FP32 copy of the FP64 bases (decoder tables).
 cudaError_t launch_basis_to_float(const double *basis_dev, float *out, int count, cudaStream_t st);
 

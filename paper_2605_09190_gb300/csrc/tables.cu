@@ -12,6 +12,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -132,6 +133,55 @@ cudaError_t build_bf16_tables(DictDev &d, const double *basis_dev, int fam0, cud
     if (e != cudaSuccess) return e;
     int sblocks = std::min((d.M + 7) / 8, 4096);
     bf16_sums_kernel<<<sblocks, 256, 0, st>>>(d.n, d.M, d.Kpad, d.Dbf, d.Sbf);
+    return cudaGetLastError();
+}
+
+// FP8 form: one warp per atom finds max_v |D[j][v]|, picks the power of two
+// s_j with max |D| s_j <= 448 (the largest finite E4M3 value), writes
+// e4m3(D[j][v] s_j) (round to nearest, saturating) with zero padding to K8,
+// and the row sum of the dequantised values (FP64, rounded once to FP32).
+__global__ void fp8_table_kernel(int b, int n, int M, int nf, int fam0, const double *basis, int K8, uint8_t *D8,
+                                 float *inv_s, float *S8) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < M; j += warps) {
+        const int fam = nf == 2 ? j / n : fam0;
+        const int f = j - (nf == 2 ? (j / n) * n : 0);
+        const int p = f % b, q = f / b;
+        const double *B = basis + (size_t)fam * b * b;
+        double mx = 0.0;
+        for (int v = lane; v < n; v += 32) mx = fmax(mx, fabs(B[p * b + v % b] * B[q * b + v / b]));
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+        int ex = 0;
+        if (mx > 0.0) ex = (int)floor(log2(448.0 / mx));
+        const double s = ldexp(1.0, ex);
+        double sum = 0.0;
+        for (int v = lane; v < K8; v += 32) {
+            __nv_fp8_storage_t q8 = 0;
+            if (v < n) {
+                const double d = B[p * b + v % b] * B[q * b + v / b];
+                q8 = __nv_cvt_float_to_fp8((float)(d * s), __NV_SATFINITE, __NV_E4M3);
+                __half_raw hr = __nv_cvt_fp8_to_halfraw(q8, __NV_E4M3);
+                sum += (double)__half2float(__half(hr)) / s;
+            }
+            D8[(size_t)j * K8 + v] = q8;
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+        if (lane == 0) {
+            inv_s[j] = (float)(1.0 / s);
+            S8[j] = (float)sum;
+        }
+    }
+}
+
+cudaError_t build_fp8_tables(DictDev &d, const double *basis_dev, int fam0, cudaStream_t st) {
+    const int K8 = kpad_fp8(d.n);
+    cudaError_t e = cudaMemsetAsync(d.D8, 0, (size_t)d.Mpad * K8, st);
+    if (e != cudaSuccess) return e;
+    const int blocks = std::min((d.M + 7) / 8, 8192);
+    fp8_table_kernel<<<blocks, 256, 0, st>>>(d.b, d.n, d.M, d.nf, fam0, basis_dev, K8, d.D8, d.inv_s8, d.S8);
     return cudaGetLastError();
 }
 

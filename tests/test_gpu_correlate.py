@@ -1,5 +1,9 @@
-"""a2 on the GPU: the tcgen05 exact-limb correlation against the integer
-SIMT kernel (bit for bit) and against the FP64 oracle's D^T y."""
+"""a2 on the GPU.  The exact correlation with the separable fixed-point
+dictionary (each 1-D basis row rounded to 2^-48, atoms their outer
+products): the tensor-core and integer SIMT kernels against each other (bit
+for bit) and against the FP64 oracle's D^T y within the bound of that
+fixed-point dictionary.  The dense exact kernels (round(D 2^48) entries)
+likewise, and the reduced-precision BF16 form within its rounding bound."""
 import numpy as np
 import pytest
 
@@ -28,17 +32,61 @@ def _blocks(L, b, seed):
     return x
 
 
-@pytest.mark.parametrize("b,dict_id,L", [(4, 0, 1), (4, 0, 200), (8, 0, 65), (8, 1, 64), (16, 0, 130),
-                                         (16, 2, 7), (32, 0, 70), (64, 0, 66), (64, 1, 3), (128, 0, 5),
-                                         (128, 2, 2)])
-def test_tensor_core_matches_simt_and_fp64(lib, b, dict_id, L):
+CASES = [(4, 0, 1), (4, 0, 200), (8, 0, 65), (8, 1, 64), (16, 0, 130), (16, 2, 7), (32, 0, 70), (64, 0, 66),
+         (64, 1, 3), (128, 0, 5), (128, 2, 2)]
+
+
+def _families(b, dict_id):
+    return {0: [oracle.dct_1d(b), oracle.haar_1d(b)], 1: [oracle.dct_1d(b)], 2: [oracle.haar_1d(b)]}[dict_id]
+
+
+def _separable_bound(b, dict_id, y_block, ref):
+    """|c - D^T y| for the separable fixed-point dictionary: each entry
+    B[p][i] B[q][m] errs by at most 2^-49 (|B[p][i]| + |B[q][m]|) + 2^-97, the
+    result is rounded once into a double-float (2^-47 |c| with margin), and
+    the FP64 reference itself errs by at most n 2^-53 sum_v |phi_j[v] y[v]|."""
+    Y = np.abs(y_block.astype(np.float64))              # Y[i][m]
+    out = []
+    for B in _families(b, dict_id):
+        A = np.abs(B)
+        a = (A @ Y).sum(axis=1)                          # a[p] = sum_{i,m} |B[p][i]| |y[i][m]|
+        c = (Y @ A.T).sum(axis=0)                        # c[q] = sum_{i,m} |y[i][m]| |B[q][m]|
+        out.append((a[None, :] + c[:, None]).reshape(-1))   # atom index q b + p
+    e = 2.0 ** -49 * np.concatenate(out) + 2.0 ** -97 * Y.sum()
+    return e + 2.0 ** -47 * np.abs(ref) + 1e-12
+
+
+@pytest.mark.parametrize("b,dict_id,L", CASES)
+def test_separable_kernels_agree_and_match_fp64(lib, b, dict_id, L):
     host = _blocks(L, b, seed=b * 100 + L + dict_id)
     dev = torch.from_numpy(host).cuda()
-    tc = lib.aqmp_correlate(b, dict_id, dev, gemm=0)
+    best = lib.aqmp_correlate(b, dict_id, dev, gemm=0)
     simt = lib.aqmp_correlate(b, dict_id, dev, gemm=1)
     torch.cuda.synchronize()
-    tc_h, simt_h = tc.cpu().numpy(), simt.cpu().numpy()
+    best_h, simt_h = best.cpu().numpy(), simt.cpu().numpy()
     # both kernels round the same exact integer once: identical bits
+    assert np.array_equal(best_h.view(np.uint32), simt_h.view(np.uint32))
+    D = oracle.dictionary(b, dict_id)
+    Dabs = np.abs(D)
+    for l in range(L):
+        y = oracle.unravel(host[l])
+        ref = D @ y
+        got = best_h[l, :, 0].astype(np.float64) + best_h[l, :, 1].astype(np.float64)
+        bound = _separable_bound(b, dict_id, host[l], ref) + y.size * 2.0 ** -53 * (Dabs @ np.abs(y))
+        assert np.all(np.abs(got - ref) <= bound), (l, np.max(np.abs(got - ref) - bound))
+
+
+@pytest.mark.parametrize("b,dict_id,L", [(4, 0, 200), (8, 1, 64), (16, 0, 130), (64, 0, 9), (128, 2, 2)])
+def test_dense_kernels_agree_and_match_fp64(lib, b, dict_id, L):
+    """The dense exact form (entries round(D 2^48), 8 digit planes on the
+    tensor cores; the allocation-free entry point's kernel) against its
+    integer SIMT twin and the FP64 D^T y."""
+    host = _blocks(L, b, seed=b * 31 + L + dict_id)
+    dev = torch.from_numpy(host).cuda()
+    tc = lib.aqmp_correlate(b, dict_id, dev, gemm=3)
+    simt = lib.aqmp_correlate(b, dict_id, dev, gemm=4)
+    torch.cuda.synchronize()
+    tc_h, simt_h = tc.cpu().numpy(), simt.cpu().numpy()
     assert np.array_equal(tc_h.view(np.uint32), simt_h.view(np.uint32))
     D = oracle.dictionary(b, dict_id)
     Dabs = np.abs(D)
@@ -47,8 +95,7 @@ def test_tensor_core_matches_simt_and_fp64(lib, b, dict_id, L):
         ref = D @ y
         got = tc_h[l, :, 0].astype(np.float64) + tc_h[l, :, 1].astype(np.float64)
         # fixed-point dictionary: |err| <= 2^-49 sum|y| + rounding of the
-        # result; plus the FP64 reference's own summation error, at most
-        # n 2^-53 sum_v |phi_j[v] y[v]| (side 128: K = 16 384 in four chunks)
+        # result; plus the FP64 reference's own summation error
         bound = (2.0 ** -47 * np.sum(np.abs(y)) + 2.0 ** -46 * np.abs(ref) + 1e-12
                  + y.size * 2.0 ** -53 * (Dabs @ np.abs(y)))
         assert np.all(np.abs(got - ref) <= bound), (l, np.max(np.abs(got - ref) - bound))
@@ -76,4 +123,33 @@ def test_bf16_form_is_within_its_rounding_bound(lib, b, dict_id, L):
         assert np.all(err <= bound), (l, float(np.max(err - bound)))
         worst = max(worst, float(np.max(err)))
     # an approximation, not the exact form (a constant block can come out exact)
+    assert worst > 0.0
+
+
+@pytest.mark.parametrize("b,dict_id,L", [(4, 0, 200), (8, 1, 64), (16, 0, 130), (32, 2, 9), (64, 0, 66), (128, 0, 3)])
+def test_fp8_form_is_within_its_rounding_bound(lib, b, dict_id, L):
+    """The FP8 form: e4m3(D s_j) against e4m3(y~ s_l) with power-of-two scales
+    per atom and per block, FP32 accumulation.  An E4M3 value carries 3
+    fraction bits (rounding error at most 2^-4 relative for normal values,
+    2^-10 absolute below 2^-6), so against the FP64 D^T y the error is at
+    most 2^-4 sum|D||y~| (pixels) + (2^-4 + 2^-8) sum|D|(|y~| + 128) (atoms)
+    + the subnormal floor + FP32 accumulation."""
+    host = _blocks(L, b, seed=b * 13 + L + dict_id)
+    dev = torch.from_numpy(host).cuda()
+    got = lib.aqmp_correlate(b, dict_id, dev, gemm=5).cpu().numpy()
+    assert np.all(got[:, :, 1] == 0.0)
+    D = oracle.dictionary(b, dict_id)
+    Dabs = np.abs(D)
+    dmax = Dabs.max(axis=1)                                  # per atom
+    worst = 0.0
+    for l in range(L):
+        y = oracle.unravel(host[l])
+        yc = np.abs(y - 128.0)
+        ref = D @ y
+        bound = (2.0 ** -4 * (Dabs @ yc) + (2.0 ** -4 + 2.0 ** -8) * (Dabs @ (yc + 128.0))
+                 + 2.0 ** -10 * (2.0 * dmax / 448.0) * np.sum(yc + 128.0)
+                 + y.size * 2.0 ** -22 * (Dabs @ (yc + 128.0)) + 1e-4)
+        err = np.abs(got[l, :, 0].astype(np.float64) - ref)
+        assert np.all(err <= bound), (l, float(np.max(err - bound)))
+        worst = max(worst, float(np.max(err)))
     assert worst > 0.0

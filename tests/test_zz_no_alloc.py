@@ -1,9 +1,10 @@
 """aqmp_correlate_noalloc: the correlation for callers that may not allocate
 device memory (memory owned by another allocator or a fixed budget, loops
 that reserve everything at start-up).  It keeps its scratch in static device
-arrays, so its result must equal the allocating entry point's bit for bit,
-call after call, although every call reuses (and overwrites) the same
-arrays.  This file is collected last on purpose."""
+arrays, so its result must equal the allocating entry point's run of the
+same kernel (aqmp_correlate with gemm 3, the dense exact tensor-core
+kernel) bit for bit, call after call, although every call reuses (and
+overwrites) the same arrays.  This file is collected last on purpose."""
 import ctypes
 
 import numpy as np
@@ -40,7 +41,7 @@ def test_noalloc_equals_allocating_entry_point_on_consecutive_calls(lib):
         blocks[0] = 255
         rc, got = _noalloc(lib, b, dict_id, blocks)
         assert rc == 0, lib.load_library().aqmp_last_error()
-        ref = lib.aqmp_correlate(b, dict_id, blocks, gemm=0)
+        ref = lib.aqmp_correlate(b, dict_id, blocks, gemm=3)
         torch.cuda.synchronize()
         assert torch.equal(got.view(torch.int32), ref.view(torch.int32)), (b, dict_id, L)
 
