@@ -1,13 +1,457 @@
-// corr_sep_tc.cu -- the separable exact correlation on the tensor cores.
+// corr_sep_tc.cu -- (a2) the separable exact correlation (sep.cuh) on the
+// 5th-generation tensor cores, side 64: the same exact integer T = B Y B^T
+// per family as the SIMT twin (corr_sep.cu), rounded the same way, so both
+// give identical bits.
+//
+// Digits.  Bf = sum_{s<6} d_s 2^(8s) with balanced digits |d_s| <= 128 (the
+// top one <= 181), all exact BF16 values, as are the centred pixels.
+//   Stage 1 (per leaf and family): Z~^T[m][p] = sum_i y~[i][m] Bf[p][i].
+//     A = [d_2u rows p ; d_2u+1 rows p] (128 rows, K = i) from shared memory,
+//     B = the leaf's pixels (rows m, K = i), one FP32 accumulator per digit
+//     pair u: lane (s parity, p), column m.  |d y~| sums over 64 terms stay
+//     below 2^24: exact.
+//   Z~ (|Z~| < 2^59) is assembled exactly in int64 from the six digit sums
+//   (the two parities meet through shared memory) and split into eight
+//   balanced base-2^8 digits e_t, written into tensor memory as the A operand
+//   of stage 2: tile v holds [e_2v rows p ; e_2v+1 rows p] (K = m).
+//   Stage 2: T~[p][q] = sum_{t,s} 2^(8(t+s)) sum_m e_t[p][m] d_s[q][m].
+//     A = tile v (tensor memory), B = d_s rows q (shared memory, 32 q per
+//     pass), accumulated into column block 2v + s: lane half h of block c
+//     then holds the digit diagonal t + s = c + h, at most four products
+//     of |e d| <= 2^20.5 summed over 64 terms: below 2^22, exact.
+//   The epilogue converts each diagonal (exact FP32 integers) and runs the
+//   base-2^8 Horner scheme in int128, the two lane halves meet through
+//   shared memory, and T = T~ + 128 R[p] R[q] is rounded once into a
+//   double-float (int128_to_df).
+//
+// One CTA per SM (8 warps, all 512 TMEM columns: A tiles 0..127, stage-1
+// accumulators 128..319, stage-2 accumulators 128..511), persistent over the
+// leaves; thread 0 issues the TMA loads and the MMAs, all threads drain.
+// Every wait is bounded by a timer; on expiry the kernel records
+// AQMP_E_TIMEOUT, frees its TMEM and returns.
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cuda_bf16.h>
 
 #include "common.cuh"
 #include "kernels.h"
+#include "sep.cuh"
 
 namespace aqmp {
 
-bool corr_sep_tc_available(int, int) { return false; }
+namespace septc {
 
-cudaError_t launch_corr_sep_tc(const CorrArgs &, cudaStream_t) { return cudaErrorNotSupported; }
+constexpr int kB = 64;                        // block side served here
+constexpr int kThreads = 256;
+constexpr int kTmemCols = 512;
+constexpr int kColA = 0;                      // stage-2 A tiles: 4 x 32 columns
+constexpr int kColD = 128;                    // accumulators
+constexpr int kTileBd = 128 * 128;            // bytes: 128 rows x 128 B (two digits of one family)
+constexpr int kTileY = 64 * 128;              // bytes: 64 rows (m) x 64 BF16 (i)
+constexpr int kOffBd = 0;                     // 6 tiles: (family, digit pair)
+constexpr int kOffY = kOffBd + 6 * kTileBd;   // 2 buffers
+constexpr int kOffX = kOffY + 2 * kTileY;     // exchange: 64 KB
+constexpr int kBytesX = 64 * 1024;
+constexpr int kOffBar = kOffX + kBytesX;      // barriers: Bd, Y[2], MMA
+constexpr int kOffMisc = kOffBar + 8 * 8;
+constexpr int kSmemBytes = kOffMisc + 16 + 1024;
+constexpr unsigned long long kWaitNs = 2000000000ull;
+
+// Stage 1: M = 128, N = 64; stage 2: M = 128, N = 32; BF16 x BF16 -> F32.
+constexpr uint32_t kIdesc1 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(64 >> 3) << 17) |
+                             ((uint32_t)(128 >> 4) << 24);
+constexpr uint32_t kIdesc2 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(32 >> 3) << 17) |
+                             ((uint32_t)(128 >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on the phase of parity `parity`.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (globaltimer() - t0 > kWaitNs) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int c0, int c1) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(dst), "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(bar)
+        : "memory");
+}
+
+// K-major tile, 128-byte rows, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ unsigned long long smem_desc(uint32_t addr) {
+    unsigned long long d = 0;
+    d |= (unsigned long long)((addr & 0x3ffffu) >> 4);
+    d |= (unsigned long long)1 << 16;
+    d |= (unsigned long long)(1024 >> 4) << 32;
+    d |= (unsigned long long)1 << 46;
+    d |= (unsigned long long)2 << 61;
+    return d;
+}
+
+__device__ __forceinline__ void mma_ss(uint32_t d, unsigned long long a, unsigned long long b, uint32_t idesc,
+                                       uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+// A from tensor memory: lane r of the tile is row r, K values packed two per
+// 32-bit column (even K in the low half).
+__device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a_tmem, unsigned long long b, uint32_t idesc,
+                                       uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}"
+        ::"r"(d), "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15, %16};"
+        ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+          "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
+
+__device__ __forceinline__ void wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// An FP32 value holding an integer of magnitude below 2^22, as an int32
+// (the integer lands in the low mantissa bits of x + 1.5 2^23).
+__device__ __forceinline__ int32_t small_int(uint32_t bits) {
+    return __float_as_int(__fadd_rn(__uint_as_float(bits), 12582912.0f)) - 0x4B400000;
+}
+
+// The BF16 bits of a small integer |e| <= 256 (exact: at most 8 significant
+// bits, so the FP32 value's low 16 bits are zero).
+__device__ __forceinline__ uint32_t bf16_bits(int32_t e) {
+    const float f = __fsub_rn(__int_as_float(0x4B400000 + e), 12582912.0f);   // (float)e, exact
+    return __float_as_uint(f) >> 16;
+}
+
+// 128-bit two's complement: (hi, lo) = value.
+struct I128 {
+    unsigned long long lo;
+    long long hi;
+};
+
+// x 2^8 + d for a small signed d.
+__device__ __forceinline__ void horner8(I128 &x, int32_t d) {
+    const unsigned long long lo = x.lo << 8;
+    long long hi = (long long)(((unsigned long long)x.hi << 8) | (x.lo >> 56));
+    const unsigned long long add = (unsigned long long)(long long)d;
+    const unsigned long long s = lo + add;
+    hi += (s < lo ? 1 : 0) + (d < 0 ? -1 : 0);
+    x.lo = s;
+    x.hi = hi;
+}
+
+__device__ __forceinline__ __int128 to_i128(const I128 &x) {
+    return (__int128)(((unsigned __int128)(unsigned long long)x.hi << 64) | x.lo);
+}
+
+}  // namespace septc
+
+// Y map: the gathered leaves viewed as [capacity * 64 rows][64] BF16 (row m of
+// leaf l at row 64 l + m, K = i); Bd map: [6 * 128 rows][64] BF16, tile (F, u)
+// at row 128 (3 F + u).
+__global__ void __launch_bounds__(septc::kThreads, 1)
+corr_sep_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ CUtensorMap tmBd, int nf,
+                   int fam0, const long long *__restrict__ Rs, const unsigned *count_dev, long long fixed_count,
+                   float2 *__restrict__ c0, Counters *ctr) {
+    using namespace septc;
+    constexpr int n = kB * kB;
+    const long long count = count_dev ? (long long)*count_dev : fixed_count;
+    if ((long long)blockIdx.x >= count) return;                  // uniform
+    const int M = nf * n;
+
+    extern __shared__ unsigned char smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t base = (raw + 1023u) & ~1023u;
+    unsigned char *gbase = smem_raw + (base - raw);
+    const uint32_t sBd = base + kOffBd, sY = base + kOffY, sBar = base + kOffBar;
+    const uint32_t barBd = sBar, barY0 = sBar + 8, barY1 = sBar + 16, barMma = sBar + 24;
+    long long *X = reinterpret_cast<long long *>(gbase + kOffX);
+    uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(gbase + kOffMisc);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        mbar_init(barBd, 1);
+        mbar_init(barY0, 1);
+        mbar_init(barY1, 1);
+        mbar_init(barMma, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(tmem_holder)), "r"(kTmemCols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_holder;
+
+    // the six digit tiles once, the first leaf's pixels
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(barBd, 6 * kTileBd);
+        for (int t = 0; t < 6; ++t) tma_load_2d(sBd + t * kTileBd, &tmBd, barBd, 0, 128 * t);
+        mbar_expect_tx(barY0, kTileY);
+        tma_load_2d(sY, &tmY, barY0, 0, (int)(64 * blockIdx.x));
+    }
+    bool ok = __syncthreads_and(mbar_wait(barBd, 0)) != 0;
+
+    // TMEM lane quarter of this warp and the half of the columns it drains
+    const int quarter = warp & 3, colhalf = warp >> 2;
+    const int row = quarter * 32 + lane;                          // TMEM lane = tile row
+    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
+    const int par = row >> 6, p = row & 63;
+    uint32_t mma_phase = 0, y_phase[2] = {0u, 0u};
+    int it = 0;
+    for (long long leaf = blockIdx.x; ok && leaf < count; leaf += gridDim.x, ++it) {
+        const int buf = it & 1;
+        const uint32_t barY = buf ? barY1 : barY0;
+        ok = __syncthreads_and(mbar_wait(barY, y_phase[buf])) != 0;
+        y_phase[buf] ^= 1u;
+        if (!ok) break;
+        // prefetch the next leaf into the other buffer (its last reader
+        // finished with the previous iteration's barriers)
+        if (threadIdx.x == 0 && leaf + gridDim.x < count) {
+            const uint32_t nb = buf ? barY0 : barY1;
+            mbar_expect_tx(nb, kTileY);
+            tma_load_2d(sY + (buf ^ 1) * kTileY, &tmY, nb, 0, (int)(64 * (leaf + gridDim.x)));
+        }
+        const uint32_t yaddr = sY + buf * kTileY;
+        for (int f = 0; f < nf && ok; ++f) {
+            const int F = nf == 2 ? f : fam0;
+            // ---- stage 1: Z~^T[m][p], one accumulator per digit pair u
+            if (threadIdx.x == 0) {
+                fence_after();
+                for (int u = 0; u < 3; ++u) {
+                    const unsigned long long ad = smem_desc(sBd + (3 * F + u) * kTileBd);
+                    const unsigned long long bd = smem_desc(yaddr);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)
+                        mma_ss(tmem + kColD + 64 * u, ad + 2ull * kk, bd + 2ull * kk, kIdesc1, kk > 0 ? 1u : 0u);
+                }
+                mma_commit(barMma);
+            }
+            ok = __syncthreads_and(mbar_wait(barMma, mma_phase)) != 0;
+            mma_phase ^= 1u;
+            if (!ok) break;
+            fence_after();
+            // ---- drain 1: this thread's parity sum Z_par[p][m] for its 32 m
+            // (lane row = (parity, p), columns m = 32 colhalf + j)
+            {
+                uint32_t r0[16], r1[16], r2[16];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint32_t col = kColD + 32 * colhalf + 16 * h;
+                    tmem_ld16(lane_base + col, r0);
+                    tmem_ld16(lane_base + col + 64, r1);
+                    tmem_ld16(lane_base + col + 128, r2);
+                    wait_ld();
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const long long z = (long long)small_int(r0[j]) + (long long)small_int(r1[j]) * 65536ll +
+                                            (long long)small_int(r2[j]) * 4294967296ll;
+                        X[(par * 64 + p) * 64 + 32 * colhalf + 16 * h + j] = z;
+                    }
+                }
+            }
+            __syncthreads();
+            // both parities of Z~[p][m] -> eight balanced digits; this lane keeps
+            // the digits of its own parity (tile v = t / 2, lane half = t mod 2)
+            {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    uint32_t packed[4][8];
+#pragma unroll
+                    for (int j2 = 0; j2 < 8; ++j2) {
+                        int32_t dig[2][4];
+#pragma unroll
+                        for (int e = 0; e < 2; ++e) {
+                            const int m = 32 * colhalf + 16 * h + 2 * j2 + e;
+                            long long z = X[(0 * 64 + p) * 64 + m] + X[(1 * 64 + p) * 64 + m] * 256ll;
+#pragma unroll
+                            for (int t = 0; t < 7; ++t) {
+                                const long long d = ((z + 128) & 255) - 128;
+                                if ((t & 1) == par) dig[e][t >> 1] = (int32_t)d;
+                                z = (z - d) >> 8;
+                            }
+                            if (par == 1) dig[e][3] = (int32_t)z;                     // t = 7
+                        }
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) packed[v][j2] = bf16_bits(dig[0][v]) | (bf16_bits(dig[1][v]) << 16);
+                    }
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        uint32_t w[16];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) w[j] = packed[v][j];
+#pragma unroll
+                        for (int j = 8; j < 16; ++j) w[j] = 0u;
+                        // 8 packed columns (16 values of m) per half
+                        asm volatile(
+                            "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
+                            ::"r"(lane_base + kColA + 32 * v + 16 * colhalf + 8 * h), "r"(w[0]), "r"(w[1]),
+                              "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
+                            : "memory");
+                    }
+                }
+                wait_st();
+            }
+            fence_before();
+            __syncthreads();
+            // ---- stage 2, 32 values of q per pass
+            for (int c = 0; c < 2 && ok; ++c) {
+                if (threadIdx.x == 0) {
+                    fence_after();
+                    uint32_t written = 0u;
+                    for (int v = 0; v < 4; ++v)
+                        for (int s = 0; s < 6; ++s) {
+                            const int cb = 2 * v + s;
+                            const uint32_t btile = sBd + (3 * F + (s >> 1)) * kTileBd + (s & 1) * (64 * 128) +
+                                                   c * (32 * 128);
+                            const unsigned long long bd = smem_desc(btile);
+#pragma unroll
+                            for (int kk = 0; kk < 4; ++kk) {
+                                const uint32_t acc = ((written >> cb) & 1u) | (kk > 0 ? 1u : 0u);
+                                mma_ts(tmem + kColD + 32 * cb, tmem + kColA + 32 * v + 8 * kk, bd + 2ull * kk,
+                                       kIdesc2, acc);
+                            }
+                            written |= 1u << cb;
+                        }
+                    mma_commit(barMma);
+                }
+                ok = __syncthreads_and(mbar_wait(barMma, mma_phase)) != 0;
+                mma_phase ^= 1u;
+                if (!ok) break;
+                fence_after();
+                // ---- drain 2: lane (half hh, p), 16 values of q; block cb holds the
+                // diagonal cb + hh; Horner from the top block down, then the lanes
+                // of the two halves add their partial sums
+                const int hh = par;
+                I128 acc[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) acc[j] = I128{0ull, 0ll};
+                for (int cb = 11; cb >= 0; --cb) {
+                    uint32_t r[16];
+                    tmem_ld16(lane_base + kColD + 32 * cb + 16 * colhalf, r);
+                    wait_ld();
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) horner8(acc[j], small_int(r[j]));
+                }
+                // T_hh = 2^(8 hh) sum_cb D 2^(8 cb): the odd half is one digit up
+                fence_before();
+                __syncthreads();                  // X is free (drain 1 done), D read
+                __int128 *XT = reinterpret_cast<__int128 *>(X);
+                // lanes of half hh finalise q = 16 colhalf + [8 hh, 8 hh + 8); they
+                // hand over the other eight
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    if ((j >> 3) != hh) {
+                        const __int128 t = to_i128(acc[j]) * (hh ? (__int128)256 : (__int128)1);
+                        XT[(size_t)((colhalf * 2 + hh) * 64 + p) * 16 + j] = t;
+                    }
+                }
+                __syncthreads();
+                if (leaf < count) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        if ((j >> 3) == hh) {
+                            const __int128 mine = to_i128(acc[j]) * (hh ? (__int128)256 : (__int128)1);
+                            const __int128 other = XT[(size_t)((colhalf * 2 + 1 - hh) * 64 + p) * 16 + j];
+                            const int q = 32 * c + 16 * colhalf + j;
+                            const __int128 T = mine + other + (__int128)(128ll * Rs[F * kB + p]) * Rs[F * kB + q];
+                            const df v = int128_to_df(T);
+                            c0[leaf * M + (nf == 2 ? f * n : 0) + q * kB + p] = make_float2(v.hi, v.lo);
+                        }
+                    }
+                }
+                fence_before();
+                __syncthreads();
+            }
+        }
+    }
+    fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0 && !ok && ctr) raise_error(ctr, kDevErrTimeout, 12u);
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+}
+
+bool corr_sep_tc_available(int b, int) { return b == septc::kB; }
+
+cudaError_t launch_corr_sep_tc(const CorrArgs &a, cudaStream_t st) {
+    const DictDev &d = *a.d;
+    if (d.b != septc::kB || !d.tmap_sepd || !a.tmap_Ysep) return cudaErrorInvalidValue;
+    const long long rows = a.count ? (long long)a.capacity : a.fixed_count;
+    if (rows <= 0) return cudaSuccess;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    const unsigned grid = (unsigned)(rows < sms ? rows : sms);
+    e = cudaFuncSetAttribute(corr_sep_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, septc::kSmemBytes);
+    if (e != cudaSuccess) return e;
+    corr_sep_tc_kernel<<<grid, septc::kThreads, septc::kSmemBytes, st>>>(
+        *reinterpret_cast<const CUtensorMap *>(a.tmap_Ysep), *reinterpret_cast<const CUtensorMap *>(d.tmap_sepd),
+        d.nf, d.fam0, d.Rs, a.count, a.fixed_count, a.c0, a.ctr);
+    return cudaGetLastError();
+}
 
 }  // namespace aqmp

@@ -305,7 +305,8 @@ struct Tuner {
 
 struct Dict {
     DictDev d{};
-    DeviceBuf limbs, dh, dl, sh, sl, w, basis, basis64, sep;
+    DeviceBuf limbs, dh, dl, sh, sl, w, basis, basis64, sep, sepd;
+    CUtensorMap tmap_sd;
     CUtensorMap tmap;
     bool tables = false;         // fixed-point correlation tables built (16 M n B + 8 M n B)
     DeviceBuf dbf, sbf;          // reduced-precision form: bf16(D) and its row sums
@@ -449,6 +450,28 @@ int get_dict(Ctx *c, int b, int dict_id, cudaStream_t st, Dict **out, bool table
             d.Rs = (long long *)(d.BsT + 2 * bb);
             CK(cudaMemcpyAsync(d.Bs, limbs.data(), sizeof(int32_t) * limbs.size(), cudaMemcpyHostToDevice, st));
             CK(cudaMemcpyAsync(d.Rs, rows.data(), sizeof(long long) * rows.size(), cudaMemcpyHostToDevice, st));
+            if (corr_sep_tc_available(b, d.nf)) {
+                // balanced base-2^8 digits d_s of Bf (s = 0..5) as BF16, in six
+                // 128-row tiles (family F, digit pair u): row r of tile (F, u)
+                // is row r mod b of digit 2u + r / b
+                std::vector<__nv_bfloat16> dg(6 * 2 * bb);
+                for (int F = 0; F < 2; ++F)
+                    for (int r = 0; r < b; ++r)
+                        for (int col = 0; col < b; ++col) {
+                            long long f = std::llrint(std::ldexp(basis[F * bb + (size_t)r * b + col], 48));
+                            for (int sd = 0; sd < 6; ++sd) {
+                                long long dv = sd < 5 ? ((f + 128) & 255) - 128 : f;
+                                f = (f - dv) >> 8;
+                                const int u = sd >> 1, half = sd & 1;
+                                dg[((size_t)(3 * F + u) * 2 * b + half * b + r) * b + col] = __float2bfloat16((float)dv);
+                            }
+                        }
+                if ((rc0 = Dn->sepd.reserve(sizeof(__nv_bfloat16) * dg.size()))) return rc0;
+                d.sepd = (__nv_bfloat16 *)Dn->sepd.p;
+                CK(cudaMemcpyAsync(d.sepd, dg.data(), sizeof(__nv_bfloat16) * dg.size(), cudaMemcpyHostToDevice, st));
+                if ((rc0 = encode_bf16_map(&Dn->tmap_sd, d.sepd, 6ull * 2 * b, b, 128))) return rc0;
+                d.tmap_sepd = &Dn->tmap_sd;
+            }
         }
         // W = C H^T with exact structural zeros: entries below 2^-40 are the
         // rounding of an exact zero (e.g. W[p][0] = <C_p, H_0> = 0 for p > 0)
@@ -806,7 +829,7 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
     CK(launch_seed_roots((const PlaneDesc *)c->planes.p, n_planes, P.max_block, (unsigned)roots, q,
                          &ctr->queue_count[0], st));
 
-    std::vector<CUtensorMap> ymaps(nlev);
+    std::vector<CUtensorMap> ymaps(nlev), ysmaps(nlev);
     for (int l = 0; l < nlev; ++l) {
         const int b = P.max_block >> l;
         const DictDev &d = dicts[l]->d;
@@ -845,6 +868,10 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
             return rc;
         }
         ca.tmap_Y = &ymaps[l];
+        if (!fp8 && !bf16 && corr_sep_tc_available(b, d.nf)) {
+            if ((rc = encode_bf16_map(&ysmaps[l], c->Y.p, cap[l] * (unsigned long long)b, b, b))) return rc;
+            ca.tmap_Ysep = &ysmaps[l];
+        }
         // exact correlation with the separable fixed-point dictionary: on the
         // tensor cores where a kernel for the side exists, else (and with
         // AQMP_FLAG_SIMT_GEMM) on the integer SIMT pipes; the two give the
@@ -1295,7 +1322,7 @@ int aqmp_correlate(int b, int dict_id, const uint8_t *blocks, int64_t L, float *
     Dict *D;
     if ((rc = get_dict(c, b, dict_id, st, &D, dense, gemm == 2, gemm == 5))) return rc;
     const DictDev &d = D->d;
-    CUtensorMap ym;
+    CUtensorMap ym, ysm;
     if (gemm == 5) {
         if ((rc = c->Y8.reserve((size_t)L * kpad_fp8(d.n)))) return rc;
         if ((rc = c->inv_sl.reserve(sizeof(float) * (size_t)L))) return rc;
@@ -1305,6 +1332,9 @@ int aqmp_correlate(int b, int dict_id, const uint8_t *blocks, int64_t L, float *
         if ((rc = c->Y.reserve(sizeof(__nv_bfloat16) * (size_t)L * d.Kpad))) return rc;
         if (gemm != 1 && gemm != 4) {
             if ((rc = encode_bf16_map(&ym, c->Y.p, (unsigned long long)L, d.Kpad, 64))) return rc;
+        }
+        if (gemm == 0 && corr_sep_tc_available(b, d.nf)) {
+            if ((rc = encode_bf16_map(&ysm, c->Y.p, (unsigned long long)L * b, b, b))) return rc;
         }
         CK(launch_gather_blocks(b, d.Kpad, blocks, L, (__nv_bfloat16 *)c->Y.p, nullptr, c->num_sms, st));
     }
@@ -1316,6 +1346,7 @@ int aqmp_correlate(int b, int dict_id, const uint8_t *blocks, int64_t L, float *
     ca.capacity = (unsigned)L;
     ca.c0 = (float2 *)corr;
     ca.tmap_Y = &ym;
+    ca.tmap_Ysep = &ysm;
     cudaError_t e = cudaSuccess;
     switch (gemm) {
         case 0:

@@ -71,6 +71,8 @@ struct DictDev {
     int2 *Bs;                    // [2][b][b] Bf[F][p][i] as 24-bit limbs (lo, hi)
     int2 *BsT;                   // [2][b][b] its transpose, BsT[F][m][q] = Bf[F][q][m]
     long long *Rs;               // [2][b] row sums R[F][p] = sum_i Bf[F][p][i]
+    __nv_bfloat16 *sepd;         // side 64: Bf digits for the tensor cores (corr_sep_tc.cu)
+    void *tmap_sepd;             // its CUtensorMap (host copy)
     __nv_bfloat16 *limbs;        // [kLimbs][Mpad][Kpad] balanced base-64 digits
     int32_t *Dh, *Dl;            // [M][n]: D_fix = Dh 2^24 + Dl, Dl in [-2^23, 2^23)
     long long *Sh, *Sl;          // per atom: sum_v D_fix = Sh 2^24 + Sl (canonical)
@@ -101,6 +103,7 @@ struct CorrArgs {
     float2 *c0;                  // [capacity][M]
     Counters *ctr;               // may be NULL
     const void *tmap_Y;          // CUtensorMap of Y (tensor-core kernel only)
+    const void *tmap_Ysep;       // Y as [capacity b][b] rows (separable tensor-core kernel)
 };
 cudaError_t launch_corr_simt(const CorrArgs &a, cudaStream_t st);
 // Exact correlation with the separable fixed-point dictionary (corr_sep.cu):
