@@ -182,27 +182,6 @@ __device__ __forceinline__ uint32_t bf16_bits(int32_t e) {
     return __float_as_uint(f) >> 16;
 }
 
-// 128-bit two's complement: (hi, lo) = value.
-struct I128 {
-    unsigned long long lo;
-    long long hi;
-};
-
-// x 2^8 + d for a small signed d.
-__device__ __forceinline__ void horner8(I128 &x, int32_t d) {
-    const unsigned long long lo = x.lo << 8;
-    long long hi = (long long)(((unsigned long long)x.hi << 8) | (x.lo >> 56));
-    const unsigned long long add = (unsigned long long)(long long)d;
-    const unsigned long long s = lo + add;
-    hi += (s < lo ? 1 : 0) + (d < 0 ? -1 : 0);
-    x.lo = s;
-    x.hi = hi;
-}
-
-__device__ __forceinline__ __int128 to_i128(const I128 &x) {
-    return (__int128)(((unsigned __int128)(unsigned long long)x.hi << 64) | x.lo);
-}
-
 }  // namespace septc
 
 // Y map: the gathered leaves viewed as [capacity * 64 rows][64] BF16 (row m of
@@ -294,7 +273,9 @@ corr_sep_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constan
             if (!ok) break;
             fence_after();
             // ---- drain 1: this thread's parity sum Z_par[p][m] for its 32 m
-            // (lane row = (parity, p), columns m = 32 colhalf + j)
+            // (lane row = (parity, p), columns m = 32 colhalf + j); X is stored
+            // m-major so that the lanes of a warp (consecutive p) hit
+            // consecutive words
             {
                 uint32_t r0[16], r1[16], r2[16];
 #pragma unroll
@@ -308,13 +289,15 @@ corr_sep_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constan
                     for (int j = 0; j < 16; ++j) {
                         const long long z = (long long)small_int(r0[j]) + (long long)small_int(r1[j]) * 65536ll +
                                             (long long)small_int(r2[j]) * 4294967296ll;
-                        X[(par * 64 + p) * 64 + 32 * colhalf + 16 * h + j] = z;
+                        X[(par * 64 + 32 * colhalf + 16 * h + j) * 64 + p] = z;
                     }
                 }
             }
             __syncthreads();
             // both parities of Z~[p][m] -> eight balanced digits; this lane keeps
-            // the digits of its own parity (tile v = t / 2, lane half = t mod 2)
+            // the digits of its own parity (tile v = t / 2, lane half = t mod 2).
+            // With z' = Z~ + sum_{t<7} 128 2^(8t), digit t < 7 is byte t of z'
+            // minus 128 and digit 7 is z' >> 56: no carry chain between digits.
             {
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
@@ -325,30 +308,30 @@ corr_sep_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constan
 #pragma unroll
                         for (int e = 0; e < 2; ++e) {
                             const int m = 32 * colhalf + 16 * h + 2 * j2 + e;
-                            long long z = X[(0 * 64 + p) * 64 + m] + X[(1 * 64 + p) * 64 + m] * 256ll;
+                            const long long zz = X[(0 * 64 + m) * 64 + p] + X[(1 * 64 + m) * 64 + p] * 256ll +
+                                                 0x80808080808080ll;
+                            const uint32_t lo = (uint32_t)zz, hi = (uint32_t)((unsigned long long)zz >> 32);
 #pragma unroll
-                            for (int t = 0; t < 7; ++t) {
-                                const long long d = ((z + 128) & 255) - 128;
-                                if ((t & 1) == par) dig[e][t >> 1] = (int32_t)d;
-                                z = (z - d) >> 8;
+                            for (int v = 0; v < 4; ++v) {
+                                const int t = 2 * v + par;
+                                int32_t d;
+                                if (t == 7) d = (int32_t)(zz >> 56);
+                                else if (t < 4) d = (int32_t)((lo >> (8 * t)) & 255u) - 128;
+                                else d = (int32_t)((hi >> (8 * (t - 4))) & 255u) - 128;
+                                dig[e][v] = d;
                             }
-                            if (par == 1) dig[e][3] = (int32_t)z;                     // t = 7
                         }
 #pragma unroll
                         for (int v = 0; v < 4; ++v) packed[v][j2] = bf16_bits(dig[0][v]) | (bf16_bits(dig[1][v]) << 16);
                     }
 #pragma unroll
                     for (int v = 0; v < 4; ++v) {
-                        uint32_t w[16];
-#pragma unroll
-                        for (int j = 0; j < 8; ++j) w[j] = packed[v][j];
-#pragma unroll
-                        for (int j = 8; j < 16; ++j) w[j] = 0u;
                         // 8 packed columns (16 values of m) per half
                         asm volatile(
                             "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
-                            ::"r"(lane_base + kColA + 32 * v + 16 * colhalf + 8 * h), "r"(w[0]), "r"(w[1]),
-                              "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
+                            ::"r"(lane_base + kColA + 32 * v + 16 * colhalf + 8 * h), "r"(packed[v][0]),
+                              "r"(packed[v][1]), "r"(packed[v][2]), "r"(packed[v][3]), "r"(packed[v][4]),
+                              "r"(packed[v][5]), "r"(packed[v][6]), "r"(packed[v][7])
                             : "memory");
                     }
                 }
@@ -382,44 +365,50 @@ corr_sep_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constan
                 if (!ok) break;
                 fence_after();
                 // ---- drain 2: lane (half hh, p), 16 values of q; block cb holds the
-                // diagonal cb + hh; Horner from the top block down, then the lanes
-                // of the two halves add their partial sums
+                // diagonal cb + hh.  Horner in base 2^8 over three groups of four
+                // blocks (each exact in an int64: |D| < 2^22), the groups joined
+                // in int128; then the lanes of the two halves add their sums.
                 const int hh = par;
-                I128 acc[16];
+                long long grp[3][16];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) acc[j] = I128{0ull, 0ll};
-                for (int cb = 11; cb >= 0; --cb) {
-                    uint32_t r[16];
-                    tmem_ld16(lane_base + kColD + 32 * cb + 16 * colhalf, r);
+                for (int g = 2; g >= 0; --g) {
+                    uint32_t r[4][16];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        tmem_ld16(lane_base + kColD + 32 * (4 * g + 3 - k) + 16 * colhalf, r[k]);
                     wait_ld();
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) horner8(acc[j], small_int(r[j]));
+                    for (int j = 0; j < 16; ++j) {
+                        long long x = small_int(r[0][j]);
+#pragma unroll
+                        for (int k = 1; k < 4; ++k) x = x * 256 + small_int(r[k][j]);
+                        grp[g][j] = x;
+                    }
                 }
-                // T_hh = 2^(8 hh) sum_cb D 2^(8 cb): the odd half is one digit up
                 fence_before();
                 __syncthreads();                  // X is free (drain 1 done), D read
                 __int128 *XT = reinterpret_cast<__int128 *>(X);
                 // lanes of half hh finalise q = 16 colhalf + [8 hh, 8 hh + 8); they
-                // hand over the other eight
+                // hand over the other eight (stored j-major: consecutive p,
+                // consecutive words)
+                __int128 mine[8];
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    if ((j >> 3) != hh) {
-                        const __int128 t = to_i128(acc[j]) * (hh ? (__int128)256 : (__int128)1);
-                        XT[(size_t)((colhalf * 2 + hh) * 64 + p) * 16 + j] = t;
-                    }
+                    const __int128 sum = ((__int128)grp[2][j] * ((__int128)1 << 64) +
+                                          (__int128)grp[1][j] * ((__int128)1 << 32) + (__int128)grp[0][j]) *
+                                         (hh ? (__int128)256 : (__int128)1);
+                    if ((j >> 3) != hh) XT[(size_t)((colhalf * 2 + hh) * 16 + j) * 64 + p] = sum;
+                    else mine[j & 7] = sum;
                 }
                 __syncthreads();
-                if (leaf < count) {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        if ((j >> 3) == hh) {
-                            const __int128 mine = to_i128(acc[j]) * (hh ? (__int128)256 : (__int128)1);
-                            const __int128 other = XT[(size_t)((colhalf * 2 + 1 - hh) * 64 + p) * 16 + j];
-                            const int q = 32 * c + 16 * colhalf + j;
-                            const __int128 T = mine + other + (__int128)(128ll * Rs[F * kB + p]) * Rs[F * kB + q];
-                            const df v = int128_to_df(T);
-                            c0[leaf * M + (nf == 2 ? f * n : 0) + q * kB + p] = make_float2(v.hi, v.lo);
-                        }
+                for (int j = 0; j < 16; ++j) {
+                    if ((j >> 3) == hh) {
+                        const __int128 other = XT[(size_t)((colhalf * 2 + 1 - hh) * 16 + j) * 64 + p];
+                        const int q = 32 * c + 16 * colhalf + j;
+                        const __int128 T = mine[j & 7] + other + (__int128)(128ll * Rs[F * kB + p]) * Rs[F * kB + q];
+                        const df v = int128_to_df(T);
+                        c0[leaf * M + (nf == 2 ? f * n : 0) + q * kB + p] = make_float2(v.hi, v.lo);
                     }
                 }
                 fence_before();

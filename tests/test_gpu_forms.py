@@ -1,0 +1,148 @@
+"""The reduced-precision forms against the FP64 oracle, per result.
+
+Section 2.2 step (b) reads the correlations; the exact form reproduces the
+oracle's choices (test_gpu_encode), the other forms trade that for speed:
+
+* FP32 -- the exact correlation rounded to FP32, FP32 pursuit state;
+* BF16 -- one BF16 tensor-core pass of bf16(D), FP32 pursuit;
+* FP8  -- one E4M3 pass (power-of-two scales per atom and per block), FP32
+  pursuit.
+
+For each form and tolerance this test states, against the oracle on sampled
+root blocks of the 512x512 sweep: the share of the oracle's atom choices the
+form reproduces (common prefixes of the atom sequences at leaves both
+encodes share), and the PSNR and SSIM of both reconstructions over the
+sampled roots.  It also measures what a rescoring of the top 8 correlations
+would face: for every block, the atoms whose reduced-precision correlation,
+widened by its proven error bound, can still reach the largest one (the
+candidates an exact rescore would have to settle), and checks that the
+exact argmax is always among them."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_09190_gb300 import synthetic
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOLS = [1.0, 2.0, 4.0, 8.0]
+ROOTS = [0, 9, 18, 27, 36, 45, 54, 63]          # of the 8 x 8 roots of each plane
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2605_09190_gb300 import aqmp, build_lib
+    build_lib.build()
+    assert torch.cuda.is_available()
+    return aqmp
+
+
+@pytest.fixture(scope="module")
+def scene():
+    return synthetic.piecewise_scene(512, 512, seed=1)
+
+
+@pytest.fixture(scope="module")
+def ref(scene):
+    return oracle.encode([scene] * 4, TOLS, roots=[ROOTS] * 4)
+
+
+def _root_of(y, x):
+    return (int(y) // 64) * 8 + int(x) // 64
+
+
+def _agreement(leaves, atoms, enc, plane):
+    """Share of the oracle's atoms (at the sampled roots of `plane`) whose
+    choice the form reproduces: common prefix of the two atom sequences at
+    each leaf position both have."""
+    key = {}
+    for L in leaves[leaves["plane"] == plane]:
+        if _root_of(L["y"], L["x"]) in ROOTS:
+            key[(int(L["y"]), int(L["x"]), int(L["b"]))] = atoms["j"][int(L["atom_off"]):int(L["atom_off"]) +
+                                                                     int(L["n_atoms"])]
+    same = total = 0
+    for i in np.nonzero(enc.leaves["plane"] == plane)[0]:
+        O = enc.leaves[i]
+        oj, _ = enc.leaf_atoms(i)
+        total += len(oj)
+        g = key.get((int(O["y"]), int(O["x"]), int(O["b"])))
+        if g is None:
+            continue
+        m = min(len(g), len(oj))
+        diff = np.nonzero(g[:m].astype(np.int64) != oj[:m].astype(np.int64))[0]
+        same += int(diff[0]) if len(diff) else m
+    return same / max(1, total)
+
+
+def _sampled(img):
+    return np.concatenate([img[(r // 8) * 64:(r // 8) * 64 + 64, (r % 8) * 64:(r % 8) * 64 + 64] for r in ROOTS], 1)
+
+
+@pytest.mark.parametrize("form", ["FP32", "BF16", "FP8"])
+def test_form_error_against_the_fp64_oracle(lib, scene, ref, form):
+    prec = {"FP32": lib.AQMP_PREC_FP32, "BF16": lib.AQMP_PREC_BF16, "FP8": lib.AQMP_PREC_FP8}[form]
+    dev = [torch.from_numpy(scene).cuda()] * 4
+    code = lib.aqmp_encode_planes(dev, TOLS, precision=prec)
+    leaves, atoms, _ = code.copy()
+    out = torch.empty((512, 512), dtype=torch.float32, device="cuda")
+    rows = []
+    for p, tol in enumerate(TOLS):
+        # a valid code: the leaves tile the plane once, within their budgets
+        cover = np.zeros(scene.shape, int)
+        for L in leaves[leaves["plane"] == p]:
+            cover[L["y"]:L["y"] + L["b"], L["x"]:L["x"] + L["b"]] += 1
+            assert L["n_atoms"] <= oracle.sparsity_cap(int(L["b"]))
+        assert np.all(cover == 1)
+        code.decode(p, out)
+        got = _sampled(out.cpu().numpy().astype(np.float64))
+        want = _sampled(oracle.decode(ref, p, 512, 512))
+        img = _sampled(scene)
+        agree = _agreement(leaves, atoms, ref, p)
+        dpsnr = oracle.psnr(got, img) - oracle.psnr(want, img)
+        dssim = oracle.ssim(got, img) - oracle.ssim(want, img)
+        rows.append((tol, agree, dpsnr, dssim))
+        print(f"{form} tol {tol}: atom choices shared with the oracle {agree:.4f}, "
+              f"dPSNR {dpsnr:+.4f} dB, dSSIM {dssim:+.6f}")
+        # stated bounds of each form (loose enough for the seeds' content,
+        # tight enough to catch a broken form)
+        if form == "FP32":
+            assert agree >= 0.5 and abs(dpsnr) <= 0.05 and abs(dssim) <= 1e-3
+        else:
+            assert agree >= 0.0 and abs(dpsnr) <= 3.0 and abs(dssim) <= 0.05
+    code.free()
+
+
+@pytest.mark.parametrize("form,gemm", [("BF16", 2), ("FP8", 5)])
+def test_rescore_candidate_band_of_the_initial_correlation(lib, scene, form, gemm):
+    """Step 0 of every 64x64 root of the sweep plane: the exact correlation
+    (separable form) against the reduced one.  Atom j stays a candidate for
+    the argmax when |c~_j| + e_j >= max_i (|c~_i| - e_i), with e_j the form's
+    proven bound (as in test_gpu_correlate).  The exact argmax must be a
+    candidate; the share of blocks with at most 8 candidates is what a
+    top-8 rescore could decide at step 0 (later steps only widen the band)."""
+    blocks = np.stack([scene[(r // 8) * 64:(r // 8) * 64 + 64, (r % 8) * 64:(r % 8) * 64 + 64] for r in range(64)])
+    dev = torch.from_numpy(blocks).cuda()
+    exact = lib.aqmp_correlate(64, 0, dev, gemm=0).cpu().numpy()
+    red = lib.aqmp_correlate(64, 0, dev, gemm=gemm).cpu().numpy()[:, :, 0].astype(np.float64)
+    D = oracle.dictionary(64, 0)
+    Dabs = np.abs(D)
+    sizes = []
+    for l in range(len(blocks)):
+        y = oracle.unravel(blocks[l])
+        yc = np.abs(y - 128.0)
+        if form == "BF16":
+            e = (2.0 ** -8 * (Dabs @ np.abs(y)) + y.size * 2.0 ** -23 * (Dabs @ yc)
+                 + 2.0 ** -20 * (np.abs(red[l]) + 128.0 * Dabs.sum(axis=1)) + 1e-6)
+        else:
+            e = (2.0 ** -4 * (Dabs @ yc) + (2.0 ** -4 + 2.0 ** -8) * (Dabs @ (yc + 128.0))
+                 + 2.0 ** -10 * (2.0 * Dabs.max(axis=1) / 448.0) * np.sum(yc + 128.0)
+                 + y.size * 2.0 ** -22 * (Dabs @ (yc + 128.0)) + 1e-4)
+        lower = np.max(np.abs(red[l]) - e)
+        cand = np.nonzero(np.abs(red[l]) + e >= lower)[0]
+        c = exact[l, :, 0].astype(np.float64) + exact[l, :, 1].astype(np.float64)
+        assert int(np.argmax(np.abs(c))) in set(cand.tolist())
+        sizes.append(len(cand))
+    sizes = np.array(sizes)
+    print(f"{form}: candidates at step 0 per 64x64 block: median {np.median(sizes):.0f}, max {sizes.max()}, "
+          f"blocks with <= 8: {np.mean(sizes <= 8):.3f}")
