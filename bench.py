@@ -748,7 +748,7 @@ def run_omp(args):
 
 PRECISION_ROOT = 128
 PRECISION_WORKLOAD = ("one 4096x4096 RGB synthetic image (piecewise scene per channel, seeds 0..2), RMSE tol 2, "
-                      "quadtree 128->4, k=b^2/4, DCT-II+Haar: exact form vs plain FP32 form vs BF16 form")
+                      "quadtree 128->4, k=b^2/4, DCT-II+Haar: exact form vs plain FP32, BF16 and FP8 forms")
 
 
 def run_precision(args):
@@ -766,7 +766,8 @@ def run_precision(args):
     planes = [torch.from_numpy(synthetic.piecewise_scene(n, n, seed=rank * 3 + c)).cuda() for c in range(3)]
     npix = 3 * n * n
     stream = torch.cuda.current_stream()
-    forms = {"exact": aqmp.AQMP_PREC_EXACT, "fp32": aqmp.AQMP_PREC_FP32, "bf16": aqmp.AQMP_PREC_BF16}
+    forms = {"exact": aqmp.AQMP_PREC_EXACT, "fp32": aqmp.AQMP_PREC_FP32, "bf16": aqmp.AQMP_PREC_BF16,
+             "fp8": aqmp.AQMP_PREC_FP8}
     out = {}
     with ClockSampler(local) as clocks:
         for name, prec in forms.items():
@@ -839,6 +840,10 @@ def run_precision(args):
                                         "unit": "MP/s", "leaves": agree["bf16"][0],
                                         "same_leaves_share": agree["bf16"][1],
                                         "same_atom_choices_share": agree["bf16"][2]},
+                          "fp8_form": {"value": weak_scaling_value(npix, args.steps, out["fp8"]["s"], world),
+                                       "unit": "MP/s", "leaves": agree["fp8"][0],
+                                       "same_leaves_share": agree["fp8"][1],
+                                       "same_atom_choices_share": agree["fp8"][2]},
                           "leaves": {"exact": len(le), "fp32": agree["fp32"][0]},
                           "per_level": {f"b{(args.root or PRECISION_ROOT) >> i}": {
                               "attempts": out["exact"]["stats"]["attempts_per_level"][i],

@@ -24,7 +24,7 @@
 //   shared memory, and T = T~ + 128 R[p] R[q] is rounded once into a
 //   double-float (int128_to_df).
 //
-// One CTA per SM (8 warps, all 512 TMEM columns: A tiles 0..127, stage-1
+// One CTA per SM (16 warps, all 512 TMEM columns: A tiles 0..127, stage-1
 // accumulators 128..319, stage-2 accumulators 128..511), persistent over the
 // leaves; thread 0 issues the TMA loads and the MMAs, all threads drain.
 // Every wait is bounded by a timer; on expiry the kernel records
@@ -42,7 +42,8 @@ namespace aqmp {
 namespace septc {
 
 constexpr int kB = 64;                        // block side served here
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;                 // 16 warps: 4 per TMEM lane quarter
+constexpr int kGroups = kThreads / 128;       // column groups per lane quarter
 constexpr int kTmemCols = 512;
 constexpr int kColA = 0;                      // stage-2 A tiles: 4 x 32 columns
 constexpr int kColD = 128;                    // accumulators
@@ -233,8 +234,8 @@ corr_sep_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constan
     }
     bool ok = __syncthreads_and(mbar_wait(barBd, 0)) != 0;
 
-    // TMEM lane quarter of this warp and the half of the columns it drains
-    const int quarter = warp & 3, colhalf = warp >> 2;
+    // TMEM lane quarter of this warp and the column group it drains
+    const int quarter = warp & 3, cg = warp >> 2;
     const int row = quarter * 32 + lane;                          // TMEM lane = tile row
     const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
     const int par = row >> 6, p = row & 63;
@@ -272,25 +273,22 @@ corr_sep_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constan
             mma_phase ^= 1u;
             if (!ok) break;
             fence_after();
-            // ---- drain 1: this thread's parity sum Z_par[p][m] for its 32 m
-            // (lane row = (parity, p), columns m = 32 colhalf + j); X is stored
+            // ---- drain 1: this thread's parity sum Z_par[p][m] for its 16 m
+            // (lane row = (parity, p), columns m = 16 cg + j); X is stored
             // m-major so that the lanes of a warp (consecutive p) hit
             // consecutive words
             {
                 uint32_t r0[16], r1[16], r2[16];
+                const uint32_t col = kColD + 16 * cg;
+                tmem_ld16(lane_base + col, r0);
+                tmem_ld16(lane_base + col + 64, r1);
+                tmem_ld16(lane_base + col + 128, r2);
+                wait_ld();
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const uint32_t col = kColD + 32 * colhalf + 16 * h;
-                    tmem_ld16(lane_base + col, r0);
-                    tmem_ld16(lane_base + col + 64, r1);
-                    tmem_ld16(lane_base + col + 128, r2);
-                    wait_ld();
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const long long z = (long long)small_int(r0[j]) + (long long)small_int(r1[j]) * 65536ll +
-                                            (long long)small_int(r2[j]) * 4294967296ll;
-                        X[(par * 64 + 32 * colhalf + 16 * h + j) * 64 + p] = z;
-                    }
+                for (int j = 0; j < 16; ++j) {
+                    const long long z = (long long)small_int(r0[j]) + (long long)small_int(r1[j]) * 65536ll +
+                                        (long long)small_int(r2[j]) * 4294967296ll;
+                    X[(par * 64 + 16 * cg + j) * 64 + p] = z;
                 }
             }
             __syncthreads();
@@ -299,41 +297,38 @@ corr_sep_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constan
             // With z' = Z~ + sum_{t<7} 128 2^(8t), digit t < 7 is byte t of z'
             // minus 128 and digit 7 is z' >> 56: no carry chain between digits.
             {
+                uint32_t packed[4][8];
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    uint32_t packed[4][8];
+                for (int j2 = 0; j2 < 8; ++j2) {
+                    int32_t dig[2][4];
 #pragma unroll
-                    for (int j2 = 0; j2 < 8; ++j2) {
-                        int32_t dig[2][4];
+                    for (int e = 0; e < 2; ++e) {
+                        const int m = 16 * cg + 2 * j2 + e;
+                        const long long zz = X[(0 * 64 + m) * 64 + p] + X[(1 * 64 + m) * 64 + p] * 256ll +
+                                             0x80808080808080ll;
+                        const uint32_t lo = (uint32_t)zz, hi = (uint32_t)((unsigned long long)zz >> 32);
 #pragma unroll
-                        for (int e = 0; e < 2; ++e) {
-                            const int m = 32 * colhalf + 16 * h + 2 * j2 + e;
-                            const long long zz = X[(0 * 64 + m) * 64 + p] + X[(1 * 64 + m) * 64 + p] * 256ll +
-                                                 0x80808080808080ll;
-                            const uint32_t lo = (uint32_t)zz, hi = (uint32_t)((unsigned long long)zz >> 32);
-#pragma unroll
-                            for (int v = 0; v < 4; ++v) {
-                                const int t = 2 * v + par;
-                                int32_t d;
-                                if (t == 7) d = (int32_t)(zz >> 56);
-                                else if (t < 4) d = (int32_t)((lo >> (8 * t)) & 255u) - 128;
-                                else d = (int32_t)((hi >> (8 * (t - 4))) & 255u) - 128;
-                                dig[e][v] = d;
-                            }
+                        for (int v = 0; v < 4; ++v) {
+                            const int t = 2 * v + par;
+                            int32_t d;
+                            if (t == 7) d = (int32_t)(zz >> 56);
+                            else if (t < 4) d = (int32_t)((lo >> (8 * t)) & 255u) - 128;
+                            else d = (int32_t)((hi >> (8 * (t - 4))) & 255u) - 128;
+                            dig[e][v] = d;
                         }
-#pragma unroll
-                        for (int v = 0; v < 4; ++v) packed[v][j2] = bf16_bits(dig[0][v]) | (bf16_bits(dig[1][v]) << 16);
                     }
 #pragma unroll
-                    for (int v = 0; v < 4; ++v) {
-                        // 8 packed columns (16 values of m) per half
-                        asm volatile(
-                            "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
-                            ::"r"(lane_base + kColA + 32 * v + 16 * colhalf + 8 * h), "r"(packed[v][0]),
-                              "r"(packed[v][1]), "r"(packed[v][2]), "r"(packed[v][3]), "r"(packed[v][4]),
-                              "r"(packed[v][5]), "r"(packed[v][6]), "r"(packed[v][7])
-                            : "memory");
-                    }
+                    for (int v = 0; v < 4; ++v) packed[v][j2] = bf16_bits(dig[0][v]) | (bf16_bits(dig[1][v]) << 16);
+                }
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    // 8 packed columns (16 values of m)
+                    asm volatile(
+                        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};"
+                        ::"r"(lane_base + kColA + 32 * v + 8 * cg), "r"(packed[v][0]), "r"(packed[v][1]),
+                          "r"(packed[v][2]), "r"(packed[v][3]), "r"(packed[v][4]), "r"(packed[v][5]),
+                          "r"(packed[v][6]), "r"(packed[v][7])
+                        : "memory");
                 }
                 wait_st();
             }
@@ -364,21 +359,27 @@ corr_sep_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constan
                 mma_phase ^= 1u;
                 if (!ok) break;
                 fence_after();
-                // ---- drain 2: lane (half hh, p), 16 values of q; block cb holds the
+                // ---- drain 2: lane (half hh, p), 8 values of q; block cb holds the
                 // diagonal cb + hh.  Horner in base 2^8 over three groups of four
                 // blocks (each exact in an int64: |D| < 2^22), the groups joined
                 // in int128; then the lanes of the two halves add their sums.
                 const int hh = par;
-                long long grp[3][16];
+                long long grp[3][8];
 #pragma unroll
                 for (int g = 2; g >= 0; --g) {
-                    uint32_t r[4][16];
+                    uint32_t r[4][8];
 #pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        tmem_ld16(lane_base + kColD + 32 * (4 * g + 3 - k) + 16 * colhalf, r[k]);
+                    for (int k = 0; k < 4; ++k) {
+                        const uint32_t ta = lane_base + kColD + 32 * (4 * g + 3 - k) + 8 * cg;
+                        asm volatile(
+                            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                            : "=r"(r[k][0]), "=r"(r[k][1]), "=r"(r[k][2]), "=r"(r[k][3]), "=r"(r[k][4]),
+                              "=r"(r[k][5]), "=r"(r[k][6]), "=r"(r[k][7])
+                            : "r"(ta));
+                    }
                     wait_ld();
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
+                    for (int j = 0; j < 8; ++j) {
                         long long x = small_int(r[0][j]);
 #pragma unroll
                         for (int k = 1; k < 4; ++k) x = x * 256 + small_int(r[k][j]);
@@ -388,25 +389,25 @@ corr_sep_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constan
                 fence_before();
                 __syncthreads();                  // X is free (drain 1 done), D read
                 __int128 *XT = reinterpret_cast<__int128 *>(X);
-                // lanes of half hh finalise q = 16 colhalf + [8 hh, 8 hh + 8); they
-                // hand over the other eight (stored j-major: consecutive p,
+                // lanes of half hh finalise q = 8 cg + [4 hh, 4 hh + 4) of the pass;
+                // they hand over the other four (stored j-major: consecutive p,
                 // consecutive words)
-                __int128 mine[8];
+                __int128 mine[4];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
+                for (int j = 0; j < 8; ++j) {
                     const __int128 sum = ((__int128)grp[2][j] * ((__int128)1 << 64) +
                                           (__int128)grp[1][j] * ((__int128)1 << 32) + (__int128)grp[0][j]) *
                                          (hh ? (__int128)256 : (__int128)1);
-                    if ((j >> 3) != hh) XT[(size_t)((colhalf * 2 + hh) * 16 + j) * 64 + p] = sum;
-                    else mine[j & 7] = sum;
+                    if ((j >> 2) != hh) XT[(size_t)((cg * 2 + hh) * 8 + j) * 64 + p] = sum;
+                    else mine[j & 3] = sum;
                 }
                 __syncthreads();
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    if ((j >> 3) == hh) {
-                        const __int128 other = XT[(size_t)((colhalf * 2 + 1 - hh) * 16 + j) * 64 + p];
-                        const int q = 32 * c + 16 * colhalf + j;
-                        const __int128 T = mine[j & 7] + other + (__int128)(128ll * Rs[F * kB + p]) * Rs[F * kB + q];
+                for (int j = 0; j < 8; ++j) {
+                    if ((j >> 2) == hh) {
+                        const __int128 other = XT[(size_t)((cg * 2 + 1 - hh) * 8 + j) * 64 + p];
+                        const int q = 32 * c + 8 * cg + j;
+                        const __int128 T = mine[j & 3] + other + (__int128)(128ll * Rs[F * kB + p]) * Rs[F * kB + q];
                         const df v = int128_to_df(T);
                         c0[leaf * M + (nf == 2 ? f * n : 0) + q * kB + p] = make_float2(v.hi, v.lo);
                     }
