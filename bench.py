@@ -61,16 +61,17 @@ WORKLOADS = {
 
 # ------------------------------------------------------------- workloads
 
-def workload_planes(name: str, rank: int = 0, world: int = 1):
+def workload_planes(name: str, rank: int = 0, world: int = 1, images: int = IMAGES_PER_RANK):
     """This rank's planes (2-D uint8 numpy arrays), their tolerances, the
     pieces of the global workload they are (see ``shard.partition``) and the
-    global plane shapes."""
+    global plane shapes; `images` per rank for the uneven batches (a smaller
+    batch serves profiler captures)."""
     from paper_2605_09190_gb300 import shard, synthetic
     if name == "sweep512":
         img = synthetic.piecewise_scene(512, 512, seed=1)
         return [img] * len(SWEEP_TOLS), list(SWEEP_TOLS), None, None
     scene = synthetic.gradient_scene if name == "uneven64" else synthetic.piecewise_scene
-    n_img = IMAGES_PER_RANK * world
+    n_img = images * world
     sizes = synthetic.uneven_sizes(n_img, seed=0)
     shapes = [hw for hw in sizes for _ in range(3)]
     pieces = shard.partition(shapes, MAX_BLOCK, world)[rank]
@@ -283,16 +284,24 @@ def roofline(name, launches, total_ms, stats_sum, peaks, peak_kind, sm_mhz, max_
             r["latency"] = lat
     elif kind.startswith("corr"):
         sep = kind.startswith("corr_sep")
-        flops = (8.0 * b ** 3 if sep else 4.0 * n * n) * attempts
+        flops = 4.0 * n * n * attempts                       # the dense GEMM's 4 n^2 per leaf
         peak = peaks.get("bf16_tflops", 1900.0)
         ach = flops / per_launch_s / 1e12
         kpad = max(64, (n + 63) // 64 * 64)
-        alg_bytes = (0 if sep else 2.0 * M * n) + attempts * (2.0 * kpad + 8.0 * M)
+        alg_bytes = 2.0 * M * n + attempts * (2.0 * kpad + 8.0 * M)
         r.update({"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                   "peak_source": f"bf16_tflops ({peak_kind})",
-                  "work": ("8 b^3 flops per leaf (B Y B^T for both families)" if sep
-                           else "4 n^2 flops per leaf (dense D^T y for M = 2n atoms)"),
+                  "work": "4 n^2 flops per leaf (SURVEY 8d count: dense D^T y for M = 2n atoms)",
                   "leaves_per_launch": attempts, "algorithmic_bytes": alg_bytes})
+        if sep:
+            # the separable kernels' own algorithmic work (B Y B^T, both
+            # families) and, on the tensor cores, the digit products issued
+            r["separable_flops_per_leaf"] = 8.0 * b ** 3
+            r["frac_separable_count"] = 8.0 * b ** 3 * attempts / per_launch_s / 1e12 / peak
+            if kind.startswith("corr_septc"):
+                issued = 2 * (3 * 4 * 2 * 128 * 64 * 16 + 2 * 96 * 2 * 128 * 32 * 16)
+                r["tensor_flops_issued_per_leaf"] = issued
+                r["tensor_pipe_frac"] = issued * attempts / per_launch_s / 1e12 / peak
     else:
         kpad = max(64, (n + 63) // 64 * 64)
         byts = attempts * (n + 2 * kpad + 4)
@@ -522,7 +531,7 @@ def run_ours(args):
         gloo = dist.new_group(backend="gloo")          # host-side gather of the records
     build_lib.build()
     aqmp.load_library()
-    planes, tols, pieces, _ = workload_planes(name, rank, world)
+    planes, tols, pieces, _ = workload_planes(name, rank, world, args.images)
     dev = [torch.from_numpy(np.ascontiguousarray(p)).cuda() for p in planes]
     npix = int(sum(p.size for p in planes))
     total_px = int(sum_over_ranks(npix, device="cuda"))
@@ -662,12 +671,14 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "int64/int128 separable correlation (bf16 digits on the tensor cores) + f32x2 pursuit",
                 "data": "synthetic",
-                "config": {"workload": WORKLOADS[name], "name": name, "planes_per_rank": len(planes),
+                "config": {"workload": WORKLOADS[name] if args.images == IMAGES_PER_RANK or name == "sweep512"
+                           else f"{WORKLOADS[name]} [reduced to {args.images} images per rank]",
+                           "name": name, "planes_per_rank": len(planes),
                            "pixels_per_step": total_px, "input": "device-resident",
                            "l2": ("flushed between steps (256 MB write)" if small
                                   else f"inputs ({npix / 1e6:.0f} MB per rank) exceed L2 (129 MB)"),
                            "parallelism": (f"sharded x{world}: contiguous (plane, root row) ranges of a "
-                                           f"{IMAGES_PER_RANK * world}-image batch, records gathered at the end"
+                                           f"{args.images * world}-image batch, records gathered at the end"
                                            if pieces is not None and world > 1 else
                                            ("single GPU" if world == 1 else f"independent replicas x{world}"))},
                 "atom_iterations_per_s": iters_per_s,
@@ -876,6 +887,8 @@ def main():
                          "refinement on 16 images (steps = Adam steps); omp512: the sweep's planes with 16x16 "
                          "roots, Orthogonal Matching Pursuit; precision4096: one 4096x4096 RGB image, the "
                          "exact form against the FP32 and BF16 forms")
+    ap.add_argument("--images", type=int, default=IMAGES_PER_RANK,
+                    help="uneven64 workloads only: images per rank (64; fewer for profiler captures)")
     ap.add_argument("--root", type=int, default=0,
                     help="precision4096 only: root block side (default 128; 64 for comparison)")
     args = ap.parse_args()

@@ -1,0 +1,71 @@
+"""What a top-8 rescore of a BF16 correlation could certify, measured on the
+oracle's own pursuits (CPU).
+
+A reduced-precision form computes the initial correlations c~0 = D^T y with
+a per-atom error of at most e_j (BF16 entries of D: 2^-8 sum_v |phi_j[v] y[v]|
+plus FP32 accumulation, the bound of test_gpu_correlate).  Were the later
+updates exact, every later correlation would carry the same error, so at
+step t the atoms that can still be the argmax are those with
+|c_j(t)| + 2 e_j >= max_i |c_i(t)|: the band a rescore has to settle
+exactly.  With at most 8 in the band a top-8 rescore decides the step; with
+more it must fall back.  The FP32 state error of a real reduced form only
+widens the band, so the share measured here is an upper bound on what the
+rescore could certify.
+
+The residual of each step is formed from the oracle's atom list and its
+correlations by the separable transform (C R C^T and H R H^T)."""
+import numpy as np
+
+import oracle
+from paper_2605_09190_gb300 import synthetic
+
+B = 64
+ROOTS = [0, 45]
+
+
+def _band_sizes(block, tol):
+    C, H = oracle.dct_1d(B), oracle.haar_1d(B)
+    enc = oracle.encode([block], [tol], min_block=B, max_block=B)
+    aj, aa = enc.leaf_atoms(0)
+    y = block.astype(np.float64)                         # y[i][m]
+    D = oracle.dictionary(B, 0)
+    yv = oracle.unravel(block)
+    Dabs = np.abs(D)
+    e = (2.0 ** -8 * (Dabs @ np.abs(yv)) + yv.size * 2.0 ** -23 * (Dabs @ np.abs(yv - 128.0))
+         + 2.0 ** -20 * 128.0 * Dabs.sum(axis=1))
+    R = y.copy()
+    sizes = []
+    for t in range(len(aj)):
+        c = np.concatenate([(C @ R @ C.T).T.reshape(-1), (H @ R @ H.T).T.reshape(-1)])   # index q b + p
+        a = np.abs(c)
+        sizes.append(int(np.sum(a + 2.0 * e >= a.max())))
+        j, alpha = int(aj[t]), float(aa[t])
+        Bm = C if j < B * B else H
+        f = j % (B * B)
+        p, q = f % B, f // B
+        R -= alpha * np.outer(Bm[p], Bm[q])
+    return np.array(sizes)
+
+
+def test_bf16_rescore_band_along_the_oracle_pursuits():
+    img = synthetic.piecewise_scene(512, 512, seed=1)
+    report = {}
+    for tol in (2.0, 8.0):
+        all_sizes, first_over = [], []
+        for r in ROOTS:
+            blk = img[(r // 8) * 64:(r // 8) * 64 + 64, (r % 8) * 64:(r % 8) * 64 + 64]
+            s = _band_sizes(blk, tol)
+            if len(s) == 0:
+                continue
+            all_sizes.append(s)
+            over = np.nonzero(s > 8)[0]
+            first_over.append(int(over[0]) if len(over) else len(s))
+            # step 0: the constant atom and its Haar twin dominate every block
+            assert s[0] <= 8
+        cat = np.concatenate(all_sizes)
+        report[tol] = (float(np.mean(cat <= 8)), int(np.median(first_over)), int(cat.max()))
+        print(f"tol {tol}: steps with <= 8 candidates {report[tol][0]:.3f}, median first step over 8 "
+              f"{report[tol][1]}, largest band {report[tol][2]}")
+    # the band grows past 8 within every pursuit that runs long: a top-8
+    # rescore cannot certify the late steps of these blocks
+    assert min(v[0] for v in report.values()) < 1.0
