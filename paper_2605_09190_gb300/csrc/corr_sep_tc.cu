@@ -176,6 +176,15 @@ __device__ __forceinline__ int32_t small_int(uint32_t bits) {
     return __float_as_int(__fadd_rn(__uint_as_float(bits), 12582912.0f)) - 0x4B400000;
 }
 
+// a 2^8 + b for two FP32 values holding integers of magnitude below 2^22:
+// their biased bit patterns (x + 1.5 2^23) combined in 32-bit arithmetic,
+// the bias removed once; exact as |a 2^8 + b| < 2^31.
+__device__ __forceinline__ int32_t pair8(uint32_t a_bits, uint32_t b_bits) {
+    const uint32_t ab = (uint32_t)__float_as_int(__fadd_rn(__uint_as_float(a_bits), 12582912.0f));
+    const uint32_t bb = (uint32_t)__float_as_int(__fadd_rn(__uint_as_float(b_bits), 12582912.0f));
+    return (int32_t)(ab * 256u + bb - 257u * 0x4B400000u);
+}
+
 // The BF16 bits of a small integer |e| <= 256 (exact: at most 8 significant
 // bits, so the FP32 value's low 16 bits are zero).
 __device__ __forceinline__ uint32_t bf16_bits(int32_t e) {
@@ -355,6 +364,11 @@ corr_sep_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constan
                         }
                     mma_commit(barMma);
                 }
+                // the row sums this lane's outputs need, fetched while the MMAs run
+                const long long rowsum_p = Rs[F * kB + p];
+                long long rowsum_q[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) rowsum_q[j] = Rs[F * kB + 32 * c + 8 * cg + 4 * par + j];
                 ok = __syncthreads_and(mbar_wait(barMma, mma_phase)) != 0;
                 mma_phase ^= 1u;
                 if (!ok) break;
@@ -380,10 +394,13 @@ corr_sep_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constan
                     wait_ld();
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
-                        long long x = small_int(r[0][j]);
-#pragma unroll
-                        for (int k = 1; k < 4; ++k) x = x * 256 + small_int(r[k][j]);
-                        grp[g][j] = x;
+                        // r[k] holds block 4g + 3 - k: two adjacent diagonals meet in
+                        // one 32-bit multiply-add on their biased bit patterns (the
+                        // bias cancels modulo 2^32 and |pair| < 2^31), two pairs in
+                        // one 64-bit multiply-add
+                        const int32_t hi2 = pair8(r[0][j], r[1][j]);        // blocks 4g+3, 4g+2
+                        const int32_t lo2 = pair8(r[2][j], r[3][j]);        // blocks 4g+1, 4g
+                        grp[g][j] = (long long)hi2 * 65536ll + (long long)lo2;
                     }
                 }
                 fence_before();
@@ -402,12 +419,13 @@ corr_sep_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constan
                     else mine[j & 3] = sum;
                 }
                 __syncthreads();
+                const long long rp128 = 128ll * rowsum_p;
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     if ((j >> 2) == hh) {
                         const __int128 other = XT[(size_t)((cg * 2 + 1 - hh) * 8 + j) * 64 + p];
                         const int q = 32 * c + 8 * cg + j;
-                        const __int128 T = mine[j & 3] + other + (__int128)(128ll * Rs[F * kB + p]) * Rs[F * kB + q];
+                        const __int128 T = mine[j & 3] + other + (__int128)rp128 * rowsum_q[j & 3];
                         const df v = int128_to_df(T);
                         c0[leaf * M + (nf == 2 ? f * n : 0) + q * kB + p] = make_float2(v.hi, v.lo);
                     }
