@@ -241,7 +241,7 @@ def level_of(b: int, max_block: int) -> int:
 
 def roofline(name, launches, total_ms, stats_sum, peaks, peak_kind, sm_mhz, max_block, step_floor_ns=None):
     """Roofline entry of one kernel, from its live event-timed launches and
-    the algorithmic work of SURVEY-style counting:
+    the algorithmic work of the method in its dense generic-dictionary form:
 
     * pursuit (``mp*``): 6 n flops per atom-iteration (2M for a dense Gram
       column, 2n for the residual) against the FP32 FMA peak in flops; the
@@ -267,7 +267,7 @@ def roofline(name, launches, total_ms, stats_sum, peaks, peak_kind, sm_mhz, max_
         exact = not kind.startswith("mp_fp32")
         r.update({"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                   "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (max SM clock)",
-                  "work": "6n flops per atom-iteration (SURVEY 8d dense-Gram count), n = b^2",
+                  "work": "6n flops per atom-iteration (dense Gram column 2M + residual 2n, M = 2n), n = b^2",
                   "atom_iterations_per_launch": iters,
                   "issued_fp32_ops_per_alg_flop": (15.0 * n if exact else 1.0 * n) / (6.0 * n),
                   "issued_note": ("the library updates only the other family's n correlations per step "
@@ -284,14 +284,14 @@ def roofline(name, launches, total_ms, stats_sum, peaks, peak_kind, sm_mhz, max_
             r["latency"] = lat
     elif kind.startswith("corr"):
         sep = kind.startswith("corr_sep")
-        flops = 4.0 * n * n * attempts                       # the dense GEMM's 4 n^2 per leaf
+        flops = 4.0 * n * n * attempts                       # the dense GEMM's 2 M n = 4 n^2 per leaf
         peak = peaks.get("bf16_tflops", 1900.0)
         ach = flops / per_launch_s / 1e12
         kpad = max(64, (n + 63) // 64 * 64)
         alg_bytes = 2.0 * M * n + attempts * (2.0 * kpad + 8.0 * M)
         r.update({"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                   "peak_source": f"bf16_tflops ({peak_kind})",
-                  "work": "4 n^2 flops per leaf (SURVEY 8d count: dense D^T y for M = 2n atoms)",
+                  "work": "4 n^2 flops per leaf (dense D^T y for M = 2n atoms)",
                   "leaves_per_launch": attempts, "algorithmic_bytes": alg_bytes})
         if sep:
             # the separable kernels' own algorithmic work (B Y B^T, both
