@@ -758,7 +758,7 @@ def run_omp(args):
 
 
 PRECISION_ROOT = 128
-PRECISION_WORKLOAD = ("one 4096x4096 RGB synthetic image (piecewise scene per channel, seeds 0..2), RMSE tol 2, "
+PRECISION_WORKLOAD = ("one 4096x4096 RGB synthetic image ({scene} scene per channel, seeds 0..2), RMSE tol 2, "
                       "quadtree 128->4, k=b^2/4, DCT-II+Haar: exact form vs plain FP32, BF16 and FP8 forms")
 
 
@@ -774,7 +774,8 @@ def run_precision(args):
     dist_init("nccl")
     build_lib.build()
     n = 4096
-    planes = [torch.from_numpy(synthetic.piecewise_scene(n, n, seed=rank * 3 + c)).cuda() for c in range(3)]
+    scene = synthetic.gradient_scene if args.scene == "gradient" else synthetic.piecewise_scene
+    planes = [torch.from_numpy(scene(n, n, seed=rank * 3 + c)).cuda() for c in range(3)]
     npix = 3 * n * n
     stream = torch.cuda.current_stream()
     forms = {"exact": aqmp.AQMP_PREC_EXACT, "fp32": aqmp.AQMP_PREC_FP32, "bf16": aqmp.AQMP_PREC_BF16,
@@ -843,7 +844,8 @@ def run_precision(args):
                           "ms_per_step": 1e3 * out["exact"]["s"] / args.steps, "higher_is_better": True,
                           "scaling": "weak", "vs_baseline": None, "dtype": "bf16-limb tensor GEMM + f32x2 pursuit",
                           "data": "synthetic",
-                          "config": {"workload": PRECISION_WORKLOAD, "pixels_per_step": npix, "input": "device-resident",
+                          "config": {"workload": PRECISION_WORKLOAD.format(scene=args.scene), "pixels_per_step": npix,
+                                     "input": "device-resident",
                                      "l2": "inputs (50 M px) and working set exceed L2"},
                           "fp32_form": {"value": weak_scaling_value(npix, args.steps, out["fp32"]["s"], world),
                                         "unit": "MP/s"},
@@ -889,6 +891,8 @@ def main():
                          "exact form against the FP32 and BF16 forms")
     ap.add_argument("--images", type=int, default=IMAGES_PER_RANK,
                     help="uneven64 workloads only: images per rank (64; fewer for profiler captures)")
+    ap.add_argument("--scene", choices=["gradient", "piecewise"], default="gradient",
+                    help="precision4096 only: the configuration-1 gradient scene (default) or the piecewise scene")
     ap.add_argument("--root", type=int, default=0,
                     help="precision4096 only: root block side (default 128; 64 for comparison)")
     args = ap.parse_args()
