@@ -345,9 +345,11 @@ def kernel_breakdown(aqmp, encode, flush):
 
 
 def autotune_choices(aqmp):
-    """The autotuner's settled choices, by kernel and side."""
-    return {f'{e["kind"]}_b{e["side"]}': (("tcgen05", "simt") if e["kind"] == "corr"
-                                          else ("default", "alternate"))[e["chosen"]]
+    """The autotuner's settled choices, by kernel and side, with each
+    candidate's best timing in ms."""
+    return {f'{e["kind"]}_b{e["side"]}': {"chosen": (("tcgen05", "simt") if e["kind"] == "corr"
+                                                     else ("default", "alternate"))[e["chosen"]],
+                                          "ms": [round(x, 4) for x in e["best_ms"]]}
             for e in aqmp.aqmp_autotune_read() if e["chosen"] >= 0}
 
 

@@ -43,7 +43,6 @@ namespace septc {
 
 constexpr int kB = 64;                        // block side served here
 constexpr int kThreads = 512;                 // 16 warps: 4 per TMEM lane quarter
-constexpr int kGroups = kThreads / 128;       // column groups per lane quarter
 constexpr int kTmemCols = 512;
 constexpr int kColA = 0;                      // stage-2 A tiles: 4 x 32 columns
 constexpr int kColD = 128;                    // accumulators

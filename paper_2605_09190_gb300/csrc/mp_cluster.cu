@@ -42,7 +42,6 @@ namespace aqmp {
 
 namespace {
 
-constexpr int kCB = 128;                                  // block side
 constexpr int kCT = 256;                                  // threads per CTA
 constexpr unsigned long long kExchangeWaitNs = 2000000000ull;
 constexpr unsigned long long kGraceNs = 50000000ull;
@@ -109,14 +108,14 @@ __device__ __forceinline__ float2 ld_peer_f2(uint32_t addr) {
 // Rank-1 update of the G elements in slots [S0, S0 + G) of one family and
 // their new top-2: element (v, S0 + s2) takes u W[q*, q'] with q' the slot's
 // column, read from the CTA's column slice at wcol[2 s2].
-template <int VT, int E, int G, int S0, bool DF>
+template <int VT, int E, int G, int S0, int TB, bool DF>
 __device__ __forceinline__ Top2 update_cols(float (&ch)[E], float (&cl)[E], int v, const df &u,
                                             const float2 *wcol) {
     Run2 acc = run2_empty();
 #pragma unroll
     for (int s2 = 0; s2 < G; ++s2) {
         const int s = S0 + s2;
-        const float2 w = wcol[2 * s2];
+        const float2 w = wcol[TB * s2];
         if (DF) {
             const df r = df_sub_mul(df{ch[s], cl[s]}, u, df{w.x, w.y});
             ch[s] = r.hi;
@@ -180,16 +179,18 @@ __device__ __forceinline__ bool cluster_exchange(uint4 *xs, unsigned long long *
 // NF: atom families (2: DCT + Haar on four CTAs; 1: one orthonormal family
 // on two); DF as in the single-CTA kernel (double-float state and certified
 // decisions, or the plain FP32 form).
-template <int NF, bool DF>
+template <int B, int C, int NF, bool DF>
 __global__ void __launch_bounds__(kCT, 1) mp_cluster_kernel(MPArgs a) {
-    constexpr int B = kCB, T = kCT, n = B * B, M = NF * n, C = 2 * NF, VT = C * T;
+    constexpr int T = kCT, n = B * B, M = NF * n, VT = C * T;
+    constexpr int TB = T / B, VB = VT / B;     // a thread's columns: TB rank + lane / B + VB s
     constexpr int E = M / VT;                  // 32 elements per thread
     constexpr int NG = NF, G = E / NG;         // one top-2 per family
     constexpr int NW = T / 32;
     constexpr int RS = B / C;                  // table rows held per CTA (NF == 2)
     constexpr int CS = B * T / VT;             // columns of a CTA's slice (NF == 2: 32)
     static_assert(M % VT == 0 && T % B == 0 && G * VT == n, "layout");
-    static_assert(NF == 1 || (CS == 32 && RS == 32), "slices");
+    static_assert(NF == 1 || (CS % TB == 0 && RS * C == B), "slices");
+    static_assert(C * NW <= 32, "one warp merges every warp's summary");
 
     extern __shared__ __align__(16) unsigned char smem[];
     // NF == 2: column slices colV[fam table][q1][32] and row shards rowV[fam table][32][b]
@@ -217,7 +218,7 @@ __global__ void __launch_bounds__(kCT, 1) mp_cluster_kernel(MPArgs a) {
     if (NF == 2) {
         for (int i = threadIdx.x; i < 2 * B * CS; i += T) {
             const int tab = i / (B * CS), r = (i / CS) % B, lc = i % CS;
-            const int q = 8 * (lc >> 1) + 2 * (int)rank + (lc & 1);
+            const int q = VB * (lc / TB) + TB * (int)rank + (lc % TB);
             sCol[i] = (tab ? a.WT : a.W)[r * B + q];
         }
         for (int i = threadIdx.x; i < 2 * RS * B; i += T) {
@@ -443,10 +444,10 @@ __global__ void __launch_bounds__(kCT, 1) mp_cluster_kernel(MPArgs a) {
                 const df u = DF ? df_mul(alpha, df{vp.x, vp.y}) : df{__fmul_rn(alpha.hi, vp.x), 0.0f};
                 const float2 *wcol = sCol + (size_t)tab * B * CS + q1 * CS + hb;
                 if (fam1) {
-                    top[0] = update_cols<VT, E, G, 0, DF>(ch, cl, vl, u, wcol);
+                    top[0] = update_cols<VT, E, G, 0, TB, DF>(ch, cl, vl, u, wcol);
                     if (owner) top[1] = zero_and_rescan<VT, E, G, G>(ch, cl, vl, j1);
                 } else {
-                    top[1] = update_cols<VT, E, G, G, DF>(ch, cl, vl, u, wcol);
+                    top[1] = update_cols<VT, E, G, G, TB, DF>(ch, cl, vl, u, wcol);
                     if (owner) top[0] = zero_and_rescan<VT, E, G, 0>(ch, cl, vl, j1);
                 }
             } else if (owner) {
@@ -541,15 +542,15 @@ __global__ void __launch_bounds__(kCT, 1) mp_cluster_kernel(MPArgs a) {
     }
 }
 
-template <int NF, bool DF>
+template <int B, int C, int NF, bool DF>
 static cudaError_t launch_cluster_t(const MPArgs &a, int num_sms, cudaStream_t st) {
-    constexpr int C = 2 * NF, NW = kCT / 32;
+    constexpr int NW = kCT / 32, CS = B * kCT / (C * kCT), RS = B / C;
     (void)num_sms;
-    // NF == 2: column slices 2 x b x 32 and row shards 2 x 32 x b double-float pairs (128 KB)
-    const size_t smem = (NF == 2 ? (size_t)4 * kCB * 32 * sizeof(float2) : 0) + 2 * C * NW * sizeof(uint4) +
+    // NF == 2: column slices 2 x b x CS and row shards 2 x RS x b double-float pairs
+    const size_t smem = (NF == 2 ? (size_t)2 * (B * CS + RS * B) * sizeof(float2) : 0) + 2 * C * NW * sizeof(uint4) +
                         2 * C * sizeof(uint4) + 4 * sizeof(unsigned long long) + 16 * sizeof(uint32_t) +
                         NW * (sizeof(unsigned long long) + sizeof(uint32_t)) + (size_t)a.lv.k * sizeof(StepRec);
-    auto kern = mp_cluster_kernel<NF, DF>;
+    auto kern = mp_cluster_kernel<B, C, NF, DF>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     cudaLaunchAttribute attr[1];
@@ -576,9 +577,14 @@ static cudaError_t launch_cluster_t(const MPArgs &a, int num_sms, cudaStream_t s
 }
 
 cudaError_t launch_mp_cluster(const MPArgs &a, int nf, bool double_float, int num_sms, cudaStream_t st) {
-    if (a.lv.b != kCB) return cudaErrorInvalidValue;
-    if (nf == 2) return double_float ? launch_cluster_t<2, true>(a, num_sms, st) : launch_cluster_t<2, false>(a, num_sms, st);
-    return double_float ? launch_cluster_t<1, true>(a, num_sms, st) : launch_cluster_t<1, false>(a, num_sms, st);
+    if (a.lv.b == 128) {
+        if (nf == 2)
+            return double_float ? launch_cluster_t<128, 4, 2, true>(a, num_sms, st)
+                                : launch_cluster_t<128, 4, 2, false>(a, num_sms, st);
+        return double_float ? launch_cluster_t<128, 2, 1, true>(a, num_sms, st)
+                            : launch_cluster_t<128, 2, 1, false>(a, num_sms, st);
+    }
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace aqmp
