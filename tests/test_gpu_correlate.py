@@ -33,7 +33,7 @@ def _blocks(L, b, seed):
 
 
 CASES = [(4, 0, 1), (4, 0, 200), (8, 0, 65), (8, 1, 64), (16, 0, 130), (16, 2, 7), (32, 0, 70), (64, 0, 66),
-         (64, 1, 3), (128, 0, 5), (128, 2, 2)]
+         (64, 0, 1), (64, 0, 153), (64, 1, 3), (64, 2, 5), (128, 0, 5), (128, 2, 2)]
 
 
 def _families(b, dict_id):
