@@ -17,12 +17,14 @@
 //   Stage 2: T~[p][q] = sum_{t,s} 2^(8(t+s)) sum_m e_t[p][m] d_s[q][m].
 //     A = tile v (tensor memory), B = d_s rows q (shared memory, 32 q per
 //     pass), accumulated into column block 2v + s: lane half h of block c
-//     then holds the digit diagonal t + s = c + h, at most four products
-//     of |e d| <= 2^20.5 summed over 64 terms: below 2^22, exact.
-//   The epilogue converts each diagonal (exact FP32 integers) and runs the
-//   base-2^8 Horner scheme in int128, the two lane halves meet through
-//   shared memory, and T = T~ + 128 R[p] R[q] is rounded once into a
-//   double-float (int128_to_df).
+//     then holds the digit diagonal t + s = c + h, the sum of at most three
+//     digit products (one per tile v with 0 <= c - 2v < 6), each below
+//     128 x 181 x 64 < 2^20.5 in magnitude: below 2^22, exact.
+//   The epilogue reads each diagonal (an exact FP32 integer), joins
+//   adjacent diagonals in one 32-bit multiply-add and those pairs in int64
+//   groups, then in int128 (the base-2^8 Horner scheme), the two lane
+//   halves meet through shared memory, and T = T~ + 128 R[p] R[q] is
+//   rounded once into a double-float (int128_to_df).
 //
 // One CTA per SM (16 warps, all 512 TMEM columns: A tiles 0..127, stage-1
 // accumulators 128..319, stage-2 accumulators 128..511), persistent over the
