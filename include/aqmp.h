@@ -252,9 +252,17 @@ int aqmp_ssim(const float *x, const float *y, int h, int w, int64_t pitch, doubl
  * holding L blocks of b x b bytes, each row-major and contiguous; `corr` is
  * device memory for L x M float pairs (hi, lo) whose sum is the correlation
  * of the 2^-48 fixed-point dictionary with the block, rounded once.
- * gemm: 0 = tcgen05 tensor-core kernel, 1 = integer SIMT kernel (both exact,
- * identical bits), 2 = the reduced-precision BF16 form (one tcgen05 pass of
- * bf16(D), FP32 accumulation; low words 0). */
+ * gemm selects the kernel:
+ *   0 = the separable exact correlation B Y B^T: tcgen05 at side 64, the
+ *       integer SIMT kernel at the other sides;
+ *   1 = the separable SIMT kernel at every side
+ *       (0 and 1 round the same exact integer once: identical bits);
+ *   3, 4 = the dense exact kernels (round(D 2^48), tcgen05 and SIMT);
+ *   2 = the reduced-precision BF16 form (one tcgen05 pass of bf16(D), FP32
+ *       accumulation; low words 0);
+ *   5 = the FP8 form (one E4M3 tcgen05 pass, per-atom and per-block
+ *       power-of-two scales; low words 0).
+ * On a kernel error the stream is synchronised before the error returns. */
 int aqmp_correlate(int b, int dict_id, const uint8_t *blocks, int64_t L, float *corr,
                    int gemm, void *stream);
 
