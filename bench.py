@@ -700,13 +700,15 @@ def run_ours(args):
     return 0
 
 
-OMP_WORKLOAD = ("piecewise-planar synthetic 512x512 gray, RMSE tol sweep {1,2,4,8} batched as 4 planes, "
-                "quadtree 16->4, k=b^2/4, DCT-II+Haar, Orthogonal Matching Pursuit (FP64 least-squares re-fit)")
+OMP_WORKLOAD = ("piecewise-planar synthetic 512x512 gray, RMSE tol sweep {{1,2,4,8}} batched as 4 planes, "
+                "quadtree {root}->4, k=b^2/4, DCT-II+Haar, Orthogonal Matching Pursuit (FP64 least-squares re-fit)")
+OMP_ROOT = 64
 
 
 def run_omp(args):
-    """OMP (the authors' solver) on the sweep's planes with 16x16 roots,
-    and MP on the same configuration for comparison."""
+    """OMP (the authors' solver) on the sweep's planes with 64x64 roots
+    (``--root`` for another side), and MP on the same configuration for
+    comparison."""
     import torch
     from paper_2605_09190_gb300 import aqmp, build_lib
     rank, world, local = dist_env()
@@ -718,8 +720,10 @@ def run_omp(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
+    root = args.root or OMP_ROOT
+
     def timed(omp):
-        encode = lambda: aqmp.aqmp_encode_planes(dev, SWEEP_TOLS, min_block=MIN_BLOCK, max_block=16, omp=omp)  # noqa: E731
+        encode = lambda: aqmp.aqmp_encode_planes(dev, SWEEP_TOLS, min_block=MIN_BLOCK, max_block=root, omp=omp)  # noqa: E731
         settle_autotuner(aqmp, encode)
         breakdown, top, per_call = kernel_breakdown(aqmp, encode, lambda: flush.zero_())
         for _ in range(args.warmup):
@@ -747,7 +751,8 @@ def run_omp(args):
                           "unit": "MP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                           "ms_per_step": 1e3 * omp_s / args.steps, "higher_is_better": True, "scaling": "weak",
                           "vs_baseline": None, "dtype": "fp64 pursuit + bf16-limb tensor GEMM", "data": "synthetic",
-                          "config": {"workload": OMP_WORKLOAD, "planes_per_step": len(dev), "pixels_per_step": npix,
+                          "config": {"workload": OMP_WORKLOAD.format(root=root), "name": "omp512",
+                                     "planes_per_step": len(dev), "pixels_per_step": npix,
                                      "input": "device-resident", "l2": "flushed between steps (256 MB write)"},
                           "atoms_per_step": st["n_atoms"], "leaves_per_step": st["n_leaves"],
                           "mp_same_config": {"value": weak_scaling_value(npix, args.steps, mp_s, world),
@@ -888,7 +893,7 @@ def main():
                     default="uneven64",
                     help="uneven64: 64 uneven RGB gradient images (default); uneven64-piecewise: the same sizes "
                          "with piecewise content; sweep512: the 512x512 tolerance sweep; refine16: coefficient "
-                         "refinement on 16 images (steps = Adam steps); omp512: the sweep's planes with 16x16 "
+                         "refinement on 16 images (steps = Adam steps); omp512: the sweep's planes with 64x64 "
                          "roots, Orthogonal Matching Pursuit; precision4096: one 4096x4096 RGB image, the "
                          "exact form against the FP32 and BF16 forms")
     ap.add_argument("--images", type=int, default=IMAGES_PER_RANK,
@@ -896,7 +901,8 @@ def main():
     ap.add_argument("--scene", choices=["gradient", "piecewise"], default="gradient",
                     help="precision4096 only: the configuration-1 gradient scene (default) or the piecewise scene")
     ap.add_argument("--root", type=int, default=0,
-                    help="precision4096 only: root block side (default 128; 64 for comparison)")
+                    help="precision4096: root block side (default 128; 64 for comparison); omp512: root side "
+                         "(default 64; 16 for comparison)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

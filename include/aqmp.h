@@ -86,9 +86,13 @@ extern "C" {
                                       coefficients are re-fitted by least
                                       squares (FP64 Cholesky); the emitted
                                       coefficients are the final fit.  Needs
-                                      max_block <= 16, AQMP_PREC_EXACT and a
-                                      budget of at most 64 atoms per leaf
-                                      (else AQMP_E_UNSUPPORTED) */
+                                      max_block <= 64, AQMP_PREC_EXACT and a
+                                      budget per leaf of at most 64 atoms at
+                                      sides 4..16 and 1024 at sides 32 and 64
+                                      (else AQMP_E_UNSUPPORTED).  Sides 32 and
+                                      64 keep a Cholesky factor of up to
+                                      k(k+1)/2 doubles per SM in device
+                                      memory (4.2 MB at k = 1024). */
 /* Autotuning: kernel choices that leave the result unchanged bit for bit
  * are measured on the first calls of each configuration and the fastest
  * is kept for the life of the process: the initial correlation on the

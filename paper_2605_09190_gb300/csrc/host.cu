@@ -323,7 +323,7 @@ struct Ctx {
     int cc_major = 0, cc_minor = 0;
     std::mutex mu;
     std::map<int, std::unique_ptr<Dict>> dicts;
-    DeviceBuf planes, staging, queues, Y, e0, c0, counters, ssim_ws, Y8, inv_sl;
+    DeviceBuf planes, staging, queues, Y, e0, c0, counters, ssim_ws, Y8, inv_sl, omp_L;
     DeviceBuf leaves_ws, atoms_ws, lo_ws, atom_leaf, cells, perm, new_off, order_status;   // emission -> canonical order
     bool gauss_ready = false;
     Tuner tuner;
@@ -667,10 +667,13 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
     const bool bf16 = P.precision == AQMP_PREC_BF16;
     const bool fp8 = P.precision == AQMP_PREC_FP8;
     if (omp) {
-        if (P.max_block > 16 || P.precision != AQMP_PREC_EXACT)
-            return fail(AQMP_E_UNSUPPORTED, "OMP needs max_block <= 16 and the exact precision");
-        if ((long long)P.max_block * P.max_block * P.cap_num / P.cap_den > omp_max_budget())
-            return fail(AQMP_E_UNSUPPORTED, "OMP budget above %d atoms per leaf", omp_max_budget());
+        if (P.max_block > 64 || P.precision != AQMP_PREC_EXACT)
+            return fail(AQMP_E_UNSUPPORTED, "OMP needs max_block <= 64 and the exact precision");
+        for (int b = P.max_block; b >= P.min_block; b >>= 1) {
+            const long long kb = std::max<long long>(1, (long long)b * b * P.cap_num / P.cap_den);
+            if (kb > omp_max_budget(b))
+                return fail(AQMP_E_UNSUPPORTED, "OMP budget above %d atoms per leaf at side %d", omp_max_budget(b), b);
+        }
     }
     unsigned long long npix = 0, roots = 0, staged = 0;
     for (int i = 0; i < n_planes; ++i) {
@@ -750,6 +753,16 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
     CK(cudaMallocFromPoolAsync((void **)&code->alpha_lo, sizeof(float) * std::max<unsigned long long>(1, atom_cap),
                                c->out_pool, st));
     if ((rc = c->counters.reserve(sizeof(Counters)))) return rc;
+    // OMP at sides 32 and 64: a packed Cholesky factor per resident CTA
+    unsigned long long omp_doubles = 0;
+    if (omp)
+        for (int l = 0; l < nlev; ++l) {
+            const int b = P.max_block >> l;
+            if (b < 32) continue;
+            const int kb = (int)std::max<long long>(1, (long long)b * b * P.cap_num / P.cap_den);
+            omp_doubles = std::max(omp_doubles, omp_cta_workspace_doubles(kb, c->num_sms));
+        }
+    if (omp_doubles && (rc = c->omp_L.reserve(sizeof(double) * omp_doubles))) return rc;
 
     // plane descriptors (and host pixels copied in)
     std::vector<PlaneDesc> pd(n_planes);
@@ -919,6 +932,9 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
         ma.atom_cap = atom_cap;
         ma.cells = cells;
         ma.ctr = ctr;
+        ma.omp_L = (double *)c->omp_L.p;
+        ma.omp_slots = c->num_sms;
+        ma.omp_L_doubles = omp_doubles;
         auto mp = [&](int v) {
             return g_prof.run(kname(exact ? "mp" : "mp_fp32", b), st,
                               [&] { return launch_mp(ma, d.nf, exact, v, c->num_sms, st); });

@@ -25,6 +25,11 @@ struct MPArgs {
     unsigned long long atom_cap;
     CellMap cells;               // emitted leaves are marked here
     Counters *ctr;
+    // OMP at sides 32 and 64: one packed Cholesky factor of up to k(k+1)/2
+    // doubles per CTA, omp_slots of them (omp_L_doubles in all)
+    double *omp_L;
+    int omp_slots;
+    unsigned long long omp_L_doubles;
 };
 // variant 0: the default launch shape; 1: the alternate one (other threads
 // per leaf at sides 16 and 32, two resident CTAs per SM at side 64; two
@@ -36,11 +41,16 @@ bool mp_has_variant(int b, int nf);
 // arguments and outputs as launch_mp.
 cudaError_t launch_mp_cluster(const MPArgs &a, int nf, bool double_float, int num_sms, cudaStream_t st);
 
-// Orthogonal Matching Pursuit of one level (omp.cu): sides 4, 8, 16, budget
-// k <= omp_max_budget(); same arguments and outputs as the MP kernel (the
-// coefficients emitted are the final least-squares values).
-int omp_max_budget();
+// Orthogonal Matching Pursuit of one level: sides 4, 8, 16 with a warp per
+// leaf (omp.cu), sides 32 and 64 with a CTA per leaf and the Cholesky factor
+// in the omp_L slots (omp_cta.cu); budget k <= omp_max_budget(b) (0: side not
+// served); same arguments and outputs as the MP kernel (the coefficients
+// emitted are the final least-squares values).
+int omp_max_budget(int b);
+unsigned long long omp_cta_workspace_doubles(int k, int slots);
 cudaError_t launch_omp(const MPArgs &a, int nf, int num_sms, cudaStream_t st);
+int omp_cta_max_budget();
+cudaError_t launch_omp_cta(const MPArgs &a, int nf, cudaStream_t st);
 
 // Block gather (gather.cu): queue entries -> centred BF16 leaf vectors
 // (column-major unravel, zero padded to Kpad) and sums of squares.

@@ -1,6 +1,6 @@
 // omp.cu -- Orthogonal Matching Pursuit per leaf (the solver the paper's
 // authors ran, Section 2.2), for sides 4..16, with the quadtree split / emit
-// of Algorithm 2.
+// of Algorithm 2 (sides 32 and 64: omp_cta.cu, the same rules).
 //
 // One warp owns one leaf.  Each step:
 //   - residual energy ||r||^2 = ||y||^2 - x_S . c0_S (the residual is
@@ -338,10 +338,15 @@ static cudaError_t launch_omp_t(const MPArgs &a, int num_sms, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-int omp_max_budget() { return 64; }
+int omp_max_budget(int b) {
+    if (b >= 4 && b <= 16) return 64;
+    if (b == 32 || b == 64) return omp_cta_max_budget();
+    return 0;
+}
 
 cudaError_t launch_omp(const MPArgs &a, int nf, int num_sms, cudaStream_t st) {
-    if (a.lv.k > omp_max_budget()) return cudaErrorInvalidValue;
+    if (a.lv.k > omp_max_budget(a.lv.b)) return cudaErrorInvalidValue;
+    if (a.lv.b >= 32) return launch_omp_cta(a, nf, st);
     if (nf == 2) {
         switch (a.lv.b) {
             case 4: return launch_omp_t<4, 2>(a, num_sms, st);
