@@ -270,6 +270,20 @@ int aqmp_ssim(const float *x, const float *y, int h, int w, int64_t pitch, doubl
 int aqmp_correlate(int b, int dict_id, const uint8_t *blocks, int64_t L, float *corr,
                    int gemm, void *stream);
 
+/* The initial correlation of the BF16 form with rescore (the correlation
+ * GEMM in BF16 on the tensor cores with FP32 accumulation; Section 2.1, 2-D
+ * atoms as outer products of 1-D rows), side 64 only (else
+ * AQMP_E_UNSUPPORTED).  For L blocks laid out as for aqmp_correlate:
+ * `corr` (device, L x M float pairs) receives c~ ~ B Y B^T per family from
+ * split BF16 products of the 1-D rows and of the intermediate, the pixels
+ * centred on each block's integer mean; `bound` (device, L x M floats)
+ * receives e_j >= |c~_j - c_j|, c_j the value aqmp_correlate (gemm 0)
+ * returns, under the accumulation model stated in the kernel's header (each
+ * FP32 MMA step errs by at most two units in the last place of its running
+ * magnitude). */
+int aqmp_correlate_bf16x2(int b, int dict_id, const uint8_t *blocks, int64_t L, float *corr, float *bound,
+                          void *stream);
+
 /* Kernel timing.  While enabled, every kernel the library launches is
  * bracketed by CUDA events on the stream it runs on; the durations are
  * folded into per-kernel totals when the launching call synchronises.

@@ -72,7 +72,8 @@ EXPORTS = ["aqmp_params_default", "aqmp_encode_planes", "aqmp_encode", "aqmp_cod
            "aqmp_correlate_noalloc", "aqmp_selftest_wait", "aqmp_code_device", "aqmp_synth_forward",
            "aqmp_synth_backward", "aqmp_ssim", "aqmp_image_to_planes", "aqmp_planes_to_image",
            "aqmp_bitstream_size", "aqmp_bitstream_write", "aqmp_bitstream_parse", "aqmp_code_from_bitstream",
-           "aqmp_autotune_read", "aqmp_autotune_reset", "aqmp_profile_filter", "aqmp_encode_batch"]
+           "aqmp_autotune_read", "aqmp_autotune_reset", "aqmp_profile_filter", "aqmp_encode_batch",
+           "aqmp_correlate_bf16x2"]
 
 
 class aqmp_tune_entry(ctypes.Structure):
@@ -122,6 +123,7 @@ def load_library(path: str | None = None):
         lib.aqmp_code_free.restype = None
         lib.aqmp_correlate.argtypes = [I, I, V, I64, V, I, V]
         lib.aqmp_correlate_noalloc.argtypes = [I, I, V, I64, V, V]
+        lib.aqmp_correlate_bf16x2.argtypes = [I, I, V, I64, V, V, V]
         lib.aqmp_selftest_wait.argtypes = [I, V]
         U64P = ctypes.POINTER(ctypes.c_uint64)
         lib.aqmp_code_device.argtypes = [V, ctypes.POINTER(V), ctypes.POINTER(V), U64P, U64P]
@@ -335,6 +337,21 @@ def aqmp_correlate(b: int, dict_id: int, blocks, gemm: int = 0, stream=None):
     _check(load_library().aqmp_correlate(b, dict_id, ctypes.c_void_p(blocks.data_ptr()), L,
                                          ctypes.c_void_p(out.data_ptr()), gemm, _stream_handle(stream)))
     return out
+
+
+def aqmp_correlate_bf16x2(b: int, dict_id: int, blocks, stream=None):
+    """The BF16 form's initial correlation of L contiguous b x b uint8
+    blocks (a CUDA tensor (L, b, b)) and its per-atom error bound: a CUDA
+    float32 tensor (L, M, 2) of double-float pairs and one (L, M)."""
+    import torch
+    L = blocks.shape[0]
+    M = aqmp_num_atoms(b, dict_id)
+    out = torch.empty((L, M, 2), dtype=torch.float32, device=blocks.device)
+    bound = torch.empty((L, M), dtype=torch.float32, device=blocks.device)
+    _check(load_library().aqmp_correlate_bf16x2(b, dict_id, ctypes.c_void_p(blocks.data_ptr()), L,
+                                                ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(bound.data_ptr()),
+                                                _stream_handle(stream)))
+    return out, bound
 
 
 def aqmp_num_atoms(b: int, dict_id: int) -> int:

@@ -38,6 +38,7 @@
 #include "common.cuh"
 #include "kernels.h"
 #include "sep.cuh"
+#include "tc_sep.cuh"
 
 namespace aqmp {
 
@@ -57,141 +58,12 @@ constexpr int kBytesX = 64 * 1024;
 constexpr int kOffBar = kOffX + kBytesX;      // barriers: Bd, Y[2], MMA
 constexpr int kOffMisc = kOffBar + 8 * 8;
 constexpr int kSmemBytes = kOffMisc + 16 + 1024;
-constexpr unsigned long long kWaitNs = 2000000000ull;
 
 // Stage 1: M = 128, N = 64; stage 2: M = 128, N = 32; BF16 x BF16 -> F32.
 constexpr uint32_t kIdesc1 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(64 >> 3) << 17) |
                              ((uint32_t)(128 >> 4) << 24);
 constexpr uint32_t kIdesc2 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(32 >> 3) << 17) |
                              ((uint32_t)(128 >> 4) << 24);
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ unsigned long long globaltimer() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait on the phase of parity `parity`.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = globaltimer();
-    for (;;) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (globaltimer() - t0 > kWaitNs) return false;
-    }
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int c0, int c1) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-        ::"r"(dst), "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(bar)
-        : "memory");
-}
-
-// K-major tile, 128-byte rows, 128-byte swizzle, 8-row groups 1024 B apart.
-__device__ __forceinline__ unsigned long long smem_desc(uint32_t addr) {
-    unsigned long long d = 0;
-    d |= (unsigned long long)((addr & 0x3ffffu) >> 4);
-    d |= (unsigned long long)1 << 16;
-    d |= (unsigned long long)(1024 >> 4) << 32;
-    d |= (unsigned long long)1 << 46;
-    d |= (unsigned long long)2 << 61;
-    return d;
-}
-
-__device__ __forceinline__ void mma_ss(uint32_t d, unsigned long long a, unsigned long long b, uint32_t idesc,
-                                       uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-        ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
-}
-
-// A from tensor memory: lane r of the tile is row r, K values packed two per
-// 32-bit column (even K in the low half).
-__device__ __forceinline__ void mma_ts(uint32_t d, uint32_t a_tmem, unsigned long long b, uint32_t idesc,
-                                       uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}"
-        ::"r"(d), "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                 : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-        "%14, %15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-}
-
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-        "%14, %15, %16};"
-        ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
-          "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
-        : "memory");
-}
-
-__device__ __forceinline__ void wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-__device__ __forceinline__ void wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
-__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// An FP32 value holding an integer of magnitude below 2^22, as an int32
-// (the integer lands in the low mantissa bits of x + 1.5 2^23).
-__device__ __forceinline__ int32_t small_int(uint32_t bits) {
-    return __float_as_int(__fadd_rn(__uint_as_float(bits), 12582912.0f)) - 0x4B400000;
-}
-
-// a 2^8 + b for two FP32 values holding integers of magnitude below 2^22:
-// their biased bit patterns (x + 1.5 2^23) combined in 32-bit arithmetic,
-// the bias removed once; exact as |a 2^8 + b| < 2^31.
-__device__ __forceinline__ int32_t pair8(uint32_t a_bits, uint32_t b_bits) {
-    const uint32_t ab = (uint32_t)__float_as_int(__fadd_rn(__uint_as_float(a_bits), 12582912.0f));
-    const uint32_t bb = (uint32_t)__float_as_int(__fadd_rn(__uint_as_float(b_bits), 12582912.0f));
-    return (int32_t)(ab * 256u + bb - 257u * 0x4B400000u);
-}
-
-// The BF16 bits of a small integer |e| <= 256 (exact: at most 8 significant
-// bits, so the FP32 value's low 16 bits are zero).
-__device__ __forceinline__ uint32_t bf16_bits(int32_t e) {
-    const float f = __fsub_rn(__int_as_float(0x4B400000 + e), 12582912.0f);   // (float)e, exact
-    return __float_as_uint(f) >> 16;
-}
 
 }  // namespace septc
 

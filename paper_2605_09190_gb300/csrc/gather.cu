@@ -4,7 +4,9 @@
 // concatenate the columns): element v = m b + i holds pixel (row i, col m).
 // The correlation kernels take it centred, y - 128, as BF16: every value in
 // [-128, 127] is exact in BF16; the centring is undone exactly inside the
-// correlation by adding 128 sum_v D_fix[j][v].
+// correlation by adding 128 sum_v D_fix[j][v].  The BF16 form with rescore
+// centres on the block's mean rounded to an integer instead (values in
+// [-255, 255], still exact in BF16), recorded per leaf.
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
@@ -31,15 +33,32 @@ __global__ void __launch_bounds__(256) gather_kernel(GatherArgs a) {
         const QueueEntry q = a.queue[leaf];
         const PlaneDesc pd = a.planes[q.plane];
         const uint8_t *base = pd.pix + (long long)q.y * pd.pitch + q.x;
-        uint32_t ss = 0;
+        uint32_t ss = 0, sy = 0;
 #pragma unroll 4
         for (int idx = t; idx < n; idx += TPL) {               // rows, coalesced
             const int i = idx / B, m = idx % B;
             const uint32_t p = base[(long long)i * pd.pitch + m];
             ss += p * p;
+            sy += p;
             tile[i * stride + m] = (uint8_t)p;
         }
         if (TPL == 32) __syncwarp(); else __syncthreads();
+        // the centre: 128, or (BF16 form with rescore) the block's mean
+        // rounded to an integer, so that y - centre stays exact in BF16
+        int centre = 128;
+        if (a.mu) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) sy += __shfl_xor_sync(0xffffffffu, sy, off);
+            if (NW > 1) {
+                if (lane == 0) s_ss[threadIdx.x >> 5] = sy;
+                __syncthreads();
+                sy = 0;
+                for (int w = 0; w < NW; ++w) sy += s_ss[w];
+                __syncthreads();
+            }
+            centre = (int)((sy + (uint32_t)(n / 2)) / (uint32_t)n);
+            if (t == 0) a.mu[leaf] = (uint8_t)centre;
+        }
         if (a.Y8) {
             // FP8 form: centred pixels times the block's power-of-two scale
             // s_l (the largest with max |y~| s_l <= 448), rounded to E4M3
@@ -73,8 +92,8 @@ __global__ void __launch_bounds__(256) gather_kernel(GatherArgs a) {
             __nv_bfloat162 *dst = reinterpret_cast<__nv_bfloat162 *>(a.Y + (size_t)leaf * a.Kpad);
             for (int v = 2 * t; v < a.Kpad; v += 2 * TPL) {      // unravel order, BF16 pairs
                 float v0 = 0.0f, v1 = 0.0f;
-                if (v < n) v0 = (float)((int)tile[(v % B) * stride + v / B] - 128);
-                if (v + 1 < n) v1 = (float)((int)tile[((v + 1) % B) * stride + (v + 1) / B] - 128);
+                if (v < n) v0 = (float)((int)tile[(v % B) * stride + v / B] - centre);
+                if (v + 1 < n) v1 = (float)((int)tile[((v + 1) % B) * stride + (v + 1) / B] - centre);
                 dst[v >> 1] = __floats2bfloat162_rn(v0, v1);
             }
         }
@@ -121,15 +140,25 @@ cudaError_t launch_gather(const GatherArgs &a, int num_sms, cudaStream_t st) {
     return cudaErrorInvalidValue;
 }
 
-// L contiguous row-major b x b blocks.
+// L contiguous row-major b x b blocks (centred on 128, or with `mu` on each
+// block's integer mean, recorded in mu[leaf]).
 __global__ void gather_blocks_kernel(int b, int Kpad, const uint8_t *blocks, long long L,
-                                     __nv_bfloat16 *Y, uint32_t *e0) {
+                                     __nv_bfloat16 *Y, uint32_t *e0, uint8_t *mu) {
     const int lane = threadIdx.x & 31;
     const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
     const int n = b * b;
     for (long long leaf = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; leaf < L; leaf += warps) {
         const uint8_t *base = blocks + leaf * n;
         __nv_bfloat16 *dst = Y + leaf * Kpad;
+        int centre = 128;
+        if (mu) {
+            uint32_t sy = 0;
+            for (int v = lane; v < n; v += 32) sy += base[v];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) sy += __shfl_xor_sync(0xffffffffu, sy, off);
+            centre = (int)((sy + (uint32_t)(n / 2)) / (uint32_t)n);
+            if (lane == 0) mu[leaf] = (uint8_t)centre;
+        }
         uint32_t ss = 0;
         for (int v = lane; v < Kpad; v += 32) {
             float val = 0.0f;
@@ -137,7 +166,7 @@ __global__ void gather_blocks_kernel(int b, int Kpad, const uint8_t *blocks, lon
                 const int m = v / b, i = v - m * b;
                 const uint32_t p = base[i * b + m];
                 ss += p * p;
-                val = (float)((int)p - 128);
+                val = (float)((int)p - centre);
             }
             dst[v] = __float2bfloat16_rn(val);
         }
@@ -148,12 +177,12 @@ __global__ void gather_blocks_kernel(int b, int Kpad, const uint8_t *blocks, lon
 }
 
 cudaError_t launch_gather_blocks(int b, int Kpad, const uint8_t *blocks, long long L,
-                                 __nv_bfloat16 *Y, uint32_t *e0, int num_sms, cudaStream_t st) {
+                                 __nv_bfloat16 *Y, uint32_t *e0, int num_sms, cudaStream_t st, uint8_t *mu) {
     long long blocks_needed = (L + 7) / 8;
     long long cap = (long long)num_sms * 8;
     if (blocks_needed > cap) blocks_needed = cap;
     if (blocks_needed < 1) blocks_needed = 1;
-    gather_blocks_kernel<<<(unsigned)blocks_needed, 256, 0, st>>>(b, Kpad, blocks, L, Y, e0);
+    gather_blocks_kernel<<<(unsigned)blocks_needed, 256, 0, st>>>(b, Kpad, blocks, L, Y, e0, mu);
     return cudaGetLastError();
 }
 

@@ -305,8 +305,8 @@ struct Tuner {
 
 struct Dict {
     DictDev d{};
-    DeviceBuf limbs, dh, dl, sh, sl, w, basis, basis64, sep, sepd;
-    CUtensorMap tmap_sd;
+    DeviceBuf limbs, dh, dl, sh, sl, w, basis, basis64, sep, sepd, sepbf;
+    CUtensorMap tmap_sd, tmap_sbf;
     CUtensorMap tmap;
     bool tables = false;         // fixed-point correlation tables built (16 M n B + 8 M n B)
     DeviceBuf dbf, sbf;          // reduced-precision form: bf16(D) and its row sums
@@ -323,7 +323,7 @@ struct Ctx {
     int cc_major = 0, cc_minor = 0;
     std::mutex mu;
     std::map<int, std::unique_ptr<Dict>> dicts;
-    DeviceBuf planes, staging, queues, Y, e0, c0, counters, ssim_ws, Y8, inv_sl, omp_L;
+    DeviceBuf planes, staging, queues, Y, e0, c0, counters, ssim_ws, Y8, inv_sl, omp_L, mu_buf, ebound;
     DeviceBuf leaves_ws, atoms_ws, lo_ws, atom_leaf, cells, perm, new_off, order_status;   // emission -> canonical order
     bool gauss_ready = false;
     Tuner tuner;
@@ -471,6 +471,40 @@ int get_dict(Ctx *c, int b, int dict_id, cudaStream_t st, Dict **out, bool table
                 CK(cudaMemcpyAsync(d.sepd, dg.data(), sizeof(__nv_bfloat16) * dg.size(), cudaMemcpyHostToDevice, st));
                 if ((rc0 = encode_bf16_map(&Dn->tmap_sd, d.sepd, 6ull * 2 * b, b, 128))) return rc0;
                 d.tmap_sepd = &Dn->tmap_sd;
+                // the BF16 form with rescore (corr_sepbf_tc.cu): three
+                // 128-row tiles of 1-D rows, [bf16(B_0); bf16(B_0 - bf16(B_0))],
+                // the same for family 1, then [|B_0| ; |B_1|] rounded up to
+                // BF16; and the row sums R[F][p] = sum_i B[F][p][i] as (hi, lo)
+                std::vector<__nv_bfloat16> sb(3 * 2 * bb);
+                std::vector<float2> rs(2 * (size_t)b);
+                for (int F = 0; F < 2; ++F)
+                    for (int r = 0; r < b; ++r) {
+                        double sum = 0.0;
+                        for (int col = 0; col < b; ++col) {
+                            const double x = basis[F * bb + (size_t)r * b + col];
+                            sum += x;
+                            const __nv_bfloat16 hi = __float2bfloat16_rn((float)x);
+                            const double rem = x - (double)__bfloat162float(hi);
+                            const __nv_bfloat16 lo = __float2bfloat16_rn((float)rem);
+                            float ax = (float)std::fabs(x);
+                            if ((double)ax < std::fabs(x)) ax = std::nextafter(ax, INFINITY);
+                            __nv_bfloat16 au = __float2bfloat16_rn(ax);
+                            if (__bfloat162float(au) < ax) au = __float2bfloat16_ru(ax);
+                            sb[((size_t)F * 2 * b + r) * b + col] = hi;
+                            sb[((size_t)F * 2 * b + b + r) * b + col] = lo;
+                            sb[((size_t)4 * b + F * b + r) * b + col] = au;
+                        }
+                        const float rh = (float)sum;
+                        rs[(size_t)F * b + r] = make_float2(rh, (float)(sum - (double)rh));
+                    }
+                if ((rc0 = Dn->sepbf.reserve(sizeof(__nv_bfloat16) * sb.size() + sizeof(float2) * rs.size())))
+                    return rc0;
+                d.sepbf = (__nv_bfloat16 *)Dn->sepbf.p;
+                d.Rbf = (float2 *)(d.sepbf + sb.size());
+                CK(cudaMemcpyAsync(d.sepbf, sb.data(), sizeof(__nv_bfloat16) * sb.size(), cudaMemcpyHostToDevice, st));
+                CK(cudaMemcpyAsync(d.Rbf, rs.data(), sizeof(float2) * rs.size(), cudaMemcpyHostToDevice, st));
+                if ((rc0 = encode_bf16_map(&Dn->tmap_sbf, d.sepbf, 6ull * b, b, 128))) return rc0;
+                d.tmap_sepbf = &Dn->tmap_sbf;
             }
         }
         // W = C H^T with exact structural zeros: entries below 2^-40 are the
@@ -1316,6 +1350,50 @@ int aqmp_profile_read(aqmp_kernel_time *out, int max, int *n) {
         ++i;
     }
     *n = std::min(i, std::max(max, 0));
+    return AQMP_OK;
+}
+
+int aqmp_correlate_bf16x2(int b, int dict_id, const uint8_t *blocks, int64_t L, float *corr, float *bound,
+                          void *stream) {
+    g_last_error.clear();
+    if (!corr_sepbf_available(b)) return fail(AQMP_E_UNSUPPORTED, "the BF16 form with rescore serves side 64 only");
+    if (dict_id < 0 || dict_id > 2) return fail(AQMP_E_DICT, "unknown dictionary id %d", dict_id);
+    if (L < 0 || (L > 0 && (!blocks || !corr || !bound))) return fail(AQMP_E_ARG, "bad pointers");
+    if (L == 0) return AQMP_OK;
+    if (L > 0x7fffffffLL) return fail(AQMP_E_UNSUPPORTED, "too many blocks");
+    Ctx *c;
+    int rc;
+    if ((rc = get_ctx(&c))) return rc;
+    std::lock_guard<std::mutex> lock(c->mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    Dict *D;
+    if ((rc = get_dict(c, b, dict_id, st, &D, false))) return rc;
+    const DictDev &d = D->d;
+    if ((rc = c->Y.reserve(sizeof(__nv_bfloat16) * (size_t)L * d.Kpad))) return rc;
+    if ((rc = c->mu_buf.reserve((size_t)L))) return rc;
+    CUtensorMap ysm;
+    if ((rc = encode_bf16_map(&ysm, c->Y.p, (unsigned long long)L * b, b, b))) return rc;
+    CK(launch_gather_blocks(b, d.Kpad, blocks, L, (__nv_bfloat16 *)c->Y.p, nullptr, c->num_sms, st,
+                            (uint8_t *)c->mu_buf.p));
+    CorrArgs ca{};
+    ca.d = &d;
+    ca.Y = (const __nv_bfloat16 *)c->Y.p;
+    ca.fixed_count = L;
+    ca.capacity = (unsigned)L;
+    ca.c0 = (float2 *)corr;
+    ca.tmap_Ysep = &ysm;
+    ca.mu = (const uint8_t *)c->mu_buf.p;
+    ca.ebound = bound;
+    const cudaError_t e = g_prof.run(kname("corr_sepbf", b), st, [&] { return launch_corr_sepbf(ca, st); });
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(st);
+        return fail(AQMP_E_CUDA, "correlation kernel: %s", cudaGetErrorString(e));
+    }
+    CK(cudaStreamSynchronize(st));
+    {
+        std::lock_guard<std::mutex> pl(g_prof.mu);
+        g_prof.resolve();
+    }
     return AQMP_OK;
 }
 

@@ -64,12 +64,15 @@ struct GatherArgs {
     uint32_t *e0;                // [capacity]
     uint8_t *Y8;                 // FP8 form: e4m3(y~ s_l) [capacity][kpad_fp8(n)], or NULL
     float *inv_sl;               // FP8 form: 1 / s_l per leaf
+    uint8_t *mu;                 // BF16 form with rescore: centre on the block's integer
+                                 // mean, written here per leaf (NULL: centre 128)
 };
 cudaError_t launch_gather(const GatherArgs &a, int num_sms, cudaStream_t st);
 
 // Same, for L contiguous row-major b x b blocks (aqmp_correlate).
 cudaError_t launch_gather_blocks(int b, int Kpad, const uint8_t *blocks, long long L,
-                                 __nv_bfloat16 *Y, uint32_t *e0, int num_sms, cudaStream_t st);
+                                 __nv_bfloat16 *Y, uint32_t *e0, int num_sms, cudaStream_t st,
+                                 uint8_t *mu = nullptr);
 cudaError_t launch_gather_blocks_fp8(int b, const uint8_t *blocks, long long L, uint8_t *Y8, float *inv_sl,
                                      int num_sms, cudaStream_t st);
 
@@ -83,6 +86,11 @@ struct DictDev {
     long long *Rs;               // [2][b] row sums R[F][p] = sum_i Bf[F][p][i]
     __nv_bfloat16 *sepd;         // side 64: Bf digits for the tensor cores (corr_sep_tc.cu)
     void *tmap_sepd;             // its CUtensorMap (host copy)
+    // side 64, the BF16 form with rescore: [bf16(B_F); bf16(B_F - bf16(B_F))]
+    // for F = 0, 1, then [|B_0|; |B_1|] rounded up, each 128 rows x b BF16
+    __nv_bfloat16 *sepbf;
+    void *tmap_sepbf;            // its CUtensorMap (host copy), boxes of 128 rows
+    float2 *Rbf;                 // [2][b] row sums sum_i B[F][p][i] as (hi, lo)
     __nv_bfloat16 *limbs;        // [kLimbs][Mpad][Kpad] balanced base-64 digits
     int32_t *Dh, *Dl;            // [M][n]: D_fix = Dh 2^24 + Dl, Dl in [-2^23, 2^23)
     long long *Sh, *Sl;          // per atom: sum_v D_fix = Sh 2^24 + Sl (canonical)
@@ -113,7 +121,10 @@ struct CorrArgs {
     float2 *c0;                  // [capacity][M]
     Counters *ctr;               // may be NULL
     const void *tmap_Y;          // CUtensorMap of Y (tensor-core kernel only)
-    const void *tmap_Ysep;       // Y as [capacity b][b] rows (separable tensor-core kernel)
+    const void *tmap_Ysep;       // Y as [capacity b][b] rows (separable tensor-core kernels)
+    // BF16 form with rescore: the per-leaf centres and the per-atom bounds
+    const uint8_t *mu;           // [capacity] integer mean each leaf's Y is centred on
+    float *ebound;               // [capacity][M] bound on |c0 - the exact form's c0|
 };
 cudaError_t launch_corr_simt(const CorrArgs &a, cudaStream_t st);
 // Exact correlation with the separable fixed-point dictionary (corr_sep.cu):
@@ -123,6 +134,10 @@ cudaError_t launch_corr_sep_simt(const CorrArgs &a, cudaStream_t st);
 // where corr_sep_tc_available() says a kernel exists.
 cudaError_t launch_corr_sep_tc(const CorrArgs &a, cudaStream_t st);
 bool corr_sep_tc_available(int b, int nf);
+// BF16 form with rescore (corr_sepbf_tc.cu): c0 from split BF16 products of
+// the separable form, Y centred on a.mu, and the per-atom bound a.ebound.
+bool corr_sepbf_available(int b);
+cudaError_t launch_corr_sepbf(const CorrArgs &a, cudaStream_t st);
 cudaError_t launch_corr_tc(const CorrArgs &a, cudaStream_t st);
 // Reduced-precision form: one BF16 pass of bf16(D), FP32 accumulation (c0 low words 0).
 cudaError_t launch_corr_tc_bf16(const CorrArgs &a, cudaStream_t st);

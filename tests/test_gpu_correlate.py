@@ -153,3 +153,48 @@ def test_fp8_form_is_within_its_rounding_bound(lib, b, dict_id, L):
         assert np.all(err <= bound), (l, float(np.max(err - bound)))
         worst = max(worst, float(np.max(err)))
     assert worst > 0.0
+
+
+def _scene_blocks(L, seed):
+    from paper_2605_09190_gb300 import synthetic
+    img = synthetic.gradient_scene(512, 512, seed=seed)
+    pw = synthetic.piecewise_scene(512, 512, seed=seed)
+    out = []
+    for l in range(L):
+        src = img if l % 2 == 0 else pw
+        r, c = (l // 2) % 8, (l // 16) % 8
+        out.append(src[64 * r:64 * r + 64, 64 * c:64 * c + 64])
+    return np.ascontiguousarray(np.stack(out))
+
+
+@pytest.mark.parametrize("dict_id,L,kind", [(0, 66, "random"), (0, 160, "scenes"), (1, 5, "random"),
+                                             (2, 7, "scenes"), (0, 1, "random")])
+def test_bf16x2_correlation_is_within_its_bound(lib, dict_id, L, kind):
+    """The BF16 form's correlation (split BF16 products, FP32 accumulation)
+    against the exact form's, atom by atom, within the bound the kernel
+    returns; and that bound against its definition, 25 2^-19 times the
+    atom's mass sum |B[p][i]| |y[i][m] - mu| |B[q][m]| (mu the block's
+    integer mean) plus the centring term's 2^-40 and the 2^-30 by which the
+    exact form's fixed-point rows may differ from the real correlation."""
+    host = _blocks(L, 64, seed=L + dict_id) if kind == "random" else _scene_blocks(L, seed=dict_id)
+    dev = torch.from_numpy(host).cuda()
+    c, e = lib.aqmp_correlate_bf16x2(64, dict_id, dev)
+    ex = lib.aqmp_correlate(64, dict_id, dev, gemm=0)
+    torch.cuda.synchronize()
+    c, e, ex = c.cpu().numpy().astype(np.float64), e.cpu().numpy().astype(np.float64), ex.cpu().numpy().astype(np.float64)
+    got, ref = c[:, :, 0] + c[:, :, 1], ex[:, :, 0] + ex[:, :, 1]
+    err = np.abs(got - ref)
+    assert np.all(err <= e), float(np.max(err - e))
+    fams = _families(64, dict_id)
+    worst = 0.0
+    for l in range(L):
+        y = host[l].astype(np.float64)                     # y[i][m]: row i, column m
+        mu = np.floor(y.mean() + 0.5)
+        Yt = np.abs(y - mu)
+        mass = np.concatenate([(np.abs(B) @ Yt @ np.abs(B).T).T.reshape(-1) for B in fams])   # index q b + p
+        R = np.concatenate([np.outer(B.sum(axis=1), B.sum(axis=1)).T.reshape(-1) for B in fams])
+        lo = 25 * 2.0 ** -19 * mass
+        hi = 25 * 2.0 ** -19 * mass * (1 + 2.0 ** -5) + 2.0 ** -39 * mu * np.abs(R) + 2.0 ** -29   # three BF16 round-ups
+        assert np.all(e[l] >= lo * (1 - 2.0 ** -12)) and np.all(e[l] <= hi)
+        worst = max(worst, float(np.max(err[l] / np.maximum(e[l], 1e-300))))
+    print(f"largest error / bound: {worst:.3f}")
