@@ -67,6 +67,20 @@ extern "C" {
                                       keeping the values within 448), FP32
                                       accumulation, rescaled; then the FP32
                                       form's pursuit; decisions not certified */
+#define AQMP_PREC_BF16_RESCORE 4   /* the BF16 form with rescore: at side 64 the
+                                      correlation from split BF16 tensor-core
+                                      products of the separable form, with a
+                                      per-atom error bound
+                                      (aqmp_correlate_bf16x2); the exact form's
+                                      pursuit, in which every atom that could
+                                      be the argmax under those bounds first
+                                      gets its exact initial correlation
+                                      recomputed from the pixels (at most 8 per
+                                      step; a leaf needing more is redone by the
+                                      exact form); decisions certified as in
+                                      the exact form.  Other sides: the exact
+                                      form.  Needs the DCT+Haar dictionary or a
+                                      single family, any max_block. */
 
 /* aqmp_params.flags */
 #define AQMP_FLAG_INPUT_DEVICE  1u /* plane pointers are device addresses */
@@ -172,6 +186,12 @@ typedef struct {
     uint64_t max_leaf_steps_per_level[8]; /* steps of the level's longest pursuit: the
                                            * level's serial chain (its launch cannot
                                            * end before that pursuit does) */
+    uint64_t rescored_atoms;    /* AQMP_PREC_BF16_RESCORE: exact initial
+                                 * correlations recomputed */
+    uint64_t fallback_leaves;   /* AQMP_PREC_BF16_RESCORE: leaves redone by the
+                                 * exact form */
+    uint64_t rescore_rounds;    /* AQMP_PREC_BF16_RESCORE: rounds of exact
+                                 * recomputation (up to 8 atoms each) */
 } aqmp_stats;
 
 typedef struct aqmp_code aqmp_code;   /* opaque, library-owned result */

@@ -27,6 +27,7 @@ AQMP_PREC_EXACT = 0
 AQMP_PREC_FP32 = 1
 AQMP_PREC_BF16 = 2
 AQMP_PREC_FP8 = 3
+AQMP_PREC_BF16_RESCORE = 4
 AQMP_FLAG_INPUT_DEVICE = 1
 AQMP_FLAG_SIMT_GEMM = 2
 AQMP_FLAG_NO_AUTOTUNE = 4
@@ -57,7 +58,9 @@ class aqmp_stats(ctypes.Structure):
     _fields_ = [("n_leaves", ctypes.c_uint64), ("n_atoms", ctypes.c_uint64), ("attempts", ctypes.c_uint64),
                 ("atom_iterations", ctypes.c_uint64), ("near_tie_leaves", ctypes.c_uint64),
                 ("attempts_per_level", ctypes.c_uint64 * 8), ("iterations_per_level", ctypes.c_uint64 * 8),
-                ("window_steps_per_level", ctypes.c_uint64 * 8), ("max_leaf_steps_per_level", ctypes.c_uint64 * 8)]
+                ("window_steps_per_level", ctypes.c_uint64 * 8), ("max_leaf_steps_per_level", ctypes.c_uint64 * 8),
+                ("rescored_atoms", ctypes.c_uint64), ("fallback_leaves", ctypes.c_uint64),
+                ("rescore_rounds", ctypes.c_uint64)]
 
 
 LEAF_DTYPE = np.dtype([("plane", np.uint32), ("y", np.uint32), ("x", np.uint32), ("atom_off", np.uint32),
@@ -279,7 +282,9 @@ def aqmp_code_stats(code: Code) -> dict:
             "attempts_per_level": list(s.attempts_per_level),
             "iterations_per_level": list(s.iterations_per_level),
             "window_steps_per_level": list(s.window_steps_per_level),
-            "max_leaf_steps_per_level": list(s.max_leaf_steps_per_level)}
+            "max_leaf_steps_per_level": list(s.max_leaf_steps_per_level),
+            "rescored_atoms": s.rescored_atoms, "fallback_leaves": s.fallback_leaves,
+            "rescore_rounds": s.rescore_rounds}
 
 
 def _pinned(n: int, dtype) -> np.ndarray:

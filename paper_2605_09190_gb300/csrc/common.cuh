@@ -59,6 +59,14 @@ struct Counters {
     unsigned int max_steps[kMaxLevels];     // longest pursuit of the level (steps)
     unsigned int queue_count[kMaxLevels + 1];
     unsigned int work_next[kMaxLevels];     // dynamic leaf assignment per level
+    // BF16 form with rescore: atoms whose exact initial correlation was
+    // computed, leaves handed to the exact path, and that path's queue count
+    // and leaf counter
+    unsigned long long rescored[kMaxLevels];
+    unsigned long long resc_rounds[kMaxLevels];
+    unsigned int fallbacks[kMaxLevels];
+    unsigned int fb_count[kMaxLevels];
+    unsigned int work_fb[kMaxLevels];
     unsigned int error;                // first AQMP_E_* code raised on the device
     unsigned int error_info;
 };

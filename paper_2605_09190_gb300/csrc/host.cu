@@ -323,7 +323,7 @@ struct Ctx {
     int cc_major = 0, cc_minor = 0;
     std::mutex mu;
     std::map<int, std::unique_ptr<Dict>> dicts;
-    DeviceBuf planes, staging, queues, Y, e0, c0, counters, ssim_ws, Y8, inv_sl, omp_L, mu_buf, ebound;
+    DeviceBuf planes, staging, queues, Y, e0, c0, counters, ssim_ws, Y8, inv_sl, omp_L, mu_buf, ebound, fbq;
     DeviceBuf leaves_ws, atoms_ws, lo_ws, atom_leaf, cells, perm, new_off, order_status;   // emission -> canonical order
     bool gauss_ready = false;
     Tuner tuner;
@@ -599,7 +599,7 @@ int check_params(const aqmp_params *p) {
     if (p->max_block > kMaxSide) return fail(AQMP_E_UNSUPPORTED, "max_block above %d is not built", kMaxSide);
     if (p->dict_id < 0 || p->dict_id > 2) return fail(AQMP_E_DICT, "unknown dictionary id %d", p->dict_id);
     if (p->precision != AQMP_PREC_EXACT && p->precision != AQMP_PREC_FP32 && p->precision != AQMP_PREC_BF16 &&
-        p->precision != AQMP_PREC_FP8)
+        p->precision != AQMP_PREC_FP8 && p->precision != AQMP_PREC_BF16_RESCORE)
         return fail(AQMP_E_UNSUPPORTED, "unknown precision %d", p->precision);
     return AQMP_OK;
 }
@@ -700,6 +700,9 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
     const bool omp = (P.flags & AQMP_FLAG_OMP) != 0;
     const bool bf16 = P.precision == AQMP_PREC_BF16;
     const bool fp8 = P.precision == AQMP_PREC_FP8;
+    // the BF16 form with rescore: its own correlation and pursuit at the sides
+    // a kernel for it serves (64), the exact form elsewhere
+    const bool resc = P.precision == AQMP_PREC_BF16_RESCORE;
     if (omp) {
         if (P.max_block > 64 || P.precision != AQMP_PREC_EXACT)
             return fail(AQMP_E_UNSUPPORTED, "OMP needs max_block <= 64 and the exact precision");
@@ -764,6 +767,19 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
         if ((rc = c->inv_sl.reserve(sizeof(float) * emax))) return rc;
     }
     if ((rc = c->c0.reserve(sizeof(float2) * cmax))) return rc;
+    if (resc) {
+        unsigned long long rmax = 0, rcap = 0;
+        for (int l = 0; l < nlev; ++l)
+            if (corr_sepbf_available(P.max_block >> l)) {
+                rmax = std::max(rmax, cap[l] * dicts[l]->d.M);
+                rcap = std::max(rcap, cap[l]);
+            }
+        if (rmax) {
+            if ((rc = c->ebound.reserve(sizeof(float) * rmax))) return rc;
+            if ((rc = c->mu_buf.reserve(rcap))) return rc;
+            if ((rc = c->fbq.reserve(sizeof(QueueEntry) * rcap))) return rc;
+        }
+    }
     // the pursuit kernels emit into the workspace; the ordering pass writes
     // the outputs, allocated per call from the stream-ordered pool at their
     // worst-case size
@@ -834,7 +850,7 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
     const OrderOut outs{code->leaves, code->atoms, code->alpha_lo};
     std::memcpy(c->host_call + out_off, &outs, sizeof outs);
     Counters *ctr = (Counters *)c->counters.p;
-    const bool exact = P.precision == AQMP_PREC_EXACT;
+    const bool exact = P.precision == AQMP_PREC_EXACT || resc;     // double-float certified pursuit
 
     // A configuration whose kernel choices are settled is captured as a CUDA
     // graph on its second call and replayed from then on: everything from
@@ -845,7 +861,7 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
         if (!tune) return true;
         for (int l = 0; l < nlev; ++l) {
             const int b = P.max_block >> l;
-            if (!simt && !bf16 && !fp8 && corr_sep_tc_available(b, dicts[l]->d.nf) &&
+            if (!simt && !bf16 && !fp8 && !(resc && corr_sepbf_available(b)) && corr_sep_tc_available(b, dicts[l]->d.nf) &&
                 c->tuner.slot(Tuner::CORR, b, P.dict_id, P.precision, cap[l]).chosen < 0)
                 return false;
             if (!alt_threads && !omp && mp_has_variant(b, dicts[l]->d.nf) &&
@@ -899,6 +915,8 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
         GatherArgs ga{b, d.n, d.Kpad, lv.queue, lv.count, lv.capacity, (const PlaneDesc *)c->planes.p,
                       (__nv_bfloat16 *)c->Y.p, (uint32_t *)c->e0.p, fp8 ? (uint8_t *)c->Y8.p : nullptr,
                       fp8 ? (float *)c->inv_sl.p : nullptr};
+        const bool resc_l = resc && corr_sepbf_available(b);
+        if (resc_l) ga.mu = (uint8_t *)c->mu_buf.p;
         CK(g_prof.run(kname("gather", b), st, [&] { return launch_gather(ga, c->num_sms, st); }));
 
         CorrArgs ca{};
@@ -930,7 +948,11 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
             return g_prof.run(kname("corr_sep", b), st, [&] { return launch_corr_sep_simt(ca, st); });
         };
         const bool tc_ok = corr_sep_tc_available(b, d.nf);
-        if (bf16) {
+        if (resc_l) {
+            ca.mu = (const uint8_t *)c->mu_buf.p;
+            ca.ebound = (float *)c->ebound.p;
+            CK(g_prof.run(kname("corr_sepbf", b), st, [&] { return launch_corr_sepbf(ca, st); }));
+        } else if (bf16) {
             CK(g_prof.run(kname("corr_bf16", b), st, [&] { return launch_corr_tc_bf16(ca, st); }));
         } else if (fp8) {
             CK(g_prof.run(kname("corr_fp8", b), st,
@@ -969,8 +991,20 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
         ma.omp_L = (double *)c->omp_L.p;
         ma.omp_slots = c->num_sms;
         ma.omp_L_doubles = omp_doubles;
+        ma.fam0 = d.fam0;
+        if (resc_l) {
+            ma.ebound = (const float *)c->ebound.p;
+            ma.Yc = (const __nv_bfloat16 *)c->Y.p;
+            ma.Kpad = d.Kpad;
+            ma.mu = (const uint8_t *)c->mu_buf.p;
+            ma.Bs = d.Bs;
+            ma.Rs = d.Rs;
+            ma.fb_queue = (QueueEntry *)c->fbq.p;
+            ma.fb_count = &ctr->fb_count[l];
+            ma.fb_capacity = lv.capacity;
+        }
         auto mp = [&](int v) {
-            return g_prof.run(kname(exact ? "mp" : "mp_fp32", b), st,
+            return g_prof.run(kname(resc_l ? "mp_resc" : exact ? "mp" : "mp_fp32", b), st,
                               [&] { return launch_mp(ma, d.nf, exact, v, c->num_sms, st); });
         };
         if (omp) {
@@ -985,6 +1019,27 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
                 const int v = Tuner::next(ts);
                 CK(c->tuner.timed(ts, v, st, [&] { return mp(v); }));
             }
+        }
+        if (resc_l) {
+            // the leaves the rescore handed back, through the exact form: the
+            // gather centred on 128, the exact correlation, the exact pursuit
+            // (its own leaf counter), children and emission as for any leaf
+            GatherArgs gf = ga;
+            gf.queue = (const QueueEntry *)c->fbq.p;
+            gf.count = &ctr->fb_count[l];
+            gf.mu = nullptr;
+            CK(g_prof.run(kname("gather_fb", b), st, [&] { return launch_gather(gf, c->num_sms, st); }));
+            CorrArgs cf = ca;
+            cf.count = &ctr->fb_count[l];
+            cf.mu = nullptr;
+            cf.ebound = nullptr;
+            CK(g_prof.run(kname("corr_fb", b), st, [&] { return launch_corr_sep_tc(cf, st); }));
+            MPArgs mf = ma;
+            mf.lv.queue = (const QueueEntry *)c->fbq.p;
+            mf.lv.count = &ctr->fb_count[l];
+            mf.work = &ctr->work_fb[l];
+            mf.ebound = nullptr;
+            CK(g_prof.run(kname("mp_fb", b), st, [&] { return launch_mp(mf, d.nf, true, 0, c->num_sms, st); }));
         }
     }
 
@@ -1105,6 +1160,9 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
         s.max_leaf_steps_per_level[l] = h.max_steps[l];
         s.attempts += h.attempts[l];
         s.atom_iterations += h.iterations[l];
+        s.rescored_atoms += h.rescored[l];
+        s.rescore_rounds += h.resc_rounds[l];
+        s.fallback_leaves += h.fallbacks[l];
     }
     *out = code.release();
     return AQMP_OK;

@@ -30,6 +30,21 @@ struct MPArgs {
     double *omp_L;
     int omp_slots;
     unsigned long long omp_L_doubles;
+    // the BF16 form with rescore (side 64; ebound NULL: off): the BF16
+    // correlation's per-atom bounds, the leaves' mean-centred pixels and their
+    // centres, the exact form's fixed-point rows and row sums, and the queue
+    // of leaves handed to the exact path
+    const float *ebound;
+    const __nv_bfloat16 *Yc;
+    int Kpad;
+    const uint8_t *mu;
+    const int2 *Bs;
+    const long long *Rs;
+    QueueEntry *fb_queue;
+    unsigned *fb_count;
+    unsigned fb_capacity;
+    unsigned *work;              // leaf counter (NULL: ctr->work_next[level])
+    int fam0;                    // family of a single-family dictionary
 };
 // variant 0: the default launch shape; 1: the alternate one (other threads
 // per leaf at sides 16 and 32, two resident CTAs per SM at side 64; two

@@ -45,6 +45,8 @@
 #include "common.cuh"
 #include "kernels.h"
 #include "mp_step.cuh"
+#include "sep.cuh"
+#include <cuda_fp16.h>
 
 
 namespace aqmp {
@@ -59,7 +61,79 @@ namespace aqmp {
 // thread follow): 1 keeps the side-64 state in registers for the fastest
 // single pursuit, 2 halves the registers so two leaves share an SM, which
 // wins when leaves outnumber SMs.
-template <int B, int T, int NF, bool DF, int MINB = (T > 32 ? 1 : 2)>
+// The BF16 form with rescore: the exact form's initial correlation of atoms
+// list[0..cnt) (cnt <= 8) of one leaf, one warp per atom, each as the exact
+// kernels compute it (sep.cuh): Z~[p][m] = sum_i Bf[p][i] y~[i][m] for
+// m = lane and lane + 32 from the leaf's pixels (pixT[i b + m] = y - 128),
+// T = sum_m Bf[q][m] Z~[p][m] + 128 R[p] R[q] in int128, rounded once;
+// rv[w] receives that value minus the BF16 correlation's, as a double-float.
+// Out of line: rounds are rare, and keeping their code out of the step keeps
+// the step's code in the instruction cache.
+template <int B, int NF>
+__device__ __noinline__ void rescore_atoms(const MPArgs &a, unsigned leaf, const int8_t *pixT,
+                                           const uint32_t *list, uint32_t cnt, float2 *rv, long long *rowbuf) {
+    static_assert(B == 64, "two columns per lane");
+    constexpr uint32_t n = B * B;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if ((uint32_t)warp >= cnt) return;
+    const uint32_t j = list[warp];
+    const int F = NF == 2 ? (int)(j >= n) : a.fam0;
+    const uint32_t f = j % n, p = f % B, q = f / B;
+    const float2 approx = lane == 0 ? a.c0[(size_t)leaf * (NF * n) + j] : make_float2(0.0f, 0.0f);
+    // row p of the fixed-point 1-D basis (its two 24-bit limbs) into this
+    // warp's buffer, two entries a lane
+    int2 *row = reinterpret_cast<int2 *>(rowbuf) + warp * B;
+    {
+        const int2 *rp = a.Bs + ((size_t)F * B + p) * B;
+        row[lane] = rp[lane];
+        row[lane + 32] = rp[lane + 32];
+    }
+    const int2 *rq = a.Bs + ((size_t)F * B + q) * B;
+    const int2 w0 = rq[lane], w1 = rq[lane + 32];
+    __syncwarp();
+    // columns m = lane and lane + 32: the hi- and lo-limb sums as 32 x 32 ->
+    // 64-bit multiply-adds (|limb y| < 2^31, 64 terms < 2^37), then
+    // Z = 2^24 Zhi + Zlo (< 2^60)
+    long long h0 = 0, l0 = 0, h1 = 0, l1 = 0;
+#pragma unroll 16
+    for (int i = 0; i < B; ++i) {
+        const int2 w = row[i];
+        const int y0 = pixT[i * B + lane], y1 = pixT[i * B + lane + 32];
+        h0 += (long long)w.y * y0;
+        l0 += (long long)w.x * y0;
+        h1 += (long long)w.y * y1;
+        l1 += (long long)w.x * y1;
+    }
+    const long long z0 = h0 * 16777216ll + l0, z1 = h1 * 16777216ll + l1;
+    __int128 acc = (__int128)((long long)w0.y * 16777216ll + (long long)w0.x) * z0 +
+                   (__int128)((long long)w1.y * 16777216ll + (long long)w1.x) * z1;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long lo = __shfl_xor_sync(0xffffffffu, (unsigned long long)acc, off);
+        const long long hi = __shfl_xor_sync(0xffffffffu, (long long)(acc >> 64), off);
+        acc += (__int128)hi * ((__int128)1 << 64) + (__int128)lo;
+    }
+    if (lane == 0) {
+        const __int128 T = acc + (__int128)(128ll * a.Rs[F * B + p]) * a.Rs[F * B + q];
+        const df d = df_sub(int128_to_df(T), df{approx.x, approx.y});
+        rv[warp] = make_float2(d.hi, d.lo);
+    }
+}
+
+// RESC: the BF16 form with rescore (side 64, several warps per leaf, double-
+// float state).  The leaf starts from the BF16 correlation c~0, within e_j
+// of the exact form's c0 for every atom j; a shared bitmask records which
+// atoms already carry their exact value.  Before a step is taken, every atom
+// that could be the argmax -- an upper bound |c_j| + e_j (0 once exact) at
+// or above the leader's lower bound less the full-precision window -- must
+// be exact: its c0 recomputed from the pixels (rescore_atoms) and the
+// difference added to its running correlation (the Gram updates applied so
+// far are the same for both starts).  A round that has to rescore fills its
+// 8 slots with further non-exact atoms above lambda times the leader (lambda
+// adapted per leaf), the likely leaders of the next steps.  The step is then
+// decided as in the exact form.  More than 8 atoms that must be rescored in
+// one step hand the leaf, untouched, to the exact path.
+template <int B, int T, int NF, bool DF, int MINB = (T > 32 ? 1 : 2), bool RESC = false>
 __global__ void __launch_bounds__(T > 32 ? T : 256, MINB)
 mp_kernel(MPArgs a) {
     constexpr int n = B * B;
@@ -67,6 +141,7 @@ mp_kernel(MPArgs a) {
     constexpr int E = (M + T - 1) / T;
     static_assert(T % B == 0, "thread count must be a multiple of the side");
     constexpr int NW = T / 32;               // warps per group (T > 32)
+    static_assert(!RESC || (DF && T > 32 && NW >= 8 && E <= 32 && (M % T) == 0), "rescore layout");
     // SPLIT: the first E/2 elements of every thread are DCT atoms and the
     // rest Haar atoms, each family cached separately; otherwise one group.
     constexpr bool SPLIT = NF == 2 && (n % T) == 0 && (E % 2) == 0;
@@ -93,7 +168,19 @@ mp_kernel(MPArgs a) {
     unsigned long long *sRk = reinterpret_cast<unsigned long long *>(sMisc + 12); // [NW]
     uint32_t *sRj = reinterpret_cast<uint32_t *>(sRk + NW);      // [NW]
     StepRec *sSteps = reinterpret_cast<StepRec *>(sRj + NW);
-
+    // RESC: the leaf's pixels (transposed), its bounds (FP16, rounded up),
+    // the exact atoms (bitmask), the rescore's partial sums and a few words
+    unsigned char *resc = reinterpret_cast<unsigned char *>(sSteps + (size_t)(T == 32 ? blockDim.x / 32 : 1) * a.lv.k);
+    resc = reinterpret_cast<unsigned char *>(((uintptr_t)resc + 15) & ~(uintptr_t)15);
+    int8_t *sPix = reinterpret_cast<int8_t *>(resc);
+    __half *sE = reinterpret_cast<__half *>(resc + B * B);                 // [M]
+    uint32_t *sEx = reinterpret_cast<uint32_t *>(sE + M);                  // [M / 32]
+    unsigned long long *sP = reinterpret_cast<unsigned long long *>(sEx + (M + 31) / 32);   // [16]
+    float2 *sRv = reinterpret_cast<float2 *>(sP + 16);                     // [8] one per rescored atom
+    uint32_t *sRW = reinterpret_cast<uint32_t *>(sRv + 8);                 // [0..1] counts, [2..9] atoms
+    float *sEm = reinterpret_cast<float *>(sRW + 16);                      // [NW]
+    long long *sRow = reinterpret_cast<long long *>(resc + ((B * B + NF * B * B * 2 + (NF * B * B + 31) / 32 * 4 +
+                                                              16 * 8 + 8 * 8 + 16 * 4 + NW * 4 + 15) & ~15));  // [8][B]
     const LevelArgs &lv = a.lv;
     __shared__ unsigned long long sCnt[3];              // per-CTA work counters (T == 32)
     __shared__ unsigned sMaxT;
@@ -113,8 +200,8 @@ mp_kernel(MPArgs a) {
     const int p_own = lane % B;
     const unsigned count = *lv.count;
     const int k = lv.k;
-    unsigned *work = &a.ctr->work_next[lv.level];
-    unsigned long long n_attempts = 0, n_steps = 0, n_windows = 0;
+    unsigned *work = a.work ? a.work : &a.ctr->work_next[lv.level];
+    unsigned long long n_attempts = 0, n_steps = 0, n_windows = 0, n_resc = 0, n_rounds = 0;
     unsigned max_t = 0;
 
     for (;;) {
@@ -166,6 +253,36 @@ mp_kernel(MPArgs a) {
                 ch[s] = 0.0f;
                 cl[s] = 0.0f;
             }
+        }
+
+        float my_emax = 0.0f;               // RESC: largest bound of this thread's non-exact atoms
+        uint32_t exm = 0u;                  // RESC: this thread's exact slots (the bitmask's own bits)
+        float lam = 0.5f;                   // RESC: speculative threshold, relative to the leader
+        float emax_all = 0.0f;              // RESC: largest bound of the leaf's non-exact atoms
+        bool fallback = false;
+        if constexpr (RESC) {
+#pragma unroll
+            for (int s2 = 0; s2 < E; ++s2) {
+                const uint32_t j = (uint32_t)(lane + T * s2);
+                const __half e = __float2half_ru(a.ebound[(size_t)leaf * M + j]);
+                my_emax = fmaxf(my_emax, __half2float(e));       // the value the scans compare with
+                sE[j] = e;
+            }
+            for (int w = lane; w < (M + 31) / 32; w += T) sEx[w] = 0u;
+            if (lane < 2) sRW[lane] = 0u;
+            {
+                float v = my_emax;
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
+                if ((lane & 31) == 0) sEm[lane >> 5] = v;
+            }
+            const int centre = (int)a.mu[leaf] - 128;
+            for (int v = lane; v < n; v += T)
+                sPix[(v % B) * B + v / B] =
+                    (int8_t)((int)__bfloat162float(a.Yc[(size_t)leaf * a.Kpad + v]) + centre);
+            __syncthreads();
+#pragma unroll
+            for (int w = 0; w < NW; ++w) emax_all = fmaxf(emax_all, sEm[w]);
         }
 
         int t = 0, windows = 0;
@@ -231,6 +348,144 @@ mp_kernel(MPArgs a) {
                 best = group_best(2);
             }
             if ((best.P >> 32) == 0ull) break;   // every correlation is exactly zero
+            if constexpr (RESC) {
+                // certify the leader against the bounds: every atom whose
+                // upper bound |c| + e reaches the leader's lower bound less the
+                // full-precision window must be exact before the step is taken.
+                // The per-step test is a branch-free mask over the thread's
+                // slots against its largest bound; the exact bounds are read
+                // only for the few slots it leaves
+                uint32_t newly = 0u;
+                for (;;) {
+                    const uint32_t jb = top2_index(best);
+                    const float amb = top2_amax(best);
+                    const bool exb = (sEx[jb >> 5] >> (jb & 31)) & 1u;
+                    const float eb = exb ? 0.0f : __half2float(sE[jb]);
+                    const float L = __fsub_rd(__fsub_rd(amb, eb), __fadd_ru(__fmul_ru(amb, 0x1p-20f), pre));
+                    // no atom can reach the leader: nothing to exchange
+                    if (exb && __fadd_ru(__uint_as_float(best.k2), emax_all) < L) break;
+                    float mine = top2_amax(top[0]);
+#pragma unroll
+                    for (int g = 1; g < NG; ++g) mine = fmaxf(mine, top2_amax(top[g]));
+                    bool found = false;
+                    if (__fadd_ru(mine, my_emax) >= L) {
+                        const float thr = __fsub_rd(L, my_emax);
+                        uint32_t cm = 0u;
+#pragma unroll
+                        for (int s2 = 0; s2 < E; ++s2) cm |= (fabsf(ch[s2]) >= thr ? 1u : 0u) << s2;
+                        cm &= ~exm;
+                        while (cm) {
+                            const int s2 = __ffs(cm) - 1;
+                            cm &= cm - 1u;
+                            float m = 0.0f;
+#pragma unroll
+                            for (int s3 = 0; s3 < E; ++s3) m = s3 == s2 ? fabsf(ch[s3]) : m;
+                            const uint32_t j = (uint32_t)(lane + T * s2);
+                            if (__fadd_ru(m, __half2float(sE[j])) >= L) {
+                                const uint32_t idx = atomicAdd(&sRW[0], 1u);
+                                if (idx < 8u) sRW[2 + idx] = j;
+                                found = true;
+                            }
+                        }
+                    }
+                    if (__syncthreads_or(found) == 0) break;          // nothing to rescore
+                    const uint32_t cnt = min(sRW[0], 9u);
+                    newly += cnt;
+                    if (newly > 8u) { fallback = true; break; }
+                    // fill the round with the likely next leaders: non-exact atoms
+                    // above lam times the leader (not already listed), counted per
+                    // warp (one shared atomic per warp), placed while there is room
+                    uint32_t qmask = 0u;
+                    if (mine >= lam * amb) {
+                        const float thq = lam * amb;
+#pragma unroll
+                        for (int s2 = 0; s2 < E; ++s2) qmask |= (fabsf(ch[s2]) >= thq ? 1u : 0u) << s2;
+                        qmask &= ~exm;
+                        // drop the ones listed above (their owner is this thread)
+                        for (uint32_t w = 0; w < cnt; ++w) {
+                            const uint32_t j = sRW[2 + w];
+                            if (j % (uint32_t)T == (uint32_t)lane) qmask &= ~(1u << (j / (uint32_t)T));
+                        }
+                    }
+                    {
+                        const uint32_t qc = (uint32_t)__popc(qmask);
+                        uint32_t incl = qc;
+#pragma unroll
+                        for (int off = 1; off < 32; off <<= 1) {
+                            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
+                            if ((lane & 31) >= off) incl += v;
+                        }
+                        const uint32_t wtot = __shfl_sync(0xffffffffu, incl, 31);
+                        uint32_t wbase = 0u;
+                        if ((lane & 31) == 31 && wtot) wbase = atomicAdd(&sRW[1], wtot);
+                        wbase = __shfl_sync(0xffffffffu, wbase, 31);
+                        uint32_t pos = cnt + wbase + incl - qc;
+                        while (qmask && pos < 8u) {
+                            const int s2 = __ffs(qmask) - 1;
+                            qmask &= qmask - 1u;
+                            sRW[2 + pos] = (uint32_t)(lane + T * s2);
+                            ++pos;
+                        }
+                    }
+                    __syncthreads();
+                    const uint32_t spec = sRW[1];
+                    const uint32_t tot = min(8u, cnt + spec);
+                    rescore_atoms<B, NF>(a, leaf, sPix, sRW + 2, tot, sRv, sRow);
+                    // steer toward 8..32 atoms above the threshold
+                    lam = spec > 32u ? 0.5f * (1.0f + lam) : spec < 8u ? 0.5f * lam : lam;
+                    __syncthreads();
+                    if (lane == 0) {
+                        sRW[0] = 0u;
+                        sRW[1] = 0u;
+                        n_resc += tot;
+                        ++n_rounds;
+                    }
+                    // into the owners' registers: one predicated pass per atom
+                    uint32_t touched = 0u;               // bit g: family g's summary to redo
+                    bool redo_e = false;                 // the thread's largest bound left with it
+                    for (uint32_t w = 0; w < tot; ++w) {
+                        const uint32_t j = sRW[2 + w];
+                        if (j % (uint32_t)T != (uint32_t)lane) continue;
+                        const uint32_t sj = j / (uint32_t)T;
+                        float vh = 0.0f, vl = 0.0f;
+#pragma unroll
+                        for (int s2 = 0; s2 < E; ++s2) {
+                            vh = (uint32_t)s2 == sj ? ch[s2] : vh;
+                            vl = (uint32_t)s2 == sj ? cl[s2] : vl;
+                        }
+                        const float2 d = sRv[w];
+                        const df c = df_add(df{vh, vl}, df{d.x, d.y});
+#pragma unroll
+                        for (int s2 = 0; s2 < E; ++s2) {
+                            ch[s2] = (uint32_t)s2 == sj ? c.hi : ch[s2];
+                            cl[s2] = (uint32_t)s2 == sj ? c.lo : cl[s2];
+                        }
+                        exm |= 1u << sj;
+                        atomicOr(&sEx[j >> 5], 1u << (j & 31));
+                        touched |= 1u << (sj / (uint32_t)G);
+                        redo_e |= __half2float(sE[j]) >= my_emax;
+                    }
+                    if (touched & 1u) top[0] = zero_and_rescan<T, E, G, 0>(ch, cl, lane, kNone);
+                    if (NG > 1 && (touched & 2u)) top[NG - 1] = zero_and_rescan<T, E, G, G>(ch, cl, lane, kNone);
+                    if (redo_e) {
+                        my_emax = 0.0f;
+                        for (int s2 = 0; s2 < E; ++s2)
+                            if (!((exm >> s2) & 1u)) my_emax = fmaxf(my_emax, __half2float(sE[lane + T * s2]));
+                    }
+                    {
+                        float v = my_emax;
+#pragma unroll
+                        for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
+                        if ((lane & 31) == 0) sEm[lane >> 5] = v;
+                    }
+                    __syncthreads();
+                    emax_all = sEm[0];
+#pragma unroll
+                    for (int w = 1; w < NW; ++w) emax_all = fmaxf(emax_all, sEm[w]);
+                    best = group_best(2);
+                }
+                if (fallback || (best.P >> 32) == 0ull) break;
+            }
             uint32_t j1 = top2_index(best);
             const float amax = top2_amax(best);
             df alpha = df{top2_negative(best) ? -amax : amax, best.lo1};
@@ -396,6 +651,17 @@ mp_kernel(MPArgs a) {
             }
             ++t;
         }
+        if (RESC && fallback) {
+            // more candidates than the rescore takes: the exact path redoes the leaf
+            if (lane == 0) {
+                const unsigned slot = atomicAdd(a.fb_count, 1u);
+                if (slot < a.fb_capacity) a.fb_queue[slot] = qe;
+                else raise_error(a.ctr, kDevErrQueueOverflow, 5u);
+                atomicAdd(&a.ctr->fallbacks[lv.level], 1u);
+            }
+            __syncthreads();
+            continue;
+        }
 
         // group-wide outcome of the certification
         bool tie_any;
@@ -499,6 +765,10 @@ mp_kernel(MPArgs a) {
         if (n_windows) atomicAdd(&a.ctr->window_steps[lv.level], n_windows);
         atomicMax(&a.ctr->max_steps[lv.level], max_t);
     }
+    if (RESC && lane == 0 && n_resc) {
+        atomicAdd(&a.ctr->rescored[lv.level], n_resc);
+        atomicAdd(&a.ctr->resc_rounds[lv.level], n_rounds);
+    }
 }
 
 template <int B, int T, int NF>
@@ -511,12 +781,17 @@ static size_t mp_smem_bytes(int k, int groups) {
     return bytes;
 }
 
-template <int B, int T, int NF, bool DF, int MINB = (T > 32 ? 1 : 2)>
+template <int B, int T, int NF, bool DF, int MINB = (T > 32 ? 1 : 2), bool RESC = false>
 static cudaError_t launch_mp_t(const MPArgs &a, int num_sms, cudaStream_t st) {
     const int block = (T == 32) ? 256 : T;
     const int groups = (T == 32) ? block / 32 : 1;
-    const size_t smem = mp_smem_bytes<B, T, NF>(a.lv.k, groups);
-    auto kern = mp_kernel<B, T, NF, DF, MINB>;
+    const size_t smem = mp_smem_bytes<B, T, NF>(a.lv.k, groups) +
+                        (RESC ? 16 + B * B + NF * B * B * 2 + (NF * B * B + 31) / 32 * 4 + 16 * 8 + 8 * sizeof(float2) +
+                                    16 * sizeof(uint32_t) + (T / 32) * sizeof(float) + 16 + 8 * B * sizeof(long long)
+                              : 0);
+    if (RESC && (!a.ebound || !a.Yc || !a.mu || !a.Bs || !a.Rs || !a.fb_queue || !a.fb_count))
+        return cudaErrorInvalidValue;
+    auto kern = mp_kernel<B, T, NF, DF, MINB, RESC>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -850,6 +1125,9 @@ static cudaError_t launch_mp_prec(const MPArgs &a, int nf, int variant, int num_
                 return variant ? launch_mp_t<32, AQMP_MP_T32_ALT, 2, DF>(a, num_sms, st)
                                : launch_mp_t<32, AQMP_MP_T32, 2, DF>(a, num_sms, st);
             case 64:
+                if (DF && a.ebound)
+                    return variant ? launch_mp_t<64, AQMP_MP_T64, 2, true, 2, true>(a, num_sms, st)
+                                   : launch_mp_t<64, AQMP_MP_T64, 2, true, 1, true>(a, num_sms, st);
                 return variant ? launch_mp_t<64, AQMP_MP_T64, 2, DF, 2>(a, num_sms, st)
                                : launch_mp_t<64, AQMP_MP_T64, 2, DF>(a, num_sms, st);
             case 128: return launch_mp_cluster(a, 2, DF, num_sms, st);
@@ -860,7 +1138,9 @@ static cudaError_t launch_mp_prec(const MPArgs &a, int nf, int variant, int num_
             case 8: return launch_mp_t<8, 32, 1, DF>(a, num_sms, st);
             case 16: return launch_mp_t<16, 32, 1, DF>(a, num_sms, st);
             case 32: return launch_mp_t<32, AQMP_MP_T32, 1, DF>(a, num_sms, st);
-            case 64: return launch_mp_t<64, AQMP_MP_T64, 1, DF>(a, num_sms, st);
+            case 64:
+                if (DF && a.ebound) return launch_mp_t<64, AQMP_MP_T64, 1, true, 1, true>(a, num_sms, st);
+                return launch_mp_t<64, AQMP_MP_T64, 1, DF>(a, num_sms, st);
             case 128: return launch_mp_cluster(a, 1, DF, num_sms, st);
         }
     }
