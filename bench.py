@@ -780,7 +780,8 @@ def run_omp(args):
 
 PRECISION_ROOT = 128
 PRECISION_WORKLOAD = ("one 4096x4096 RGB synthetic image ({scene} scene per channel, seeds 0..2), RMSE tol 2, "
-                      "quadtree 128->4, k=b^2/4, DCT-II+Haar: exact form vs plain FP32, BF16 and FP8 forms")
+                      "quadtree {root}->4, k=b^2/4, DCT-II+Haar: exact form vs plain FP32, BF16, FP8 and "
+                      "BF16+rescore forms")
 
 
 def run_precision(args):
@@ -800,7 +801,7 @@ def run_precision(args):
     npix = 3 * n * n
     stream = torch.cuda.current_stream()
     forms = {"exact": aqmp.AQMP_PREC_EXACT, "fp32": aqmp.AQMP_PREC_FP32, "bf16": aqmp.AQMP_PREC_BF16,
-             "fp8": aqmp.AQMP_PREC_FP8}
+             "fp8": aqmp.AQMP_PREC_FP8, "bf16_rescore": aqmp.AQMP_PREC_BF16_RESCORE}
     out = {}
     with ClockSampler(local) as clocks:
         for name, prec in forms.items():
@@ -865,7 +866,8 @@ def run_precision(args):
                           "ms_per_step": 1e3 * out["exact"]["s"] / args.steps, "higher_is_better": True,
                           "scaling": "weak", "vs_baseline": None, "dtype": "bf16-limb tensor GEMM + f32x2 pursuit",
                           "data": "synthetic",
-                          "config": {"workload": PRECISION_WORKLOAD.format(scene=args.scene), "pixels_per_step": npix,
+                          "config": {"workload": PRECISION_WORKLOAD.format(scene=args.scene, root=args.root or PRECISION_ROOT),
+                                     "pixels_per_step": npix,
                                      "input": "device-resident",
                                      "l2": "inputs (50 M px) and working set exceed L2"},
                           "fp32_form": {"value": weak_scaling_value(npix, args.steps, out["fp32"]["s"], world),
@@ -878,6 +880,15 @@ def run_precision(args):
                                        "unit": "MP/s", "leaves": agree["fp8"][0],
                                        "same_leaves_share": agree["fp8"][1],
                                        "same_atom_choices_share": agree["fp8"][2]},
+                          "bf16_rescore_form": {
+                              "value": weak_scaling_value(npix, args.steps, out["bf16_rescore"]["s"], world),
+                              "unit": "MP/s", "leaves": agree["bf16_rescore"][0],
+                              "same_leaves_share": agree["bf16_rescore"][1],
+                              "same_atom_choices_share": agree["bf16_rescore"][2],
+                              "rescored_atoms": out["bf16_rescore"]["stats"]["rescored_atoms"],
+                              "rescore_rounds": out["bf16_rescore"]["stats"]["rescore_rounds"],
+                              "fallback_leaves": out["bf16_rescore"]["stats"]["fallback_leaves"],
+                              "note": "the rescore serves side 64; side-128 leaves take the exact path"},
                           "leaves": {"exact": len(le), "fp32": agree["fp32"][0]},
                           "per_level": {f"b{(args.root or PRECISION_ROOT) >> i}": {
                               "attempts": out["exact"]["stats"]["attempts_per_level"][i],

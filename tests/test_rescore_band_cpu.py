@@ -69,3 +69,45 @@ def test_bf16_rescore_band_along_the_oracle_pursuits():
     # the band grows past 8 within every pursuit that runs long: a top-8
     # rescore cannot certify the late steps of these blocks
     assert min(v[0] for v in report.values()) < 1.0
+
+
+def _split_band_sizes(block, tol):
+    """The band of the BF16 form with rescore: split BF16 operands (error at
+    most 25 2^-19 of each atom's mass sum |B[p][i]| |y[i][m] - mu| |B[q][m]|,
+    mu the block's integer mean), exact updates, and atoms staying exact once
+    rescored; returns, per step, how many atoms not yet exact the step must
+    rescore."""
+    C, H = oracle.dct_1d(B), oracle.haar_1d(B)
+    enc = oracle.encode([block], [tol], min_block=B, max_block=B)
+    aj, aa = enc.leaf_atoms(0)
+    y = block.astype(np.float64)
+    Yt = np.abs(y - np.floor(y.mean() + 0.5))
+    e = 25 * 2.0 ** -19 * np.concatenate([(np.abs(M) @ Yt @ np.abs(M).T).T.reshape(-1) for M in (C, H)])
+    exact = np.zeros(2 * B * B, bool)
+    R = y.copy()
+    new = []
+    for t in range(len(aj)):
+        c = np.abs(np.concatenate([(C @ R @ C.T).T.reshape(-1), (H @ R @ H.T).T.reshape(-1)]))
+        ee = np.where(exact, 0.0, e)
+        lead = np.max(c - ee)
+        cand = (c + ee >= lead) & ~exact
+        new.append(int(cand.sum()))
+        exact |= cand
+        j, alpha = int(aj[t]), float(aa[t])
+        Bm = C if j < B * B else H
+        f = j % (B * B)
+        R -= alpha * np.outer(Bm[f % B], Bm[f // B])
+    return np.array(new)
+
+
+def test_split_bf16_band_with_per_atom_bounds_is_narrow():
+    """The form that is built: along the oracle's pursuits of gradient and
+    piecewise blocks at tol 2 at most 8 atoms need rescoring in every step,
+    and about one new atom per step on average."""
+    img = synthetic.gradient_scene(512, 512, seed=2)
+    pw = synthetic.piecewise_scene(512, 512, seed=1)
+    sizes = [_split_band_sizes(img[64 * r:64 * r + 64, 64 * (r + 1):64 * (r + 2)], 2.0) for r in range(3)]
+    sizes.append(_split_band_sizes(pw[64:128, 64:128], 4.0))
+    cat = np.concatenate(sizes)
+    print(f"steps {len(cat)}, largest per-step rescore count {cat.max()}, mean {cat.mean():.2f}")
+    assert cat.max() <= 8 and cat.mean() <= 1.5
