@@ -825,7 +825,12 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
             d.pitch = pl.pitch;
         } else {
             uint8_t *dst = (uint8_t *)c->staging.p + soff;
-            CK(cudaMemcpy2DAsync(dst, pl.width, pl.pixels, pl.pitch, pl.width, pl.height, cudaMemcpyHostToDevice, st));
+            // one linear copy for a contiguous plane (faster than the strided form)
+            if (pl.pitch == pl.width)
+                CK(cudaMemcpyAsync(dst, pl.pixels, (size_t)pl.height * pl.width, cudaMemcpyHostToDevice, st));
+            else
+                CK(cudaMemcpy2DAsync(dst, pl.width, pl.pixels, pl.pitch, pl.width, pl.height, cudaMemcpyHostToDevice,
+                                     st));
             d.pix = dst;
             d.pitch = pl.width;
             soff += (unsigned long long)pl.height * pl.width;
