@@ -43,11 +43,17 @@ __device__ __forceinline__ long long mul_wide(int32_t a, int32_t b) { return (lo
 
 }  // namespace
 
+// Threads per CTA: at side 128 the leaf's Z~ (192 KB of limbs) leaves room
+// for one CTA per SM, so that CTA takes 768 threads to hide the latency of
+// its loads; 256 elsewhere.
+template <int B>
+constexpr int sep_threads() { return B >= 128 ? 768 : 256; }
+
 // One CTA handles G leaves at a time (grid-stride over the leaves); for each
 // family it runs stage 1 into shared memory (Z~ as limbs, row p, column m),
 // then stage 2 with each thread owning one q and PT values of p.
 template <int B>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(sep_threads<B>())
 corr_sep_simt_kernel(int nf, int fam0, int Kpad, const int2 *__restrict__ Bs, const int2 *__restrict__ BsT,
                      const long long *__restrict__ Rs, const __nv_bfloat16 *__restrict__ Y,
                      const unsigned *count_dev, long long fixed_count, float2 *__restrict__ c0) {
@@ -139,7 +145,7 @@ static cudaError_t launch_sep_simt_t(const CorrArgs &a, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, sep_threads<B>(), smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -149,8 +155,8 @@ static cudaError_t launch_sep_simt_t(const CorrArgs &a, cudaStream_t st) {
     if (need < grid) grid = need;
     if (grid < 1) grid = 1;
     const DictDev &d = *a.d;
-    kern<<<(unsigned)grid, 256, smem, st>>>(d.nf, d.fam0, d.Kpad, d.Bs, d.BsT, d.Rs, a.Y, a.count, a.fixed_count,
-                                             a.c0);
+    kern<<<(unsigned)grid, sep_threads<B>(), smem, st>>>(d.nf, d.fam0, d.Kpad, d.Bs, d.BsT, d.Rs, a.Y, a.count,
+                                                          a.fixed_count, a.c0);
     return cudaGetLastError();
 }
 
