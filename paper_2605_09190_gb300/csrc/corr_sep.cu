@@ -9,9 +9,11 @@
 // D^T y.  In integers:
 //   stage 1  Z~[p][m] = sum_i Bf[p][i] y~[i][m]   (48-bit x 8-bit -> int64)
 //   stage 2  T~[p][q] = sum_m Bf[q][m] Z~[p][m]   (48-bit x 59-bit -> int128)
-// Bf is held as 24-bit limbs (lo in [-2^23, 2^23), hi = (Bf - lo) / 2^24) and
-// Z~ as three (two balanced 24-bit limbs and the rest), so every partial
-// product fits a 32 x 32 -> 64-bit multiply-add and every limb sum an int64.
+// Bf is held as 24-bit limbs (lo in [-2^23, 2^23), hi = (Bf - lo) / 2^24,
+// |hi| < 2^23.5) and Z~ as two 32-bit ones (zl in [-2^31, 2^31), zh =
+// (Z~ - zl) / 2^32, |zh| < 2^27), so every partial product is one 32 x 32 ->
+// 64-bit multiply-add, at most 2^54.5 in magnitude, and each of the four
+// limb sums over b <= 128 terms stays below 2^62.
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
@@ -27,23 +29,21 @@ namespace {
 template <int B>
 constexpr int sep_group() { return B >= 64 ? 1 : 4096 / (B * B); }
 
-// Z~ split into balanced limbs: z = z0 + z1 2^24 + z2 2^48.
-struct Limbs3 {
-    int32_t z0, z1, z2;
+// Z~ split into balanced limbs: z = zl + zh 2^32.
+struct Limbs2 {
+    int32_t zl, zh;
 };
 
-__device__ __forceinline__ Limbs3 split3(long long z) {
-    const long long z0 = ((z + (1ll << 23)) & ((1ll << 24) - 1)) - (1ll << 23);
-    const long long r = (z - z0) >> 24;
-    const long long z1 = ((r + (1ll << 23)) & ((1ll << 24) - 1)) - (1ll << 23);
-    return Limbs3{(int32_t)z0, (int32_t)z1, (int32_t)((r - z1) >> 24)};
+__device__ __forceinline__ Limbs2 split2(long long z) {
+    const int32_t zl = (int32_t)(uint32_t)(unsigned long long)z;    // z mod 2^32, in [-2^31, 2^31)
+    return Limbs2{zl, (int32_t)((z - (long long)zl) >> 32)};
 }
 
 __device__ __forceinline__ long long mul_wide(int32_t a, int32_t b) { return (long long)a * (long long)b; }
 
 }  // namespace
 
-// Threads per CTA: at side 128 the leaf's Z~ (192 KB of limbs) leaves room
+// Threads per CTA: at side 128 the leaf's Z~ (128 KB of limbs) leaves room
 // for one CTA per SM, so that CTA takes 768 threads to hide the latency of
 // its loads; 256 elsewhere.
 template <int B>
@@ -62,7 +62,7 @@ corr_sep_simt_kernel(int nf, int fam0, int Kpad, const int2 *__restrict__ Bs, co
     constexpr int PT = B >= 4 ? 4 : B;                   // p values per thread in stage 2
     extern __shared__ __align__(16) unsigned char smem[];
     int8_t *yt = reinterpret_cast<int8_t *>(smem);                        // [G][i][m]
-    Limbs3 *Z = reinterpret_cast<Limbs3 *>(smem + ((G * n + 15) & ~15)); // [G][p][m]
+    Limbs2 *Z = reinterpret_cast<Limbs2 *>(smem + ((G * n + 15) & ~15)); // [G][p][m]
 
     const long long count = count_dev ? (long long)*count_dev : fixed_count;
     const int M = nf * n;
@@ -95,7 +95,7 @@ corr_sep_simt_kernel(int nf, int fam0, int Kpad, const int2 *__restrict__ Bs, co
                     lo += mul_wide(w.x, y);
                     hi += mul_wide(w.y, y);
                 }
-                Z[g * n + p * B + m] = split3(hi * (1ll << 24) + lo);   // |hi 2^24| < 2^63
+                Z[g * n + p * B + m] = split2(hi * (1ll << 24) + lo);   // |hi 2^24| < 2^63
             }
             __syncthreads();
             // stage 2: T~[g][p][q] for q = lane-fastest, PT values of p per thread
@@ -110,22 +110,19 @@ corr_sep_simt_kernel(int nf, int fam0, int Kpad, const int2 *__restrict__ Bs, co
                     const int2 w = BfT[m * B + q];                 // Bf[q][m]: (lo, hi)
 #pragma unroll
                     for (int k = 0; k < PT; ++k) {
-                        const Limbs3 z = Z[g * n + (p0 + k) * B + m];
-                        a0[k] += mul_wide(w.x, z.z0);
-                        a1[k] += mul_wide(w.x, z.z1) + mul_wide(w.y, z.z0);
-                        a2[k] += mul_wide(w.x, z.z2) + mul_wide(w.y, z.z1);
-                        a3[k] += mul_wide(w.y, z.z2);
+                        const Limbs2 z = Z[g * n + (p0 + k) * B + m];
+                        a0[k] += mul_wide(w.x, z.zl);              // weight 1
+                        a1[k] += mul_wide(w.y, z.zl);              // 2^24
+                        a2[k] += mul_wide(w.x, z.zh);              // 2^32
+                        a3[k] += mul_wide(w.y, z.zh);              // 2^56
                     }
                 }
                 if (g < live) {
 #pragma unroll
                     for (int k = 0; k < PT; ++k) {
                         const int p = p0 + k;
-                        const __int128 s24 = (__int128)1 << 24;
-                        __int128 T = (__int128)a3[k];
-                        T = T * s24 + a2[k];
-                        T = T * s24 + a1[k];
-                        T = T * s24 + a0[k];
+                        __int128 T = (__int128)a3[k] * ((__int128)1 << 56) + (__int128)a2[k] * ((__int128)1 << 32) +
+                                     (__int128)a1[k] * ((__int128)1 << 24) + (__int128)a0[k];
                         T += (__int128)(128ll * R[p]) * R[q];
                         const df c = int128_to_df(T);
                         c0[(base + g) * M + (nf == 2 ? f * n : 0) + q * B + p] = make_float2(c.hi, c.lo);
@@ -140,7 +137,7 @@ corr_sep_simt_kernel(int nf, int fam0, int Kpad, const int2 *__restrict__ Bs, co
 template <int B>
 static cudaError_t launch_sep_simt_t(const CorrArgs &a, cudaStream_t st) {
     constexpr int G = sep_group<B>();
-    const size_t smem = (size_t)((G * B * B + 15) & ~15) + sizeof(Limbs3) * G * B * B;
+    const size_t smem = (size_t)((G * B * B + 15) & ~15) + sizeof(Limbs2) * G * B * B;
     auto kern = corr_sep_simt_kernel<B>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
