@@ -212,22 +212,28 @@ def load_peaks():
             "sm_max_mhz": 2070.0}, "fallback"
 
 
-def profiled_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
-    None when the kernel's sources changed since that capture."""
+def profiled_traffic(kernel: str, workload=None, leaves=None):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary,
+    scaled to a launch of `leaves` leaves; None when the entry is for another
+    workload or the kernel's sources changed since that capture."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         entry = json.load(f).get(kernel)
-    if not entry:
+    if not entry or (workload and entry.get("workload") not in (None, workload)):
         return None
     h = hashlib.sha256()
     for src in entry["sources"]:
         with open(os.path.join(ROOT, "paper_2605_09190_gb300", "csrc", src), "rb") as f:
             h.update(f.read())
-    return entry["dram_bytes_per_launch"] if h.hexdigest() == entry["sources_sha256"] else None
+    if h.hexdigest() != entry["sources_sha256"]:
+        return None
+    byts = entry["dram_bytes_per_launch"]
+    if leaves and entry.get("leaves_per_launch"):
+        byts = byts * leaves / entry["leaves_per_launch"]
+    return byts
 
 
 def fp32_peak_tflops(mhz: float = MAX_SM_MHZ) -> float:
@@ -239,7 +245,8 @@ def level_of(b: int, max_block: int) -> int:
     return int(np.log2(max_block // b))
 
 
-def roofline(name, launches, total_ms, stats_sum, peaks, peak_kind, sm_mhz, max_block, step_floor_ns=None):
+def roofline(name, launches, total_ms, stats_sum, peaks, peak_kind, sm_mhz, max_block, step_floor_ns=None,
+             workload=None):
     """Roofline entry of one kernel, from its live event-timed launches and
     the algorithmic work of the method in its dense generic-dictionary form:
 
@@ -247,9 +254,10 @@ def roofline(name, launches, total_ms, stats_sum, peaks, peak_kind, sm_mhz, max_
       column, 2n for the residual) against the FP32 FMA peak in flops; the
       latency view adds the level's longest pursuit (its serial chain of
       steps) against the launch time;
-    * correlation (``corr*``): the GEMM's 4 n^2 flops per leaf for the dense
-      kernels and 8 b^3 (two b x b x b products per family, both families)
-      for the separable ones, against the BF16 dense tensor peak;
+    * correlation (``corr*``): the GEMM's 2 n^2 flops per leaf and family
+      (4 n^2 for both; a launch named ``*_dct`` or ``*_haar`` computes one
+      family) for the dense kernels and 4 b^3 per family (two b x b x b
+      products) for the separable ones, against the BF16 dense tensor peak;
     * gather: n bytes in, 2 Kpad + 4 bytes out per leaf, against HBM."""
     kind, b = name.rsplit("_b", 1)
     b = int(b)
@@ -284,22 +292,25 @@ def roofline(name, launches, total_ms, stats_sum, peaks, peak_kind, sm_mhz, max_
             r["latency"] = lat
     elif kind.startswith("corr"):
         sep = kind.startswith("corr_sep")
-        flops = 4.0 * n * n * attempts                       # the dense GEMM's 2 M n = 4 n^2 per leaf
+        fam = 1 if kind.endswith(("_dct", "_haar")) else 2
+        Mf = fam * n                                         # atoms this launch correlates per leaf
+        flops = 2.0 * Mf * n * attempts                      # the dense GEMM's 2 M n (4 n^2 for both families)
         peak = peaks.get("bf16_tflops", 1900.0)
         ach = flops / per_launch_s / 1e12
         kpad = max(64, (n + 63) // 64 * 64)
-        alg_bytes = 2.0 * M * n + attempts * (2.0 * kpad + 8.0 * M)
+        alg_bytes = 2.0 * Mf * n + attempts * (2.0 * kpad + 8.0 * Mf)
         r.update({"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                   "peak_source": f"bf16_tflops ({peak_kind})",
-                  "work": "4 n^2 flops per leaf (dense D^T y for M = 2n atoms)",
+                  "work": (f"{2 * fam} n^2 flops per leaf (dense D^T y for M = {fam}n atoms"
+                           + (", one family)" if fam == 1 else ")")),
                   "leaves_per_launch": attempts, "algorithmic_bytes": alg_bytes})
         if sep:
-            # the separable kernels' own algorithmic work (B Y B^T, both
-            # families) and, on the tensor cores, the digit products issued
-            r["separable_flops_per_leaf"] = 8.0 * b ** 3
-            r["frac_separable_count"] = 8.0 * b ** 3 * attempts / per_launch_s / 1e12 / peak
+            # the separable kernels' own algorithmic work (B Y B^T per
+            # family) and, on the tensor cores, the digit products issued
+            r["separable_flops_per_leaf"] = 4.0 * fam * b ** 3
+            r["frac_separable_count"] = 4.0 * fam * b ** 3 * attempts / per_launch_s / 1e12 / peak
             if kind.startswith("corr_septc"):
-                issued = 2 * (3 * 4 * 2 * 128 * 64 * 16 + 2 * 96 * 2 * 128 * 32 * 16)
+                issued = fam * (3 * 4 * 2 * 128 * 64 * 16 + 2 * 96 * 2 * 128 * 32 * 16)
                 r["tensor_flops_issued_per_leaf"] = issued
                 r["tensor_pipe_frac"] = issued * attempts / per_launch_s / 1e12 / peak
     else:
@@ -309,7 +320,7 @@ def roofline(name, launches, total_ms, stats_sum, peaks, peak_kind, sm_mhz, max_
         ach = byts / per_launch_s / 1e9
         r.update({"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                   "peak_source": f"hbm_gbs ({peak_kind})", "algorithmic_bytes": byts})
-    r["traffic"] = profiled_traffic(name)
+    r["traffic"] = profiled_traffic(name, workload, attempts)
     if r["traffic"] and r.get("algorithmic_bytes"):
         r["traffic_ratio"] = r["traffic"] / r["algorithmic_bytes"]
     return r
@@ -665,7 +676,7 @@ def run_ours(args):
     roof = None
     if top in profile:
         roof = roofline(top, profile[top][0], profile[top][1], stats_sum, peaks, peak_kind, clk.get("sm_mhz"),
-                        MAX_BLOCK, step_floor)
+                        MAX_BLOCK, step_floor, workload=name)
     tot = max(1e-12, sum(x[1] for x in breakdown.values()))
     kernels = {k: {"launches": v[0], "ms": round(v[1], 4), "share": round(v[1] / tot, 4)}
                for k, v in sorted(breakdown.items(), key=lambda kv: -kv[1][1])}
@@ -675,8 +686,9 @@ def run_ours(args):
         if v[1] / tot > 0.05 and k != top:
             st1 = {kk: ([x / args.steps for x in vv] if isinstance(vv, list) and not kk.startswith("max_")
                         else vv) for kk, vv in stats_sum.items()}
-            rr = roofline(k, v[0], v[1], st1, peaks, peak_kind, clk.get("sm_mhz"), MAX_BLOCK)
-            others[k] = {kk: rr[kk] for kk in ("bound", "achieved", "peak", "unit", "frac", "launch_ms")}
+            rr = roofline(k, v[0], v[1], st1, peaks, peak_kind, clk.get("sm_mhz"), MAX_BLOCK, workload=name)
+            others[k] = {kk: rr.get(kk) for kk in ("bound", "achieved", "peak", "unit", "frac", "launch_ms", "traffic",
+                                                   "traffic_ratio") if rr.get(kk) is not None}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -274,13 +274,17 @@ int aqmp_ssim(const float *x, const float *y, int h, int w, int64_t pitch, doubl
  * of side b: c[l][j] = <y_l, phi_j> for every atom j, with y_l the
  * column-major unravel of block l (Appendix A).  `blocks` is device memory
  * holding L blocks of b x b bytes, each row-major and contiguous; `corr` is
- * device memory for L x M float pairs (hi, lo) whose sum is the correlation
- * of the 2^-48 fixed-point dictionary with the block, rounded once.
+ * device memory, 16-byte aligned (else AQMP_E_ARG), for L x M float pairs
+ * (hi, lo) whose sum is the correlation of the 2^-48 fixed-point dictionary
+ * with the block, rounded once.
  * gemm selects the kernel:
- *   0 = the separable exact correlation B Y B^T: tcgen05 at side 64, the
- *       integer SIMT kernel at the other sides;
- *   1 = the separable SIMT kernel at every side
- *       (0 and 1 round the same exact integer once: identical bits);
+ *   0 = the separable exact correlation B Y B^T: at side 64 the DCT-II
+ *       family on tcgen05 and the Haar family on the integer SIMT pipes,
+ *       the integer SIMT kernel at the other sides;
+ *   1 = the separable SIMT kernel at every side;
+ *   6 = the separable tcgen05 kernel for every family, side 64 only (else
+ *       AQMP_E_UNSUPPORTED)
+ *       (0, 1 and 6 round the same exact integer once: identical bits);
  *   3, 4 = the dense exact kernels (round(D 2^48), tcgen05 and SIMT);
  *   2 = the reduced-precision BF16 form (one tcgen05 pass of bf16(D), FP32
  *       accumulation; low words 0);

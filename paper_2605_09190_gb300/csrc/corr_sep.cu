@@ -5,8 +5,9 @@
 // Section 2.2 step (b) needs <r0, phi_j> for every atom j.  The DCT-II and
 // Haar atoms are outer products of 1-D rows (Section 2.1), so the M = 2 b^2
 // correlations of a block are B Y B^T for each family: two b x b x b products
-// (8 b^3 multiply-adds for both families) instead of the 4 b^4 of a dense
-// D^T y.  In integers:
+// instead of the b^4 per family of a dense D^T y, and the rows' structure
+// (the DCT-II rows' mirror symmetry, the Haar rows' two constant halves)
+// cuts that further, as the kernel below describes.  In integers:
 //   stage 1  Z~[p][m] = sum_i Bf[p][i] y~[i][m]   (48-bit x 8-bit -> int64)
 //   stage 2  T~[p][q] = sum_m Bf[q][m] Z~[p][m]   (48-bit x 59-bit -> int128)
 // Bf is held as 24-bit limbs (lo in [-2^23, 2^23), hi = (Bf - lo) / 2^24,
@@ -19,11 +20,14 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "haar_rows.cuh"
 #include "sep.cuh"
 
 namespace aqmp {
 
 namespace {
+
+constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x / 2); }
 
 // Leaves per CTA: enough for 4096 outputs per family and stage.
 template <int B>
@@ -43,89 +47,239 @@ __device__ __forceinline__ long long mul_wide(int32_t a, int32_t b) { return (lo
 
 }  // namespace
 
-// Threads per CTA: at side 128 the leaf's Z~ (128 KB of limbs) leaves room
-// for one CTA per SM, so that CTA takes 768 threads to hide the latency of
-// its loads; 256 elsewhere.
+// Threads per CTA: at side 128 the leaf's shared memory (177 KB, most of it
+// Z~+-) leaves room for one CTA per SM, so that CTA takes 768 threads to hide
+// the latency of its loads; 256 elsewhere.
 template <int B>
 constexpr int sep_threads() { return B >= 128 ? 768 : 256; }
 
-// One CTA handles G leaves at a time (grid-stride over the leaves); for each
-// family it runs stage 1 into shared memory (Z~ as limbs, row p, column m),
-// then stage 2 with each thread owning one q and PT values of p.
+// Shared-memory layout of one CTA (G leaves): the centred pixels, their
+// even and odd column halves, and the Z~ region, which the Haar pass reuses
+// for its summed-area table.
+template <int B>
+struct SepSmem {
+    static constexpr int n = B * B, H = B / 2, G = sep_group<B>();
+    static constexpr int RS = B + 1;                           // row stride of Z~+- and of the table
+    static constexpr int YS = B + 4;                           // row stride of the pixels (bytes): the
+                                                               // transposing stores hit distinct banks
+    static constexpr size_t yt = 0;                            // int8  [G][i][YS]
+    static constexpr size_t ys = (G * B * YS + 15) & ~15;      // int16 [G][parity][i < H][m]
+    static constexpr size_t z = ys + ((2 * G * n + 15) & ~15); // Limbs2 [G][p][RS]  /  int [G][RS][RS]
+    static constexpr int E = 1 + ilog2(B);                     // Haar scale classes: row 0, scales 1 .. b/2
+    static constexpr size_t hrow = z + sizeof(Limbs2) * G * B * RS;   // int4 [B]: s, h, class, sign
+    static constexpr size_t ptab = hrow + sizeof(int4) * B;    // ulonglong2 [E][E]: fL(c1) fL(c2), int128
+    static constexpr size_t bytes = ptab + sizeof(ulonglong2) * E * E;
+    static_assert(sizeof(int) * RS * RS <= sizeof(Limbs2) * B * RS, "table fits the Z~ region");
+};
+
+__device__ __forceinline__ long long bf_value(int2 w) { return (long long)w.y * (1ll << 24) + w.x; }
+
+__device__ __forceinline__ __int128 load_i128(const ulonglong2 &v) {
+    return (__int128)(((unsigned __int128)v.y << 64) | v.x);
+}
+
+// One CTA handles G leaves at a time (grid-stride over the leaves).
+//
+// DCT-II family: row p of Bf equals (-1)^p times its mirror image, so with
+// the column halves y+-[i][m] = y~[i][m] +- y~[b-1-i][m] (i < b/2) stage 1
+// needs b/2 terms, and stage 1 stores Z~+-[p][m] = Z~[p][m] +- Z~[p][b-1-m]
+// (m < b/2), of which stage 2 takes Z~+ for even q and Z~- for odd q, again
+// over b/2 terms: half the multiply-adds of the plain products, the same
+// exact integers.  |Z~+-| < 2^60, so zh < 2^28 and every limb sum over
+// b/2 <= 64 terms stays below 2^61.
+//
+// Haar family: row p of Bf is constant on each of two dyadic halves
+// (haar_halves), fL on the first and s_p fL on the second (s_p = +1 for row
+// 0, -1 otherwise), and fL depends only on the row's scale.  So T~[p][q] =
+// fL(p) fL(q) K with K = LL + s_q LR + s_p RL + s_p s_q RR, the sums of y~
+// over the four half-by-half rectangles, read from the summed-area table of
+// y~ (|entries| <= 2^21, |K| <= 2^21); the products fL(c1) fL(c2) of the
+// 1 + log2 b scale classes are formed once per CTA in int128.
 template <int B>
 __global__ void __launch_bounds__(sep_threads<B>())
-corr_sep_simt_kernel(int nf, int fam0, int Kpad, const int2 *__restrict__ Bs, const int2 *__restrict__ BsT,
+corr_sep_simt_kernel(int nf, int fam0, int fmask, int Kpad, const int2 *__restrict__ Bs, const int2 *__restrict__ BsT,
                      const long long *__restrict__ Rs, const __nv_bfloat16 *__restrict__ Y,
                      const unsigned *count_dev, long long fixed_count, float2 *__restrict__ c0) {
-    constexpr int n = B * B;
-    constexpr int G = sep_group<B>();
-    constexpr int PT = B >= 4 ? 4 : B;                   // p values per thread in stage 2
+    using L = SepSmem<B>;
+    constexpr int n = L::n, H = L::H, G = L::G, RS = L::RS, YS = L::YS;
+    constexpr int PT = 4;                                     // p values per thread in DCT stage 2
+    static_assert(B >= PT && B % PT == 0, "side");
     extern __shared__ __align__(16) unsigned char smem[];
-    int8_t *yt = reinterpret_cast<int8_t *>(smem);                        // [G][i][m]
-    Limbs2 *Z = reinterpret_cast<Limbs2 *>(smem + ((G * n + 15) & ~15)); // [G][p][m]
+    int8_t *yt = reinterpret_cast<int8_t *>(smem + L::yt);
+    int16_t *ys = reinterpret_cast<int16_t *>(smem + L::ys);
+    Limbs2 *Z = reinterpret_cast<Limbs2 *>(smem + L::z);
+    int *S = reinterpret_cast<int *>(smem + L::z);
+
+    constexpr int nt = sep_threads<B>(), nw = nt / 32, E = L::E;
+    int4 *hrow = reinterpret_cast<int4 *>(smem + L::hrow);
+    ulonglong2 *ptab = reinterpret_cast<ulonglong2 *>(smem + L::ptab);
 
     const long long count = count_dev ? (long long)*count_dev : fixed_count;
     const int M = nf * n;
     const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    if ((nf == 2 || fam0 == 1) && ((fmask >> 1) & 1)) {
+        // the Haar rows' supports and classes, and the class products
+        const int2 *Bh = Bs + (size_t)n;
+        for (int r = tid; r < B; r += nt) {
+            int sr, hr;
+            haar_halves(r, B, sr, hr);
+            const int cls = r == 0 ? 0 : 1 + (31 - __clz(B / (2 * hr)));
+            hrow[r] = make_int4(sr, hr, cls, r == 0 ? 1 : -1);
+        }
+        for (int e = tid; e < E * E; e += nt) {
+            const int c1 = e / E, c2 = e - c1 * E;
+            const int r1 = c1 == 0 ? 0 : 1 << (c1 - 1), r2 = c2 == 0 ? 0 : 1 << (c2 - 1);   // first row of the class
+            const unsigned __int128 P = (unsigned __int128)((__int128)bf_value(Bh[r1 * B]) * bf_value(Bh[r2 * B]));
+            ptab[e] = make_ulonglong2((unsigned long long)P, (unsigned long long)(P >> 64));
+        }
+        __syncthreads();
+    }
     for (long long base = (long long)blockIdx.x * G; base < count; base += (long long)gridDim.x * G) {
         const int live = (int)min((long long)G, count - base);
-        // centred pixels, transposed so that stage 1 reads consecutive m
-        for (int o = tid; o < G * n; o += blockDim.x) {
+        // centred pixels, transposed so that the contractions read consecutive m
+        for (int o = tid; o < G * n; o += nt) {
             const int g = o / n, v = o - g * n;
             const int m = v / B, i = v - m * B;
             int8_t y = 0;
             if (g < live) y = (int8_t)__bfloat162float(Y[(base + g) * Kpad + v]);
-            yt[g * n + i * B + m] = y;
+            yt[(g * B + i) * YS + m] = y;
         }
         __syncthreads();
         for (int f = 0; f < nf; ++f) {
             const int F = nf == 2 ? f : fam0;
+            if (!((fmask >> F) & 1)) continue;                   // uniform
             const int2 *Bf = Bs + (size_t)F * n;
-            const int2 *BfT = BsT + (size_t)F * n;
             const long long *R = Rs + F * B;
-            // stage 1: Z~[g][p][m], m fastest across threads
-            for (int o = tid; o < G * n; o += blockDim.x) {
-                const int g = o / n, r = o - g * n;
-                const int p = r / B, m = r - p * B;
-                long long lo = 0, hi = 0;
-#pragma unroll 8
-                for (int i = 0; i < B; ++i) {
-                    const int2 w = Bf[p * B + i];
-                    const int32_t y = yt[g * n + i * B + m];
-                    lo += mul_wide(w.x, y);
-                    hi += mul_wide(w.y, y);
+            float2 *out = c0 + (nf == 2 ? f * n : 0);
+            if (F == 0) {
+                const int2 *BfT = BsT + (size_t)F * n;
+                for (int o = tid; o < G * H * B; o += nt) {
+                    const int g = o / (H * B), r = o - g * (H * B);
+                    const int i = r / B, m = r - i * B;
+                    const int a = yt[(g * B + i) * YS + m], c = yt[(g * B + B - 1 - i) * YS + m];
+                    ys[(2 * g) * H * B + r] = (int16_t)(a + c);
+                    ys[(2 * g + 1) * H * B + r] = (int16_t)(a - c);
                 }
-                Z[g * n + p * B + m] = split2(hi * (1ll << 24) + lo);   // |hi 2^24| < 2^63
-            }
-            __syncthreads();
-            // stage 2: T~[g][p][q] for q = lane-fastest, PT values of p per thread
-            for (int o = tid; o < G * n / PT; o += blockDim.x) {
-                const int g = o / (n / PT), r = o - g * (n / PT);
-                const int q = r % B, p0 = (r / B) * PT;
-                long long a0[PT], a1[PT], a2[PT], a3[PT];
+                __syncthreads();
+                // stage 1: Z~[p][m] and Z~[p][b-1-m] together, m < b/2 across threads
+                for (int o = tid; o < G * B * H; o += nt) {
+                    const int g = o / (B * H), r = o - g * (B * H);
+                    const int p = r / H, m = r - p * H;
+                    const int16_t *yp = ys + (2 * g + (p & 1)) * H * B;
+                    long long lo1 = 0, hi1 = 0, lo2 = 0, hi2 = 0;
+#pragma unroll 8
+                    for (int i = 0; i < H; ++i) {
+                        const int2 w = Bf[p * B + i];
+                        const int32_t a = yp[i * B + m], c = yp[i * B + B - 1 - m];
+                        lo1 += mul_wide(w.x, a);
+                        hi1 += mul_wide(w.y, a);
+                        lo2 += mul_wide(w.x, c);
+                        hi2 += mul_wide(w.y, c);
+                    }
+                    const long long z1 = hi1 * (1ll << 24) + lo1, z2 = hi2 * (1ll << 24) + lo2;
+                    Limbs2 *zr = Z + (g * B + p) * RS;
+                    zr[m] = split2(z1 + z2);
+                    zr[H + 1 + m] = split2(z1 - z2);
+                }
+                __syncthreads();
+                // stage 2: T~[g][p][q], q lane-fastest, PT consecutive p per thread
+                for (int o = tid; o < G * n / PT; o += nt) {
+                    const int g = o / (n / PT), r = o - g * (n / PT);
+                    const int q = r % B, p0 = (r / B) * PT;
+                    const Limbs2 *zr = Z + (g * B + p0) * RS + ((q & 1) ? H + 1 : 0);
+                    long long a0[PT], a1[PT], a2[PT], a3[PT];
 #pragma unroll
-                for (int k = 0; k < PT; ++k) a0[k] = a1[k] = a2[k] = a3[k] = 0;
+                    for (int k = 0; k < PT; ++k) a0[k] = a1[k] = a2[k] = a3[k] = 0;
 #pragma unroll 4
-                for (int m = 0; m < B; ++m) {
-                    const int2 w = BfT[m * B + q];                 // Bf[q][m]: (lo, hi)
+                    for (int m = 0; m < H; ++m) {
+                        const int2 w = BfT[m * B + q];                 // Bf[q][m]: (lo, hi)
 #pragma unroll
-                    for (int k = 0; k < PT; ++k) {
-                        const Limbs2 z = Z[g * n + (p0 + k) * B + m];
-                        a0[k] += mul_wide(w.x, z.zl);              // weight 1
-                        a1[k] += mul_wide(w.y, z.zl);              // 2^24
-                        a2[k] += mul_wide(w.x, z.zh);              // 2^32
-                        a3[k] += mul_wide(w.y, z.zh);              // 2^56
+                        for (int k = 0; k < PT; ++k) {
+                            const Limbs2 z = zr[k * RS + m];
+                            a0[k] += mul_wide(w.x, z.zl);              // weight 1
+                            a1[k] += mul_wide(w.y, z.zl);              // 2^24
+                            a2[k] += mul_wide(w.x, z.zh);              // 2^32
+                            a3[k] += mul_wide(w.y, z.zh);              // 2^56
+                        }
+                    }
+                    if (g < live) {
+                        float v[2 * PT];
+#pragma unroll
+                        for (int k = 0; k < PT; ++k) {
+                            __int128 T = (__int128)a3[k] * ((__int128)1 << 56) + (__int128)a2[k] * ((__int128)1 << 32) +
+                                         (__int128)a1[k] * ((__int128)1 << 24) + (__int128)a0[k];
+                            T += (__int128)(128ll * R[p0 + k]) * R[q];
+                            const df c = int128_to_df(T);
+                            v[2 * k] = c.hi;
+                            v[2 * k + 1] = c.lo;
+                        }
+                        float4 *dst = reinterpret_cast<float4 *>(out + (base + g) * M + q * B + p0);
+#pragma unroll
+                        for (int k = 0; k < PT / 2; ++k)
+                            dst[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
                     }
                 }
-                if (g < live) {
+            } else {
+                // summed-area table S[i][m] = sum of y~ over [0, i) x [0, m):
+                // prefix sums along m (one warp per row), then along i (one
+                // warp per column; stride RS = 1 mod 32 keeps it conflict-free)
+                for (int o = tid; o < G * RS; o += nt) {
+                    const int g = o / RS, e = o - g * RS;
+                    S[g * RS * RS + e] = 0;                            // row 0
+                    S[g * RS * RS + e * RS] = 0;                       // column 0
+                }
+                for (int row = warp; row < G * B; row += nw) {
+                    const int g = row / B, i = row - g * B;
+                    int carry = 0;
+                    for (int c = 0; c < B; c += 32) {
+                        int v = c + lane < B ? (int)yt[(g * B + i) * YS + c + lane] : 0;
 #pragma unroll
-                    for (int k = 0; k < PT; ++k) {
-                        const int p = p0 + k;
-                        __int128 T = (__int128)a3[k] * ((__int128)1 << 56) + (__int128)a2[k] * ((__int128)1 << 32) +
-                                     (__int128)a1[k] * ((__int128)1 << 24) + (__int128)a0[k];
-                        T += (__int128)(128ll * R[p]) * R[q];
+                        for (int d = 1; d < 32; d <<= 1) {
+                            const int u = __shfl_up_sync(0xffffffffu, v, d);
+                            if (lane >= d) v += u;
+                        }
+                        if (c + lane < B) S[g * RS * RS + (i + 1) * RS + c + lane + 1] = carry + v;
+                        carry += __shfl_sync(0xffffffffu, v, 31);
+                    }
+                }
+                __syncthreads();
+                for (int col = warp; col < G * B; col += nw) {
+                    const int g = col / B, m = col - g * B + 1;
+                    int carry = 0;
+                    for (int c = 0; c < B; c += 32) {
+                        int *at = S + g * RS * RS + (c + lane + 1) * RS + m;
+                        int v = c + lane < B ? *at : 0;
+#pragma unroll
+                        for (int d = 1; d < 32; d <<= 1) {
+                            const int u = __shfl_up_sync(0xffffffffu, v, d);
+                            if (lane >= d) v += u;
+                        }
+                        if (c + lane < B) *at = carry + v;
+                        carry += __shfl_sync(0xffffffffu, v, 31);
+                    }
+                }
+                __syncthreads();
+                // T~[g][p][q], p lane-fastest
+                for (int o = tid; o < G * n; o += nt) {
+                    const int g = o / n, r = o - g * n;
+                    const int q = r / B, p = r - q * B;
+                    const int4 hp = hrow[p], hq = hrow[q];
+                    const int *Sg = S + g * RS * RS;
+                    const int *r0 = Sg + hp.x * RS, *r1 = r0 + hp.y * RS, *r2 = r1 + hp.y * RS;
+                    const int m0 = hq.x, m1 = hq.x + hq.y, m2 = hq.x + 2 * hq.y;
+                    const int s00 = r0[m0], s01 = r0[m1], s02 = r0[m2];
+                    const int s10 = r1[m0], s11 = r1[m1], s12 = r1[m2];
+                    const int s20 = r2[m0], s21 = r2[m1], s22 = r2[m2];
+                    const int LL = s11 - s01 - s10 + s00, LR = s12 - s02 - s11 + s01;
+                    const int RL = s21 - s11 - s20 + s10, RR = s22 - s12 - s21 + s11;
+                    const int K = (LL + hq.w * LR) + hp.w * (RL + hq.w * RR);
+                    __int128 T = load_i128(ptab[hp.z * E + hq.z]) * (__int128)K;
+                    const long long Rp = R[p], Rq = R[q];
+                    if (Rp != 0 && Rq != 0) T += (__int128)(128ll * Rp) * Rq;
+                    if (g < live) {
                         const df c = int128_to_df(T);
-                        c0[(base + g) * M + (nf == 2 ? f * n : 0) + q * B + p] = make_float2(c.hi, c.lo);
+                        out[(base + g) * M + q * B + p] = make_float2(c.hi, c.lo);
                     }
                 }
             }
@@ -137,7 +291,7 @@ corr_sep_simt_kernel(int nf, int fam0, int Kpad, const int2 *__restrict__ Bs, co
 template <int B>
 static cudaError_t launch_sep_simt_t(const CorrArgs &a, cudaStream_t st) {
     constexpr int G = sep_group<B>();
-    const size_t smem = (size_t)((G * B * B + 15) & ~15) + sizeof(Limbs2) * G * B * B;
+    const size_t smem = SepSmem<B>::bytes;
     auto kern = corr_sep_simt_kernel<B>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -152,7 +306,8 @@ static cudaError_t launch_sep_simt_t(const CorrArgs &a, cudaStream_t st) {
     if (need < grid) grid = need;
     if (grid < 1) grid = 1;
     const DictDev &d = *a.d;
-    kern<<<(unsigned)grid, sep_threads<B>(), smem, st>>>(d.nf, d.fam0, d.Kpad, d.Bs, d.BsT, d.Rs, a.Y, a.count,
+    kern<<<(unsigned)grid, sep_threads<B>(), smem, st>>>(d.nf, d.fam0, a.fmask ? a.fmask : 3, d.Kpad, d.Bs, d.BsT,
+                                                          d.Rs, a.Y, a.count,
                                                           a.fixed_count, a.c0);
     return cudaGetLastError();
 }

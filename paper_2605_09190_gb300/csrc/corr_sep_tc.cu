@@ -72,8 +72,8 @@ constexpr uint32_t kIdesc2 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(32
 // at row 128 (3 F + u).
 __global__ void __launch_bounds__(septc::kThreads, 1)
 corr_sep_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ CUtensorMap tmBd, int nf,
-                   int fam0, const long long *__restrict__ Rs, const unsigned *count_dev, long long fixed_count,
-                   float2 *__restrict__ c0, Counters *ctr) {
+                   int fam0, int fmask, const long long *__restrict__ Rs, const unsigned *count_dev,
+                   long long fixed_count, float2 *__restrict__ c0, Counters *ctr) {
     using namespace septc;
     constexpr int n = kB * kB;
     const long long count = count_dev ? (long long)*count_dev : fixed_count;
@@ -139,6 +139,7 @@ corr_sep_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constan
         const uint32_t yaddr = sY + buf * kTileY;
         for (int f = 0; f < nf && ok; ++f) {
             const int F = nf == 2 ? f : fam0;
+            if (!((fmask >> F) & 1)) continue;                   // uniform
             // ---- stage 1: Z~^T[m][p], one accumulator per digit pair u
             if (threadIdx.x == 0) {
                 fence_after();
@@ -331,7 +332,7 @@ cudaError_t launch_corr_sep_tc(const CorrArgs &a, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     corr_sep_tc_kernel<<<grid, septc::kThreads, septc::kSmemBytes, st>>>(
         *reinterpret_cast<const CUtensorMap *>(a.tmap_Ysep), *reinterpret_cast<const CUtensorMap *>(d.tmap_sepd),
-        d.nf, d.fam0, d.Rs, a.count, a.fixed_count, a.c0, a.ctr);
+        d.nf, d.fam0, a.fmask ? a.fmask : 3, d.Rs, a.count, a.fixed_count, a.c0, a.ctr);
     return cudaGetLastError();
 }
 

@@ -24,6 +24,7 @@
 #include "../../include/aqmp.h"
 #include "common.cuh"
 #include "kernels.h"
+#include "haar_rows.cuh"
 #include "code.h"
 
 using namespace aqmp;
@@ -69,11 +70,16 @@ int ilog2(int v) { int l = 0; while ((1 << l) < v) ++l; return l; }
 void make_bases(int b, std::vector<double> &basis) {
     basis.assign(2 * (size_t)b * b, 0.0);
     double *C = basis.data(), *H = basis.data() + (size_t)b * b;
+    // DCT-II row k is even (k even) or odd (k odd) about the block centre:
+    // the second half mirrors the first exactly, so that the fixed-point rows
+    // keep the symmetry the exact separable correlation relies on
     for (int k = 0; k < b; ++k) {
         const double ak = k == 0 ? std::sqrt(1.0 / b) : std::sqrt(2.0 / b);
-        for (int m = 0; m < b; ++m) {
+        for (int m = 0; m < b / 2; ++m) {
             const long long num = (long long)(2 * m + 1) * k;
-            C[k * b + m] = k == 0 ? ak : ak * std::cos(M_PI * (double)num / (2.0 * b));
+            const double v = k == 0 ? ak : ak * std::cos(M_PI * (double)num / (2.0 * b));
+            C[k * b + m] = v;
+            C[k * b + b - 1 - m] = (k & 1) ? -v : v;
         }
     }
     for (int m = 0; m < b; ++m) H[m] = std::sqrt(1.0 / b);
@@ -86,6 +92,31 @@ void make_bases(int b, std::vector<double> &basis) {
         for (int m = t * len; m < t * len + len / 2; ++m) H[r * b + m] = v;
         for (int m = t * len + len / 2; m < (t + 1) * len; ++m) H[r * b + m] = -v;
     }
+}
+
+// The exact SIMT correlation relies on these facts of the rows: DCT-II row
+// k equals (-1)^k times its mirror image; Haar row r is v_r on the first of
+// the halves haar_halves gives and -v_r on the second (row 0: v_0 on both),
+// zero elsewhere, with v_r the same for every row of one scale (the rows
+// 2^j .. 2^(j+1) - 1).  Checked once per dictionary.
+bool sep_rows_structured(int b, const std::vector<double> &basis) {
+    const double *C = basis.data(), *H = basis.data() + (size_t)b * b;
+    for (int k = 0; k < b; ++k) {
+        for (int m = 0; m < b; ++m)
+            if (C[k * b + b - 1 - m] != ((k & 1) ? -C[k * b + m] : C[k * b + m])) return false;
+        int s, h;
+        haar_halves(k, b, s, h);
+        int first = k;                                   // first row of k's scale
+        if (k > 0)
+            while (first & (first - 1)) first &= first - 1;
+        const double v = H[k * b + s];
+        if (v == 0.0 || v != H[first * b]) return false;
+        for (int m = 0; m < b; ++m) {
+            const double want = m < s || m >= s + 2 * h ? 0.0 : (m < s + h || k == 0) ? v : -v;
+            if (H[k * b + m] != want) return false;
+        }
+    }
+    return true;
 }
 
 // Compensated dot product (Ogita-Rump-Oishi Dot2): result as accurate as if
@@ -238,6 +269,26 @@ thread_local std::vector<Profiler::Pending> *Profiler::capture_to = nullptr;
 Profiler g_prof;
 
 std::string kname(const char *k, int b) { return std::string(k) + "_b" + std::to_string(b); }
+
+// The exact separable correlation on the tensor-core path: the DCT-II family
+// on the tensor cores, the Haar family on the SIMT pipes, where its rows' two
+// constant halves reduce it to a summed-area computation with no contraction
+// left to speed up.  Bit for bit the SIMT kernel's result for both families.
+cudaError_t corr_sep_hybrid(const CorrArgs &ca, int b, cudaStream_t st) {
+    const DictDev &d = *ca.d;
+    const bool dct = d.nf == 2 || d.fam0 == 0, haar = d.nf == 2 || d.fam0 == 1;
+    CorrArgs a = ca;
+    cudaError_t e = cudaSuccess;
+    if (dct) {
+        a.fmask = 1;
+        e = g_prof.run(kname("corr_septc_dct", b), st, [&] { return launch_corr_sep_tc(a, st); });
+    }
+    if (e == cudaSuccess && haar) {
+        a.fmask = 2;
+        e = g_prof.run(kname("corr_sep_haar", b), st, [&] { return launch_corr_sep_simt(a, st); });
+    }
+    return e;
+}
 
 // ------------------------------------------------------------ autotuner
 //
@@ -422,6 +473,7 @@ int get_dict(Ctx *c, int b, int dict_id, cudaStream_t st, Dict **out, bool table
 
         std::vector<double> basis;
         make_bases(b, basis);
+        if (!sep_rows_structured(b, basis)) return AQMP_E_UNSUPPORTED;
 
         // separable fixed-point dictionary: Bf = round(B 2^48) per 1-D row,
         // as 24-bit limbs (lo in [-2^23, 2^23), hi), its transpose, and the
@@ -942,13 +994,12 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
             if ((rc = encode_bf16_map(&ysmaps[l], c->Y.p, cap[l] * (unsigned long long)b, b, b))) return rc;
             ca.tmap_Ysep = &ysmaps[l];
         }
-        // exact correlation with the separable fixed-point dictionary: on the
-        // tensor cores where a kernel for the side exists, else (and with
-        // AQMP_FLAG_SIMT_GEMM) on the integer SIMT pipes; the two give the
-        // same bits, so the autotuner may time both
-        auto corr_tc = [&] {
-            return g_prof.run(kname("corr_septc", b), st, [&] { return launch_corr_sep_tc(ca, st); });
-        };
+        // exact correlation with the separable fixed-point dictionary: where
+        // a tensor-core kernel for the side exists, the DCT-II family there
+        // and the Haar family on the SIMT pipes, else (and with
+        // AQMP_FLAG_SIMT_GEMM) all on the integer SIMT pipes; the two give
+        // the same bits, so the autotuner may time both
+        auto corr_tc = [&] { return corr_sep_hybrid(ca, b, st); };
         auto corr_simt = [&] {
             return g_prof.run(kname("corr_sep", b), st, [&] { return launch_corr_sep_simt(ca, st); });
         };
@@ -1465,10 +1516,14 @@ int aqmp_correlate(int b, int dict_id, const uint8_t *blocks, int64_t L, float *
     if (!is_pow2(b) || b < 4 || b > kMaxSide) return fail(AQMP_E_ARG, "side must be a power of two in [4, %d]", kMaxSide);
     if (dict_id < 0 || dict_id > 2) return fail(AQMP_E_DICT, "unknown dictionary id %d", dict_id);
     if (L < 0 || (L > 0 && (!blocks || !corr))) return fail(AQMP_E_ARG, "bad pointers");
-    if (gemm < 0 || gemm > 5)
+    if (gemm < 0 || gemm > 6)
         return fail(AQMP_E_ARG, "gemm must be 0 (separable, best kernel), 1 (separable SIMT), 2 (BF16 form), "
-                                "3 (dense tensor cores), 4 (dense SIMT) or 5 (FP8 form)");
+                                "3 (dense tensor cores), 4 (dense SIMT), 5 (FP8 form) or 6 (separable "
+                                "tensor cores, every family)");
+    if (gemm == 6 && !corr_sep_tc_available(b, 2))
+        return fail(AQMP_E_UNSUPPORTED, "no separable tensor-core kernel for side %d", b);
     if (L == 0) return AQMP_OK;
+    if (((uintptr_t)corr & 15) != 0) return fail(AQMP_E_ARG, "corr must be 16-byte aligned");
     if (L > 0x7fffffffLL) return fail(AQMP_E_UNSUPPORTED, "too many blocks");
     Ctx *c;
     int rc;
@@ -1490,7 +1545,7 @@ int aqmp_correlate(int b, int dict_id, const uint8_t *blocks, int64_t L, float *
         if (gemm != 1 && gemm != 4) {
             if ((rc = encode_bf16_map(&ym, c->Y.p, (unsigned long long)L, d.Kpad, 64))) return rc;
         }
-        if (gemm == 0 && corr_sep_tc_available(b, d.nf)) {
+        if ((gemm == 0 || gemm == 6) && corr_sep_tc_available(b, d.nf)) {
             if ((rc = encode_bf16_map(&ysm, c->Y.p, (unsigned long long)L * b, b, b))) return rc;
         }
         CK(launch_gather_blocks(b, d.Kpad, blocks, L, (__nv_bfloat16 *)c->Y.p, nullptr, c->num_sms, st));
@@ -1508,9 +1563,10 @@ int aqmp_correlate(int b, int dict_id, const uint8_t *blocks, int64_t L, float *
     switch (gemm) {
         case 0:
             e = corr_sep_tc_available(b, d.nf)
-                    ? g_prof.run(kname("corr_septc", b), st, [&] { return launch_corr_sep_tc(ca, st); })
+                    ? corr_sep_hybrid(ca, b, st)
                     : g_prof.run(kname("corr_sep", b), st, [&] { return launch_corr_sep_simt(ca, st); });
             break;
+        case 6: e = g_prof.run(kname("corr_septc", b), st, [&] { return launch_corr_sep_tc(ca, st); }); break;
         case 1: e = g_prof.run(kname("corr_sep", b), st, [&] { return launch_corr_sep_simt(ca, st); }); break;
         case 2: e = g_prof.run(kname("corr_bf16", b), st, [&] { return launch_corr_tc_bf16(ca, st); }); break;
         case 3: e = g_prof.run(kname("corr_tc", b), st, [&] { return launch_corr_tc(ca, st); }); break;

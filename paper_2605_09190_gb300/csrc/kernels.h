@@ -140,6 +140,10 @@ struct CorrArgs {
     // BF16 form with rescore: the per-leaf centres and the per-atom bounds
     const uint8_t *mu;           // [capacity] integer mean each leaf's Y is centred on
     float *ebound;               // [capacity][M] bound on |c0 - the exact form's c0|
+    // separable exact kernels: the families (bit F: 0 DCT-II, 1 Haar) this
+    // launch computes, 0 = all of the dictionary's; the others' outputs are
+    // left as they are (the layout is always the dictionary's [capacity][M])
+    int fmask;
 };
 cudaError_t launch_corr_simt(const CorrArgs &a, cudaStream_t st);
 // Exact correlation with the separable fixed-point dictionary (corr_sep.cu):

@@ -46,6 +46,20 @@ def test_correlation_roofline_counts_4n2_flops_per_leaf_against_bf16():
     assert r["frac_separable_count"] == pytest.approx(8 * 64 ** 3 * 50910 / 10.29e-3 / 1e12 / 1917.6)
 
 
+def test_one_family_correlation_counts_half_the_work():
+    # the DCT-II family alone (the tensor-core half of the side-64 split)
+    st = _stats(0, attempts=50910)
+    r = bench.roofline("corr_septc_dct_b64", 1, 5.0, st, PEAKS, "measured", 2070.0, 64)
+    n = 64 * 64
+    assert r["achieved"] == pytest.approx(2 * n * n * 50910 / 5.0e-3 / 1e12)
+    assert r["separable_flops_per_leaf"] == 4 * 64 ** 3
+    kpad = n
+    assert r["algorithmic_bytes"] == pytest.approx(2.0 * n * n + 50910 * (2.0 * kpad + 8.0 * n))
+    both = bench.roofline("corr_septc_b64", 1, 5.0, st, PEAKS, "measured", 2070.0, 64)
+    assert both["achieved"] == pytest.approx(2 * r["achieved"])
+    assert both["tensor_flops_issued_per_leaf"] == 2 * r["tensor_flops_issued_per_leaf"]
+
+
 def test_fp32_form_issues_one_fma_per_updated_correlation():
     st = _stats(1, attempts=10, iters=1000, longest=200)
     exact = bench.roofline("mp_b32", 1, 0.1, st, PEAKS, "measured", None, 64)
@@ -65,3 +79,23 @@ def test_gather_roofline_counts_bytes_against_hbm():
 def test_critical_path_sums_the_longest_pursuits():
     st = {"max_leaf_steps_per_level": [1024, 256, 64, 16, 4, 0, 0, 0]}
     assert bench.critical_path(st) == 1364
+
+
+def test_profiled_traffic_matches_workload_and_scales_by_leaves(tmp_path, monkeypatch):
+    import hashlib
+    import json
+    src = tmp_path / "paper_2605_09190_gb300" / "csrc"
+    src.mkdir(parents=True)
+    (src / "k.cu").write_bytes(b"kernel source")
+    (tmp_path / "profiles").mkdir()
+    entry = {"dram_bytes_per_launch": 1000, "sources": ["k.cu"],
+             "sources_sha256": hashlib.sha256(b"kernel source").hexdigest(),
+             "workload": "uneven64", "leaves_per_launch": 100}
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps({"k_b64": entry}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.profiled_traffic("k_b64", "uneven64", 100) == 1000
+    assert bench.profiled_traffic("k_b64", "uneven64", 25) == 250
+    assert bench.profiled_traffic("k_b64", "sweep512", 100) is None     # captured on another workload
+    assert bench.profiled_traffic("other_b64", "uneven64", 100) is None
+    (src / "k.cu").write_bytes(b"kernel source, changed")
+    assert bench.profiled_traffic("k_b64", "uneven64", 100) is None     # sources changed since the capture

@@ -1,6 +1,7 @@
 """a2 on the GPU.  The exact correlation with the separable fixed-point
 dictionary (each 1-D basis row rounded to 2^-48, atoms their outer
-products): the tensor-core and integer SIMT kernels against each other (bit
+products): the tensor-core, integer SIMT and mixed (DCT-II family on the
+tensor cores, Haar family on the SIMT pipes) kernels against each other (bit
 for bit) and against the FP64 oracle's D^T y within the bound of that
 fixed-point dictionary.  The dense exact kernels (round(D 2^48) entries)
 likewise, and the reduced-precision BF16 form within its rounding bound."""
@@ -66,6 +67,12 @@ def test_separable_kernels_agree_and_match_fp64(lib, b, dict_id, L):
     best_h, simt_h = best.cpu().numpy(), simt.cpu().numpy()
     # both kernels round the same exact integer once: identical bits
     assert np.array_equal(best_h.view(np.uint32), simt_h.view(np.uint32))
+    if b == 64:
+        # at side 64 the default runs the DCT-II family on the tensor cores and
+        # the Haar family on the SIMT pipes; the tensor-core kernel's own Haar
+        # path (mode 6) agrees too
+        tc_h = lib.aqmp_correlate(b, dict_id, dev, gemm=6).cpu().numpy()
+        assert np.array_equal(tc_h.view(np.uint32), simt_h.view(np.uint32))
     D = oracle.dictionary(b, dict_id)
     Dabs = np.abs(D)
     for l in range(L):
