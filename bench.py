@@ -397,6 +397,20 @@ def pursuit_step_floor_ns(aqmp, torch, b: int):
     return prof[key][1] * 1e6 / steps if key in prof and steps else None
 
 
+def timed_encode(aqmp, torch, stream, encode):
+    """One encode call, timed on the device by the library's own CUDA events
+    around its kernels (on the stream that ran them) and, for reference, by
+    the caller's events around the call, which also hold the call's host
+    work: argument marshalling, the library's checks and its read-back."""
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    code = encode()
+    e1.record(stream)
+    dev_ms = aqmp.aqmp_last_device_ms()
+    e1.synchronize()
+    return code, dev_ms, e0.elapsed_time(e1)
+
+
 def add_stats(acc, st):
     if acc is None:
         return {k: (list(v) if isinstance(v, list) else v) for k, v in st.items()}
@@ -568,18 +582,16 @@ def run_ours(args):
             flush()
             encode().free()
         barrier()
-        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-        stops = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-        stats = None
+        stats, ms, caller_ms = None, [], []
         for i in range(steps):
             flush()
-            starts[i].record(stream)
-            code = encode()
-            stops[i].record(stream)
+            code, dev_ms, call_ms = timed_encode(aqmp, torch, stream, encode)
+            ms.append(dev_ms)
+            caller_ms.append(call_ms)
             stats = add_stats(stats, code.stats())
             code.free()
         barrier()
-        ms = [a.elapsed_time(b) for a, b in zip(starts, stops)]
+        stats["caller_ms"] = sum(caller_ms)
         return max_over_ranks(sum(ms) / 1e3, device="cuda"), stats
 
     encode = lambda: aqmp.aqmp_encode_planes(dev, tols, **kw)  # noqa: E731
@@ -641,13 +653,9 @@ def run_ours(args):
             ms = []
             for _ in range(args.warmup + args.steps):
                 flush()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                c = enc1()
-                e1.record(stream)
+                c, dev_ms, _ = timed_encode(aqmp, torch, stream, enc1)
                 c.free()
-                torch.cuda.synchronize()
-                ms.append(e0.elapsed_time(e1))
+                ms.append(dev_ms)
             per_tol[str(t)] = one[0].numel() * args.steps / 1e6 / (sum(ms[args.warmup:]) / 1e3)
 
     # end to end: pinned host input -> encode -> host copy of the result
@@ -708,7 +716,11 @@ def run_ours(args):
                            "parallelism": (f"sharded x{world}: contiguous (plane, root row) ranges of a "
                                            f"{args.images * world}-image batch, records gathered at the end"
                                            if pieces is not None and world > 1 else
-                                           ("single GPU" if world == 1 else f"independent replicas x{world}"))},
+                                           ("single GPU" if world == 1 else f"independent replicas x{world}")),
+                           "timing": ("device: the library's CUDA events around each encode's kernels, on the "
+                                      "stream that runs them; caller_ms_per_step: the caller's events around "
+                                      "the call, which add its host work (argument marshalling, read-back)")},
+                "caller_ms_per_step": stats_sum["caller_ms"] / args.steps,
                 "atom_iterations_per_s": iters_per_s,
                 "atom_iterations_per_step": stats_sum["atom_iterations"] / args.steps,
                 "leaves_per_step": stats_sum["n_leaves"] / args.steps,
@@ -758,14 +770,10 @@ def run_omp(args):
         ms, stats = [], None
         for _ in range(args.steps):
             flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            code = encode()
-            e1.record(stream)
+            code, dev_ms, _ = timed_encode(aqmp, torch, stream, encode)
             stats = code.stats()
             code.free()
-            torch.cuda.synchronize()
-            ms.append(e0.elapsed_time(e1))
+            ms.append(dev_ms)
         return max_over_ranks(sum(ms) / 1e3, device="cuda"), breakdown, per_call, stats
 
     with ClockSampler(local) as clocks:
@@ -824,12 +832,8 @@ def run_precision(args):
                 encode().free()
             ms = []
             for _ in range(args.steps):
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                code = encode()
-                e1.record(stream)
-                torch.cuda.synchronize()
-                ms.append(e0.elapsed_time(e1))
+                code, dev_ms, _ = timed_encode(aqmp, torch, stream, encode)
+                ms.append(dev_ms)
                 if len(ms) < args.steps:
                     code.free()
             out[name] = {"s": max_over_ranks(sum(ms) / 1e3, device="cuda"), "code": code,

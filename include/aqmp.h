@@ -444,6 +444,15 @@ int aqmp_num_atoms(int b, int dict_id);
 /* Message of the calling thread's last failed call ("" if none). */
 const char *aqmp_last_error(void);
 
+/* Device time in milliseconds of the most recent aqmp_encode_planes,
+ * aqmp_encode or aqmp_encode_batch call on the current device: CUDA events
+ * recorded on the stream that runs the call's kernels, just before the first
+ * of them (after the call's wait on the caller's stream) and just after the
+ * last; host-side work of the call (argument checks, the read-back of the
+ * counters) lies outside it.  *ms = -1 when no encode has completed on the
+ * device.  Errors: AQMP_E_ARG (ms NULL), AQMP_E_CUDA. */
+int aqmp_last_device_ms(double *ms);
+
 /* Library version string. */
 const char *aqmp_version(void);
 

@@ -76,7 +76,7 @@ EXPORTS = ["aqmp_params_default", "aqmp_encode_planes", "aqmp_encode", "aqmp_cod
            "aqmp_synth_backward", "aqmp_ssim", "aqmp_image_to_planes", "aqmp_planes_to_image",
            "aqmp_bitstream_size", "aqmp_bitstream_write", "aqmp_bitstream_parse", "aqmp_code_from_bitstream",
            "aqmp_autotune_read", "aqmp_autotune_reset", "aqmp_profile_filter", "aqmp_encode_batch",
-           "aqmp_correlate_bf16x2"]
+           "aqmp_correlate_bf16x2", "aqmp_last_device_ms"]
 
 
 class aqmp_tune_entry(ctypes.Structure):
@@ -135,6 +135,7 @@ def load_library(path: str | None = None):
         lib.aqmp_ssim.argtypes = [V, V, I, I, I64, V, V, ctypes.c_double, V]
         lib.aqmp_num_atoms.argtypes = [I, I]
         lib.aqmp_last_error.restype = ctypes.c_char_p
+        lib.aqmp_last_device_ms.argtypes = [ctypes.POINTER(ctypes.c_double)]
         lib.aqmp_version.restype = ctypes.c_char_p
         lib.aqmp_profile_enable.argtypes = [I]
         lib.aqmp_profile_reset.argtypes = []
@@ -357,6 +358,14 @@ def aqmp_correlate_bf16x2(b: int, dict_id: int, blocks, stream=None):
                                                 ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(bound.data_ptr()),
                                                 _stream_handle(stream)))
     return out, bound
+
+
+def aqmp_last_device_ms() -> float:
+    """Device time (ms) of the last encode on the current device, from CUDA
+    events around its kernels on the stream that ran them (-1: none yet)."""
+    ms = ctypes.c_double()
+    _check(load_library().aqmp_last_device_ms(ctypes.byref(ms)))
+    return ms.value
 
 
 def aqmp_num_atoms(b: int, dict_id: int) -> int:

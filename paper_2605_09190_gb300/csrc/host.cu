@@ -392,6 +392,10 @@ struct Ctx {
     std::map<std::vector<long long>, int> seen;     // direct runs per configuration (-1: capture failed)
     cudaStream_t graph_stream = nullptr;            // graphs run here (capture needs a non-legacy stream)
     cudaEvent_t graph_in = nullptr, graph_out = nullptr;
+    // device time of the last encode: events on the stream that runs its
+    // kernels, recorded just before the first and just after the last
+    cudaEvent_t dev_t0 = nullptr, dev_t1 = nullptr;
+    float last_device_ms = -1.0f;
     void drop_graphs() {
         for (auto &kv : graphs) {
             if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
@@ -680,6 +684,17 @@ int device_sm_count(int *sms) {
 extern "C" {
 
 const char *aqmp_last_error(void) { return g_last_error.c_str(); }
+
+int aqmp_last_device_ms(double *ms) {
+    g_last_error.clear();
+    if (!ms) return fail(AQMP_E_ARG, "ms is NULL");
+    Ctx *c;
+    int rc;
+    if ((rc = get_ctx(&c))) return rc;
+    std::lock_guard<std::mutex> lock(c->mu);
+    *ms = c->last_device_ms;
+    return AQMP_OK;
+}
 
 int aqmp_autotune_read(aqmp_tune_entry *out, int max, int *n) {
     if (!n || (max > 0 && !out)) return fail(AQMP_E_ARG, "NULL argument");
@@ -1129,7 +1144,9 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
     auto replay = [&](Ctx::Graph &gr) -> int {
         CK(cudaEventRecord(c->graph_in, st));
         CK(cudaStreamWaitEvent(c->graph_stream, c->graph_in, 0));
+        CK(cudaEventRecord(c->dev_t0, c->graph_stream));
         CK(cudaGraphLaunch(gr.exec, c->graph_stream));
+        CK(cudaEventRecord(c->dev_t1, c->graph_stream));
         CK(cudaEventRecord(c->graph_out, c->graph_stream));
         CK(cudaStreamWaitEvent(st, c->graph_out, 0));
         if (!gr.prof.empty()) {
@@ -1138,6 +1155,11 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
         }
         return AQMP_OK;
     };
+    if (!c->dev_t0) {
+        CK(cudaEventCreate(&c->dev_t0));
+        CK(cudaEventCreate(&c->dev_t1));
+    }
+    c->last_device_ms = -1.0f;
     auto git = c->graphs.find(key);
     if (git != c->graphs.end() && git->second.generation != g_ws_generation.load()) {
         c->drop_graphs();
@@ -1184,11 +1206,18 @@ int aqmp_encode_planes(const aqmp_params *params, const aqmp_plane *planes, int 
             cudaGetLastError();
         }
         if (!done) {
+            CK(cudaEventRecord(c->dev_t0, st));
             if ((rc = body(st))) return rc;
+            CK(cudaEventRecord(c->dev_t1, st));
             if (runs >= 0) ++runs;
         }
     }
     CK(cudaStreamSynchronize(st));
+    {
+        float ms = -1.0f;
+        if (cudaEventElapsedTime(&ms, c->dev_t0, c->dev_t1) == cudaSuccess) c->last_device_ms = ms;
+        cudaGetLastError();
+    }
     {
         std::lock_guard<std::mutex> pl(g_prof.mu);
         g_prof.resolve();

@@ -85,4 +85,5 @@ def test_null_and_empty_inputs_are_rejected(lib):
     assert lib.aqmp_correlate(12, 0, None, 4, None, 0, None) == -1
     assert lib.aqmp_correlate(8, 5, None, 4, None, 0, None) == -3
     assert lib.aqmp_correlate(64, 0, None, 0, None, 7, None) == -1      # no such mode
+    assert lib.aqmp_last_device_ms(None) == -1
     assert lib.aqmp_correlate(32, 0, None, 0, None, 6, None) == -8      # tensor cores for every family: side 64 only
