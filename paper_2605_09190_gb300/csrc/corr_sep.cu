@@ -74,8 +74,15 @@ struct SepSmem {
 
 __device__ __forceinline__ long long bf_value(int2 w) { return (long long)w.y * (1ll << 24) + w.x; }
 
-__device__ __forceinline__ __int128 load_i128(const ulonglong2 &v) {
-    return (__int128)(((unsigned __int128)v.y << 64) | v.x);
+// P K for 0 <= P < 2^96 (as 64-bit halves lo, hi < 2^32) and |K| < 2^31:
+// three 32 x 32 -> 64-bit products joined in int128.
+__device__ __forceinline__ __int128 mul_u96_i32(const ulonglong2 &P, int K) {
+    const unsigned k = (unsigned)(K < 0 ? -K : K);
+    const unsigned long long a0 = (unsigned long long)(unsigned)P.x * k;
+    const unsigned long long a1 = (unsigned long long)(unsigned)(P.x >> 32) * k;
+    const unsigned long long a2 = (unsigned long long)(unsigned)P.y * k;
+    const unsigned __int128 m = (unsigned __int128)a0 + ((unsigned __int128)a1 << 32) + ((unsigned __int128)a2 << 64);
+    return K < 0 ? -(__int128)m : (__int128)m;
 }
 
 // One CTA handles G leaves at a time (grid-stride over the leaves).
@@ -274,9 +281,10 @@ corr_sep_simt_kernel(int nf, int fam0, int fmask, int Kpad, const int2 *__restri
                     const int LL = s11 - s01 - s10 + s00, LR = s12 - s02 - s11 + s01;
                     const int RL = s21 - s11 - s20 + s10, RR = s22 - s12 - s21 + s11;
                     const int K = (LL + hq.w * LR) + hp.w * (RL + hq.w * RR);
-                    __int128 T = load_i128(ptab[hp.z * E + hq.z]) * (__int128)K;
-                    const long long Rp = R[p], Rq = R[q];
-                    if (Rp != 0 && Rq != 0) T += (__int128)(128ll * Rp) * Rq;
+                    __int128 T = mul_u96_i32(ptab[hp.z * E + hq.z], K);
+                    // rows r >= 1 sum to zero (halves of equal length and
+                    // opposite values), so only (0, 0) has a centring term
+                    if ((p | q) == 0) T += (__int128)(128ll * R[0]) * R[0];
                     if (g < live) {
                         const df c = int128_to_df(T);
                         out[(base + g) * M + q * B + p] = make_float2(c.hi, c.lo);

@@ -95,10 +95,10 @@ void make_bases(int b, std::vector<double> &basis) {
 }
 
 // The exact SIMT correlation relies on these facts of the rows: DCT-II row
-// k equals (-1)^k times its mirror image; Haar row r is v_r on the first of
-// the halves haar_halves gives and -v_r on the second (row 0: v_0 on both),
-// zero elsewhere, with v_r the same for every row of one scale (the rows
-// 2^j .. 2^(j+1) - 1).  Checked once per dictionary.
+// k equals (-1)^k times its mirror image; Haar row r is v_r > 0 on the
+// first of the halves haar_halves gives and -v_r on the second (row 0: v_0
+// on both), zero elsewhere, with v_r the same for every row of one scale
+// (the rows 2^j .. 2^(j+1) - 1).  Checked once per dictionary.
 bool sep_rows_structured(int b, const std::vector<double> &basis) {
     const double *C = basis.data(), *H = basis.data() + (size_t)b * b;
     for (int k = 0; k < b; ++k) {
@@ -110,7 +110,7 @@ bool sep_rows_structured(int b, const std::vector<double> &basis) {
         if (k > 0)
             while (first & (first - 1)) first &= first - 1;
         const double v = H[k * b + s];
-        if (v == 0.0 || v != H[first * b]) return false;
+        if (!(v > 0.0) || v != H[first * b]) return false;
         for (int m = 0; m < b; ++m) {
             const double want = m < s || m >= s + 2 * h ? 0.0 : (m < s + h || k == 0) ? v : -v;
             if (H[k * b + m] != want) return false;
