@@ -368,6 +368,15 @@ int aqmp_correlate_noalloc(int b, int dict_id, const uint8_t *blocks, int64_t L,
  * AQMP_OK would mean the wait was not bounded. */
 int aqmp_selftest_wait(int limit_ms, void *stream);
 
+/* The rounding every exact correlation ends in: each of n integers T
+ * (device memory, two int64 words per value, low word first, two's
+ * complement, |T| < 2^112) becomes the double-float
+ * (RN(T), RN(T - RN(T))) 2^-96, ties to even, written to `out` (device,
+ * n float pairs; a zero low word carries the sign of T).  For tests of that
+ * rounding against exact integer arithmetic.  Synchronises `stream`.  Errors: AQMP_E_ARG (NULL or
+ * unaligned pointers, n out of [0, 2^31)), AQMP_E_CUDA. */
+int aqmp_selftest_round(const int64_t *words, int64_t n, float *out, void *stream);
+
 /* ---- Codec stages around the encoder (Section 2.3 and Appendix A) ----
  * Step (i) converts the channels of an image to RGB or YCbCr and codes each
  * channel on its own; step (iii) applies a lossless coder (DEFLATE) to the

@@ -76,7 +76,7 @@ EXPORTS = ["aqmp_params_default", "aqmp_encode_planes", "aqmp_encode", "aqmp_cod
            "aqmp_synth_backward", "aqmp_ssim", "aqmp_image_to_planes", "aqmp_planes_to_image",
            "aqmp_bitstream_size", "aqmp_bitstream_write", "aqmp_bitstream_parse", "aqmp_code_from_bitstream",
            "aqmp_autotune_read", "aqmp_autotune_reset", "aqmp_profile_filter", "aqmp_encode_batch",
-           "aqmp_correlate_bf16x2", "aqmp_last_device_ms"]
+           "aqmp_correlate_bf16x2", "aqmp_last_device_ms", "aqmp_selftest_round"]
 
 
 class aqmp_tune_entry(ctypes.Structure):
@@ -136,6 +136,7 @@ def load_library(path: str | None = None):
         lib.aqmp_num_atoms.argtypes = [I, I]
         lib.aqmp_last_error.restype = ctypes.c_char_p
         lib.aqmp_last_device_ms.argtypes = [ctypes.POINTER(ctypes.c_double)]
+        lib.aqmp_selftest_round.argtypes = [V, I64, V, V]
         lib.aqmp_version.restype = ctypes.c_char_p
         lib.aqmp_profile_enable.argtypes = [I]
         lib.aqmp_profile_reset.argtypes = []
@@ -358,6 +359,18 @@ def aqmp_correlate_bf16x2(b: int, dict_id: int, blocks, stream=None):
                                                 ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(bound.data_ptr()),
                                                 _stream_handle(stream)))
     return out, bound
+
+
+def aqmp_selftest_round(words, stream=None):
+    """int128 -> double-float rounding on the device: `words` is a CUDA int64
+    tensor of shape (n, 2), (low, high) words of each integer T; returns a
+    CUDA float32 tensor (n, 2) of (RN(T), RN(T - RN(T))) 2^-96."""
+    import torch
+    words = words.contiguous()
+    out = torch.empty((words.shape[0], 2), dtype=torch.float32, device=words.device)
+    _check(load_library().aqmp_selftest_round(ctypes.c_void_p(words.data_ptr()), words.shape[0],
+                                              ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)))
+    return out
 
 
 def aqmp_last_device_ms() -> float:

@@ -24,6 +24,7 @@
 #include "../../include/aqmp.h"
 #include "common.cuh"
 #include "kernels.h"
+#include "selftest.h"
 #include "haar_rows.cuh"
 #include "code.h"
 
@@ -1458,6 +1459,21 @@ int aqmp_selftest_wait(int limit_ms, void *stream) {
     CK(cudaStreamSynchronize(st));
     if (c->host_ctr->error == kDevErrTimeout)
         return fail(AQMP_E_TIMEOUT, "bounded device wait gave up after %d ms (as intended)", limit_ms);
+    return AQMP_OK;
+}
+
+int aqmp_selftest_round(const int64_t *words, int64_t n, float *out, void *stream) {
+    g_last_error.clear();
+    if (n < 0 || n > 0x7fffffffLL || (n > 0 && (!words || !out))) return fail(AQMP_E_ARG, "bad arguments");
+    if (n == 0) return AQMP_OK;
+    if (((uintptr_t)words & 7) != 0 || ((uintptr_t)out & 7) != 0)
+        return fail(AQMP_E_ARG, "words and out must be 8-byte aligned");
+    Ctx *c;
+    int rc;
+    if ((rc = get_ctx(&c))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(launch_round_selftest((const long long *)words, (long long)n, (float2 *)out, st));
+    CK(cudaStreamSynchronize(st));
     return AQMP_OK;
 }
 

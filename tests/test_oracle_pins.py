@@ -49,6 +49,38 @@ def test_haar_rows_match_filter_bank(b):
     np.testing.assert_allclose(oracle.haar_1d(b), ref, atol=2e-15, rtol=0)
 
 
+@pytest.mark.parametrize("b", SIDES + [64, 128])
+def test_dct_rows_are_even_or_odd_about_the_centre(b):
+    # cos(pi k (2 (b - 1 - m) + 1) / 2b) = (-1)^k cos(pi k (2m + 1) / 2b): the
+    # symmetry the exact separable kernels use to halve the DCT-II contractions
+    C = scipy.fft.dct(np.eye(b), type=2, norm="ortho", axis=0)
+    sign = (-1.0) ** np.arange(b)[:, None]
+    np.testing.assert_allclose(C[:, ::-1], sign * C, atol=2e-13, rtol=0)
+    np.testing.assert_allclose(oracle.dct_1d(b)[:, ::-1], sign * oracle.dct_1d(b), atol=2e-13, rtol=0)
+
+
+@pytest.mark.parametrize("b", SIDES + [64, 128])
+def test_haar_rows_are_two_constant_halves_of_one_magnitude_per_scale(b):
+    # each Haar row is v > 0 on the first half of a dyadic interval and -v on
+    # the second (row 0: v on the whole block), with v fixed by the interval's
+    # length: the structure behind the summed-area form of the Haar correlations
+    H = np.stack([fast_haar_1d(e) for e in np.eye(b)], axis=1)
+    by_len = {}
+    for r in range(b):
+        nz = np.nonzero(np.abs(H[r]) > 1e-12)[0]
+        s, e = int(nz[0]), int(nz[-1]) + 1
+        L = e - s
+        assert len(nz) == L and L & (L - 1) == 0 and s % L == 0
+        v = H[r, s]
+        assert v > 0
+        want = np.full(L, v) if r == 0 else np.concatenate([np.full(L // 2, v), np.full(L // 2, -v)])
+        np.testing.assert_allclose(H[r, s:e], want, atol=1e-15, rtol=0)
+        key = (L, r == 0)
+        by_len.setdefault(key, v)
+        assert abs(by_len[key] - v) < 1e-15
+        np.testing.assert_allclose(oracle.haar_1d(b)[r], H[r], atol=2e-15, rtol=0)
+
+
 @pytest.mark.parametrize("b", SIDES)
 def test_dictionary_families_orthonormal(b):
     n = b * b
