@@ -55,8 +55,9 @@ constexpr int sep_threads() { return B >= 128 ? 768 : 256; }
 
 // Shared-memory layout of one CTA (G leaves): the centred pixels, their
 // even and odd column halves, and the Z~ region, which the Haar pass reuses
-// for its summed-area table.
-template <int B>
+// for its summed-area table.  A Haar-only launch (HO) keeps the pixels and
+// the table alone.
+template <int B, bool HO = false>
 struct SepSmem {
     static constexpr int n = B * B, H = B / 2, G = sep_group<B>();
     static constexpr int RS = B + 1;                           // row stride of Z~+- and of the table
@@ -64,9 +65,10 @@ struct SepSmem {
                                                                // transposing stores hit distinct banks
     static constexpr size_t yt = 0;                            // int8  [G][i][YS]
     static constexpr size_t ys = (G * B * YS + 15) & ~15;      // int16 [G][parity][i < H][m]
-    static constexpr size_t z = ys + ((2 * G * n + 15) & ~15); // Limbs2 [G][p][RS]  /  int [G][RS][RS]
+    static constexpr size_t z = ys + (HO ? 0 : ((2 * G * n + 15) & ~15));   // Limbs2 [G][p][RS] / int [G][RS][RS]
+    static constexpr size_t zbytes = HO ? ((sizeof(int) * G * RS * RS + 15) & ~15) : sizeof(Limbs2) * G * B * RS;
     static constexpr int E = 1 + ilog2(B);                     // Haar scale classes: row 0, scales 1 .. b/2
-    static constexpr size_t hrow = z + sizeof(Limbs2) * G * B * RS;   // int4 [B]: s, h, class, sign
+    static constexpr size_t hrow = z + zbytes;                 // int4 [B]: s, h, class, sign
     static constexpr size_t ptab = hrow + sizeof(int4) * B;    // ulonglong2 [E][E]: fL(c1) fL(c2), int128
     static constexpr size_t bytes = ptab + sizeof(ulonglong2) * E * E;
     static_assert(sizeof(int) * RS * RS <= sizeof(Limbs2) * B * RS, "table fits the Z~ region");
@@ -102,13 +104,14 @@ __device__ __forceinline__ __int128 mul_u96_i32(const ulonglong2 &P, int K) {
 // over the four half-by-half rectangles, read from the summed-area table of
 // y~ (|entries| <= 2^21, |K| <= 2^21); the products fL(c1) fL(c2) of the
 // 1 + log2 b scale classes are formed once per CTA in int128.
-template <int B>
+template <int B, bool HO>
 __global__ void __launch_bounds__(sep_threads<B>())
 corr_sep_simt_kernel(int nf, int fam0, int fmask, int Kpad, const int2 *__restrict__ Bs, const int2 *__restrict__ BsT,
                      const long long *__restrict__ Rs, const __nv_bfloat16 *__restrict__ Y,
                      const unsigned *count_dev, long long fixed_count, float2 *__restrict__ c0) {
-    using L = SepSmem<B>;
+    using L = SepSmem<B, HO>;
     constexpr int n = L::n, H = L::H, G = L::G, RS = L::RS, YS = L::YS;
+    if (HO) fmask &= 2;                                       // the Haar family alone
     constexpr int PT = 4;                                     // p values per thread in DCT stage 2
     static_assert(B >= PT && B % PT == 0, "side");
     extern __shared__ __align__(16) unsigned char smem[];
@@ -160,6 +163,7 @@ corr_sep_simt_kernel(int nf, int fam0, int fmask, int Kpad, const int2 *__restri
             const long long *R = Rs + F * B;
             float2 *out = c0 + (nf == 2 ? f * n : 0);
             if (F == 0) {
+                if constexpr (!HO) {
                 const int2 *BfT = BsT + (size_t)F * n;
                 for (int o = tid; o < G * H * B; o += nt) {
                     const int g = o / (H * B), r = o - g * (H * B);
@@ -226,6 +230,7 @@ corr_sep_simt_kernel(int nf, int fam0, int fmask, int Kpad, const int2 *__restri
                         for (int k = 0; k < PT / 2; ++k)
                             dst[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
                     }
+                }
                 }
             } else {
                 // summed-area table S[i][m] = sum of y~ over [0, i) x [0, m):
@@ -296,11 +301,11 @@ corr_sep_simt_kernel(int nf, int fam0, int fmask, int Kpad, const int2 *__restri
     }
 }
 
-template <int B>
+template <int B, bool HO>
 static cudaError_t launch_sep_simt_t(const CorrArgs &a, cudaStream_t st) {
     constexpr int G = sep_group<B>();
-    const size_t smem = SepSmem<B>::bytes;
-    auto kern = corr_sep_simt_kernel<B>;
+    const size_t smem = SepSmem<B, HO>::bytes;
+    auto kern = corr_sep_simt_kernel<B, HO>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -321,13 +326,17 @@ static cudaError_t launch_sep_simt_t(const CorrArgs &a, cudaStream_t st) {
 }
 
 cudaError_t launch_corr_sep_simt(const CorrArgs &a, cudaStream_t st) {
-    switch (a.d->b) {
-        case 4: return launch_sep_simt_t<4>(a, st);
-        case 8: return launch_sep_simt_t<8>(a, st);
-        case 16: return launch_sep_simt_t<16>(a, st);
-        case 32: return launch_sep_simt_t<32>(a, st);
-        case 64: return launch_sep_simt_t<64>(a, st);
-        case 128: return launch_sep_simt_t<128>(a, st);
+    // the Haar family alone gets its own instantiation: no DCT-II code or
+    // shared memory, so more CTAs fit on an SM
+    const DictDev &d = *a.d;
+    const bool ho = a.fmask == 2 || (d.nf == 1 && d.fam0 == 1);
+    switch (d.b) {
+        case 4: return ho ? launch_sep_simt_t<4, true>(a, st) : launch_sep_simt_t<4, false>(a, st);
+        case 8: return ho ? launch_sep_simt_t<8, true>(a, st) : launch_sep_simt_t<8, false>(a, st);
+        case 16: return ho ? launch_sep_simt_t<16, true>(a, st) : launch_sep_simt_t<16, false>(a, st);
+        case 32: return ho ? launch_sep_simt_t<32, true>(a, st) : launch_sep_simt_t<32, false>(a, st);
+        case 64: return ho ? launch_sep_simt_t<64, true>(a, st) : launch_sep_simt_t<64, false>(a, st);
+        case 128: return ho ? launch_sep_simt_t<128, true>(a, st) : launch_sep_simt_t<128, false>(a, st);
     }
     return cudaErrorInvalidValue;
 }
