@@ -11,10 +11,11 @@
 //   stage 1  Z~[p][m] = sum_i Bf[p][i] y~[i][m]   (48-bit x 8-bit -> int64)
 //   stage 2  T~[p][q] = sum_m Bf[q][m] Z~[p][m]   (48-bit x 59-bit -> int128)
 // Bf is held as 24-bit limbs (lo in [-2^23, 2^23), hi = (Bf - lo) / 2^24,
-// |hi| < 2^23.5) and Z~ as two 32-bit ones (zl in [-2^31, 2^31), zh =
-// (Z~ - zl) / 2^32, |zh| < 2^27), so every partial product is one 32 x 32 ->
-// 64-bit multiply-add, at most 2^54.5 in magnitude, and each of the four
-// limb sums over b <= 128 terms stays below 2^62.
+// |hi| < 2^23.5), and the stage-1 results (Z~+-, below, |Z~+-| < 2^60) as
+// two 32-bit ones (zl in [-2^31, 2^31), zh = (z - zl) / 2^32, |zh| < 2^28),
+// so every partial product is one 32 x 32 -> 64-bit multiply-add, at most
+// 2^54.5 in magnitude, and each of the four limb sums over at most b/2 = 64
+// terms stays below 2^61.
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
@@ -47,7 +48,7 @@ __device__ __forceinline__ long long mul_wide(int32_t a, int32_t b) { return (lo
 
 }  // namespace
 
-// Threads per CTA: at side 128 the leaf's shared memory (177 KB, most of it
+// Threads per CTA: at side 128 the leaf's shared memory (181 KB, most of it
 // Z~+-) leaves room for one CTA per SM, so that CTA takes 768 threads to hide
 // the latency of its loads; 256 elsewhere.
 template <int B>
